@@ -1,0 +1,343 @@
+"""Throughput of the fused Reg-FLBM D3Q27 step on GB300, one JSON line on stdout.
+
+Workload (default): periodic 128^3 box, float32 populations, tau 0.8, rho0 1, kT 1e-4,
+Philox seed 1, fluid at rest thermalised by the warm-up steps (the thermal-equilibrium
+configuration of the paper's tests). One step = one launch of the fused
+stream-and-collide kernel over every site. The two population buffers (2 x 226 MB)
+exceed the 129 MB L2, so no flush is needed between steps.
+
+Arms:
+  --impl gb300 (default): the CUDA library through its C ABI; N > 1 ranks (torchrun)
+      run independent replicas (weak scaling), barrier + max-over-ranks timing.
+  --impl reference: the FP64 CPU oracle on the host cores, each step a bounded sample
+      of sites of the same box, sized so the whole run ends within a few minutes.
+
+Reported: MLUPS (sites x steps / s / 1e6) from CUDA events on the launching stream; the
+roofline of the step kernel (216 algorithmic bytes per site update against the measured
+HBM copy bandwidth); the end-to-end MLUPS through the ABI with host buffers; the
+oracle's CPU MLUPS on a bounded sample; SM clocks sampled during the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Reg-FLBM D3Q27 MLUPS + % HBM roofline, FP32 vs mixed at fixed FDT error"
+BYTES_PER_SITE_F32 = 216          # 27 float32 read + 27 float32 written per site update
+FALLBACK_HBM_GBS = 6800.0
+PROFILE = os.path.join(ROOT, "profiles", "step_pull_f32_128cubed.md")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--edge", type=int, default=128)
+    ap.add_argument("--tau", type=float, default=0.8)
+    ap.add_argument("--kT", type=float, default=1e-4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    e = args.edge
+    return {"workload": f"periodic {e}^3 Reg-FLBM D3Q27 thermal equilibrium, float32 "
+                        f"populations, tau {args.tau}, rho0 1, kT {args.kT:g}, seed 1, rest start",
+            "box": [e, e, e], "sites": e ** 3, "tau": args.tau, "kT": args.kT,
+            "storage": "f32 shifted by w_i rho0", "streaming": "pull, ping-pong",
+            "l2": f"inputs {2 * 27 * 4 * e ** 3 / 1e6:.0f} MB (two population buffers) > 129 MB L2, no flush",
+            "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ measurement helpers
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            peaks = json.load(fh)
+        return float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_08820_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
+    when the summary is missing or was taken on different kernel sources."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(sources ([0-9a-f]+)\)", text)
+    if not m or m.group(2) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join("/tmp", f"rflbm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": []}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = sorted(x for x in (num(r[1]) for r in rows) if x is not None)
+        mx = [x for x in (num(r[2]) for r in rows) if x is not None]
+        pw = [x for x in (num(r[3]) for r in rows) if x is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
+
+
+def device_uuid(torch):
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_sample_rate(edge, tau, kT, budget_s, min_sites=64, max_sites=None, steps=None):
+    """Times the FP64 oracle's per-site collision plus streaming on sampled sites of the
+    same box in a single-threaded subprocess; returns (MLUPS, sites, steps, seconds)."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import rflbm_oracle as o
+from paper_2507_08820_gb300 import workloads as W
+edge, tau, kT, budget = {edge}, {tau}, {kT}, {budget_s}
+n = edge ** 3
+# calibrate on a small sample, then size the per-step sample to the budget
+f = o.rest_state(512) + W.population_perturbation(512, 3, 1e-4)
+t0 = time.perf_counter(); o.collide(f, tau, kT, 1, 0, np.arange(512, dtype=np.uint64)); dt = time.perf_counter() - t0
+per_site = dt / 512
+steps = {steps if steps else 0} or 3
+m = int(budget / steps / per_site)
+m = max({min_sites}, min(m, {max_sites if max_sites else 'n'}, n))
+sites = W.sample_sites(n, m, 7)
+f = o.rest_state(sites.size) + W.population_perturbation(sites.size, 5, 1e-4)
+t0 = time.perf_counter()
+for t in range(steps):
+    fs = o.collide(f, tau, kT, 1, t, sites.astype(np.uint64))
+    f = o.stream(fs, (sites.size, 1, 1))
+el = time.perf_counter() - t0
+print(json.dumps(dict(mlups=sites.size * steps / el / 1e6, sites=int(sites.size), steps=steps, seconds=el)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         timeout=max(600, 20 * budget_s))
+    if res.returncode != 0:
+        raise RuntimeError("oracle timing failed:\n" + res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args):
+    from paper_2507_08820_gb300 import dist
+    info = dist.rank_info()
+    if info.rank != 0:
+        return 0
+    # each of the warmup + steps "steps" collides a bounded sample of the box's sites;
+    # the whole run is held to about two minutes of CPU
+    total = max(1, args.steps + args.warmup)
+    r = oracle_sample_rate(args.edge, args.tau, args.kT, budget_s=min(120.0, 2.0 * total),
+                           min_sites=16, steps=total)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": r["mlups"], "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * r["seconds"] / r["steps"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload(args),
+        "cpu_baseline": {"value": r["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 oracle collision + streaming of {r['sites']} sampled "
+                                   f"sites of the {args.edge}^3 box per step, {r['steps']} steps, "
+                                   f"{r['seconds']:.1f} s, one thread"},
+        "e2e": {"value": r["mlups"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def time_steps(R, torch, box, stream, steps):
+    """CUDA-event time (ms) of `steps` launches on the box's stream."""
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    R.rflbm_step(box.h, steps)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end)
+
+
+def gb300_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_2507_08820_gb300 import build, dist
+    build.build()
+    from paper_2507_08820_gb300 import rflbm as R
+
+    info = dist.rank_info()
+    torch.cuda.set_device(info.local_rank)
+    dev = torch.device("cuda", info.local_rank)
+    dist.init(info, "nccl")
+    e = args.edge
+    n = e ** 3
+    stream = torch.cuda.Stream(device=dev)
+    box = R.Box(e, e, e, tau=args.tau, kT=args.kT, seed=1, replica=info.rank,
+                stream=stream.cuda_stream, torch_buffers=True, device=info.local_rank)
+    R.rflbm_init_rest(box.h)
+    R.rflbm_step(box.h, args.warmup)
+    R.rflbm_synchronize(box.h)
+
+    sampler = ClockSampler(device_uuid(torch))
+    dist.barrier(info, info.local_rank)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)  # let the sampler take its first reading
+    ms = time_steps(R, torch, box, stream, args.steps)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    dist.barrier(info, info.local_rank)
+    ms_max = dist.max_over_ranks(info, ms, dev)
+    st, status = R.rflbm_stats(box.h)
+
+    # end to end through the ABI with host buffers: pinned populations in, stats out
+    k_e2e = max(3, min(args.steps, 2000) // 10)
+    host = torch.empty((27, n), dtype=torch.float32).pin_memory()
+    R.rflbm_get_populations_f32(box.h, host)
+    R.rflbm_set_populations_f32(box.h, host)   # untimed: allocates the staging buffer
+    dist.barrier(info, info.local_rank)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        R.rflbm_set_populations_f32(box.h, host)
+        R.rflbm_step(box.h, 1)
+        R.rflbm_stats(box.h)
+    e2e_s = dist.max_over_ranks(info, time.perf_counter() - t0, dev)
+
+    variants = {}
+    if not args.no_variants and info.world == 1:
+        for name, kw in (("reg_lbm_kT0", dict(kT=0.0)),
+                         ("bgk_flbm", dict(kT=args.kT, model=R.RFLBM_MODEL_BGK))):
+            vb = R.Box(e, e, e, tau=args.tau, seed=1, stream=stream.cuda_stream, **kw)
+            R.rflbm_init_rest(vb.h)
+            R.rflbm_step(vb.h, 50)
+            k = max(10, args.steps // 4)
+            vms = time_steps(R, torch, vb, stream, k)
+            variants[name] = {"value": n * k / (vms * 1e-3) / 1e6, "unit": "MLUPS", "steps": k}
+            vb.close()
+    box.close()
+
+    if info.rank != 0:
+        dist.finalize(info)
+        return 0
+    value = info.world * n * args.steps / (ms_max * 1e-3) / 1e6
+    per_launch_s = ms * 1e-3 / args.steps
+    achieved = BYTES_PER_SITE_F32 * n / per_launch_s / 1e9
+    peak, peak_kind = measured_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(),
+                "peak_source": f"hbm_gbs of {peak_kind}",
+                "kernel": "step_pull_f32<Reg, noise>",
+                "algorithmic_bytes_per_launch": BYTES_PER_SITE_F32 * n}
+    cpu = None
+    if not args.no_cpu_baseline:
+        r = oracle_sample_rate(e, args.tau, args.kT, budget_s=15.0, steps=2)
+        cpu = {"value": r["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 oracle collision + streaming of {r['sites']} sampled sites of "
+                         f"the {e}^3 box, {r['steps']} steps, {r['seconds']:.1f} s, one thread"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": info.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload(args), "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": info.world * n * k_e2e / e2e_s / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": 27 * 4 * n, "d2h_bytes_per_step": 6 * 8, "steps": k_e2e,
+                "path": "rflbm_set_populations_f32 (pinned host) + rflbm_step + rflbm_stats"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "stats_after": {"mass_rel_drift": (st.mass - n) / n, "max_speed": st.max_speed,
+                        "nonfinite": st.nonfinite},
+        "variants": variants,
+    }
+    print(json.dumps(line))
+    dist.finalize(info)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gb300_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

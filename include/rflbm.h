@@ -1,0 +1,195 @@
+/*
+ * rflbm.h - C ABI of a GB300 (sm_103a) implementation of the regularized fluctuating
+ * lattice Boltzmann model on the D3Q27 lattice (Reg-FLBM; Lauricella, Montessori,
+ * Tiribocchi, Succi, arXiv 2507.08820).
+ *
+ * One handle holds one periodic box of nx*ny*nz lattice sites and advances it with the
+ * fused per-site stream-and-collide step of Eq. 25 (Sec. II.B): density, velocity and
+ * the second Hermite moment are projected from the 27 populations, the equilibrium is
+ * the full D3Q27 Hermite expansion of Eq. 26 with the recursive coefficients of Eq. 21,
+ * the stress modes relax at omega_h = 1/tau, the ghost modes at omega_g (1 in the
+ * paper), Gaussian noise with the amplitude of Eq. 10 enters every non-conserved mode
+ * (k = 4..26 of Table II), the populations are rebuilt by the back transform of Eq. 11
+ * and streamed (Eq. 8).
+ *
+ * Conventions used by every entry point
+ *   - Sites: s = x + nx*(y + ny*z), x fastest; every field is indexed by s.
+ *   - Populations: 27 planes of N = nx*ny*nz values, plane i holding f_i for every site
+ *     ("structure of arrays", element [i*N + s]). Velocity order (Table I groups; order
+ *     inside a group as follows): i = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = the
+ *     (x,y), (x,z), (y,z) diagonals each as (+,+),(+,-),(-,+),(-,-); 19..26 =
+ *     (+-1,+-1,+-1) counting in binary with x slowest and + before -.
+ *   - Time: the state held is the pre-collision f(x, t) of step t (t = 0 after an init
+ *     call). rflbm_step(h, n) takes steps t .. t+n-1; the noise of step t at site s is
+ *     drawn from Philox4x32-10 (Salmon et al., SC'11) at counter (s, t, j, replica),
+ *     j = 0..5, key (seed mod 2^32, seed div 2^32), Box-Muller on word pairs (0,1) and
+ *     (2,3), uniforms (x + 1/2) 2^-32, r_k = n[k - 4].
+ *   - on_device: 0 = the pointer is host memory (pinned or pageable), 1 = CUDA device
+ *     memory of the handle's device. The caller owns every buffer it passes; the
+ *     library never frees caller memory.
+ *   - Errors: functions returning int return RFLBM_OK (0) or a negative rflbm_status;
+ *     functions returning a pointer return NULL. rflbm_last_error() then describes the
+ *     failure (thread-local, valid until the next call on the same thread). Work is
+ *     enqueued on the handle's stream; a CUDA error raised by a kernel surfaces at the
+ *     next call that synchronises (moments, stats, get_*, synchronize).
+ */
+#ifndef RFLBM_H
+#define RFLBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rflbm rflbm_t;
+
+typedef enum {
+  RFLBM_OK = 0,
+  RFLBM_EINVAL = -1,     /* invalid argument (sizes, tau <= 1/2, kT < 0, rho0 <= 0, ...) */
+  RFLBM_ENOMEM = -2,     /* device or host allocation failed */
+  RFLBM_ECUDA = -3,      /* CUDA runtime error (no device, launch or kernel failure) */
+  RFLBM_EUNSTABLE = -4,  /* the state holds non-finite values (reported by rflbm_stats) */
+  RFLBM_ETIMEOUT = -5,   /* a bounded device wait expired */
+  RFLBM_ESTATE = -6      /* call not valid in the handle's current state */
+} rflbm_status;
+
+typedef enum {
+  RFLBM_MODEL_REG = 0,   /* Reg-FLBM, Eq. 25 (Eq. 24 split with omega_g) */
+  RFLBM_MODEL_BGK = 1    /* BGK-FLBM, Eq. 12 with the equilibrium of Eq. 26 (Sec. III) */
+} rflbm_model;
+
+typedef enum {
+  RFLBM_STORE_F32 = 0    /* populations stored as float32, shifted by w_i*rho0 */
+} rflbm_storage;
+
+typedef enum {
+  RFLBM_PHI_LOCAL_RHO = 0, /* rho in Eq. 10 is the site's density (default) */
+  RFLBM_PHI_RHO0 = 1       /* rho in Eq. 10 is the reference density rho0 */
+} rflbm_phi_rho;
+
+typedef struct {
+  int nx, ny, nz;        /* box edges, each >= 1; N = nx*ny*nz < 2^31 */
+  double tau;            /* hydrodynamic relaxation time tau_h = 1/omega_h > 1/2 */
+  double kT;             /* thermal energy k_B T >= 0 (0: deterministic Reg-LBM) */
+  double rho0;           /* reference density > 0 (rest state, storage shift) */
+  uint64_t seed;         /* Philox key */
+  double omega_g;        /* ghost relaxation rate in (0, 2); the paper uses 1 */
+  int model;             /* rflbm_model */
+  int storage;           /* rflbm_storage */
+  int phi_rho;           /* rflbm_phi_rho */
+  uint32_t replica;      /* fourth Philox counter word (independent replicas) */
+  void* stream;          /* cudaStream_t for all work, NULL = legacy default stream */
+  void* buffers[2];      /* optional caller-owned device buffers of
+                            rflbm_buffer_bytes(cfg) bytes each, 256-byte aligned;
+                            NULL: the library allocates and frees them */
+  int device;            /* CUDA device ordinal, -1 = the current device */
+} rflbm_config_t;
+
+typedef struct {
+  int64_t step;          /* current step t */
+  double mass;           /* sum_s rho(s) (Eq. 3), FP64 accumulation */
+  double momentum[3];    /* sum_s rho u(s) (Eq. 4), FP64 accumulation */
+  double max_speed;      /* max_s |u(s)| */
+  int64_t nonfinite;     /* sites whose density or momentum is not finite */
+} rflbm_stats_t;
+
+/* Fills cfg with the defaults: 32^3, tau 0.8, kT 0, rho0 1, seed 1, omega_g 1, Reg model,
+ * float32 storage, local rho in Eq. 10, replica 0, default stream, library buffers,
+ * current device. */
+void rflbm_config_default(rflbm_config_t* cfg);
+
+/* Bytes of one population buffer for cfg (two are used, ping-pong), or a negative
+ * rflbm_status if cfg is invalid. */
+int64_t rflbm_buffer_bytes(const rflbm_config_t* cfg);
+
+/* Creates a handle for a periodic box with the paper's defaults (Reg-FLBM, omega_g = 1,
+ * Sec. II.B) and the state uninitialised (call an init function before stepping).
+ * NULL on error. */
+rflbm_t* rflbm_create(int nx, int ny, int nz, double tau, double kT, double rho0,
+                      uint64_t seed);
+
+/* Creates a handle from a full configuration. NULL on error. */
+rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg);
+
+/* Releases the handle and the device memory the library allocated for it. NULL is a
+ * no-op. Waits for the handle's outstanding work. */
+void rflbm_destroy(rflbm_t* h);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char* rflbm_last_error(void);
+
+/* Fluid at rest: f_i = w_i rho0 (Table I weights; the u = 0 value of Eq. 26); t = 0. */
+int rflbm_init_rest(rflbm_t* h);
+
+/* f_i(x, 0) = f_i^(0)(rho(x), u(x)), the equilibrium of Eq. 26; t = 0.
+ * rho: N doubles, or NULL for rho0 everywhere; u: 3*N doubles (rows x, y, z), or NULL
+ * for rest. Host or device memory per on_device. */
+int rflbm_init_field(rflbm_t* h, const double* rho, const double* u, int on_device);
+
+/* Advances n >= 0 steps (Eq. 25, or Eq. 12 for the BGK model, then Eq. 8). Asynchronous
+ * on the handle's stream. */
+int rflbm_step(rflbm_t* h, int64_t n);
+
+/* Pre-collision moments of the current state, FP64 (Eqs. 3-4; Pi = a^(2) of Sec. III):
+ * rho (N), u (3*N, rows x, y, z), pi (6*N, rows xx, yy, zz, xy, xz, yz with
+ * Pi_ab = sum_i f_i (c_ia c_ib - cs2 delta_ab)). Any pointer may be NULL to skip that
+ * field. Synchronous. */
+int rflbm_moments(rflbm_t* h, double* rho, double* u, double* pi, int on_device);
+
+/* Global diagnostics of the current state in FP64 (see rflbm_stats_t). Synchronous.
+ * Returns RFLBM_EUNSTABLE (with *out filled) when non-finite values are present. */
+int rflbm_stats(rflbm_t* h, rflbm_stats_t* out);
+
+/* Current populations f_i(x, t) as 27*N doubles / floats (layout above). Synchronous. */
+int rflbm_get_populations(rflbm_t* h, double* f, int on_device);
+int rflbm_get_populations_f32(rflbm_t* h, float* f, int on_device);
+
+/* Replaces the state by f (27*N doubles / floats) without changing t. */
+int rflbm_set_populations(rflbm_t* h, const double* f, int on_device);
+int rflbm_set_populations_f32(rflbm_t* h, const float* f, int on_device);
+
+/* Populations of selected sites: sites (n indices in [0, N), host memory) -> f (27*n
+ * doubles in host memory, element [i*n + j] for site sites[j]). Synchronous. */
+int rflbm_get_sites(rflbm_t* h, const int64_t* sites, int64_t n, double* f);
+
+/* Checkpoint / resume. rflbm_state_bytes: size of the raw storage image of the state
+ * (the float32 shifted populations in the library's internal layout). rflbm_save_state
+ * copies that image out, rflbm_load_state replaces the state by an image saved from a
+ * handle of the same box; with rflbm_set_step and the same seed the run continues
+ * bit-identically to an uninterrupted one (the noise is keyed by the step). */
+int64_t rflbm_state_bytes(const rflbm_t* h);
+int rflbm_save_state(rflbm_t* h, void* image, int on_device);
+int rflbm_load_state(rflbm_t* h, const void* image, int on_device);
+
+/* Step counter: read, and set (checkpoint/resume: with the populations and the seed it
+ * reproduces the noise of an uninterrupted run exactly). */
+int64_t rflbm_get_step(const rflbm_t* h);
+int rflbm_set_step(rflbm_t* h, int64_t step);
+
+/* Changes the stream of all later work (cudaStream_t, NULL = legacy default stream). */
+int rflbm_set_stream(rflbm_t* h, void* stream);
+
+/* Waits for all work enqueued on the handle's stream; reports asynchronous errors. */
+int rflbm_synchronize(rflbm_t* h);
+
+/* Box edges and number of kernel launches one rflbm_step(h, 1) makes. */
+int rflbm_get_dims(const rflbm_t* h, int* nx, int* ny, int* nz);
+int rflbm_launches_per_step(const rflbm_t* h);
+
+/* Test entry points of the noise source (Eq. 9 r_k; the generator is the reading
+ * stated above). Host buffers; computed on the current device.
+ * rflbm_philox4x32_10: out[4*j + w] = word w of Philox4x32-10(ctr[4*j .. 4*j+3],
+ *   key = (k0, k1)) for j < n.
+ * rflbm_site_normals: out[24*j + m] = normal n[m] of site sites[j] at (seed, step,
+ *   replica), exactly as the step kernel draws it (float32). */
+int rflbm_philox4x32_10(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
+                        int64_t n);
+int rflbm_site_normals(uint64_t seed, int64_t step, uint32_t replica,
+                       const uint32_t* sites, int64_t n, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RFLBM_H */

@@ -1,0 +1,82 @@
+// Counter-based noise source of the step kernel: Philox4x32-10 (Salmon, Moraes, Dror,
+// Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11) and Box-Muller (1958).
+// The paper's Eq. 9 needs standard normals r_k and names no generator; this is the
+// generator of the library's noise contract (rflbm.h).
+#pragma once
+
+#include <cstdint>
+
+namespace rflbm_dev {
+
+// Philox4x32 multipliers and Weyl key increments (Salmon et al., SC'11).
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+// Ten rounds of the Philox4x32 bijection on counter c under key (k0, k1).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return c;
+}
+
+// One Box-Muller pair from two uint32 draws, returned as radius and direction:
+// n0 = r * c, n1 = r * s with r = sqrt(-2 ln u0), (c, s) = (cos 2 pi u1, sin 2 pi u1),
+// u = (x + 1/2) 2^-32.
+//
+// -ln u0 is evaluated without cancellation: for x0 >= 2^31 it is -ln(1 - e) with
+// e = 1 - u0 = (~x0 + 1/2) 2^-32 formed exactly from the integer, by the series
+// e + e^2/2 + e^3/3 + e^4/4 + e^5/5 when e < 1/64 (truncation below 1e-10 relative) and
+// by log2 otherwise, so that radii near 0 keep their relative accuracy.
+// The angle is taken in (-pi, pi] where __sincosf is accurate: 2 pi u1 - pi, whose
+// cosine and sine are the negatives of those of 2 pi u1.
+__device__ __forceinline__ void box_muller(uint32_t x0, uint32_t x1, float& r, float& c,
+                                           float& s) {
+  const bool upper = (x0 >> 31) != 0u;
+  const uint32_t xm = upper ? ~x0 : x0;  // < 2^31
+  const float e = fmaf(__uint2float_rn(xm), 0x1p-32f, 0x1p-33f);  // (0, 1/2]
+  const float arg = upper ? 1.0f - e : e;
+  float nl = -0.69314718055994531f * __log2f(arg);  // -ln(arg)
+  if (upper && e < 0.015625f) {
+    nl = e * fmaf(e, fmaf(e, fmaf(e, fmaf(e, 0.2f, 0.25f), 0.33333333f), 0.5f), 1.0f);
+  }
+  r = sqrtf(2.0f * nl);
+  const float t = fmaf(__uint2float_rn(x1), 6.283185307179586f * 0x1p-32f,
+                       6.283185307179586f * 0x1p-33f - 3.14159265358979f);
+  float st, ct;
+  __sincosf(t, &st, &ct);
+  c = -ct;
+  s = -st;
+}
+
+// The 24 normals of one site at one step as 12 (radius, cos, sin) triples, pair m of
+// call j at index 2*j + m (normals n[4j + 2m] = r c, n[4j + 2m + 1] = r s).
+struct SiteNoise {
+  float r[12], c[12], s[12];
+};
+
+__device__ __forceinline__ void site_noise(uint32_t site, uint32_t step, uint32_t replica,
+                                           uint32_t k0, uint32_t k1, SiteNoise& out) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const uint4 w = philox4x32_10(make_uint4(site, step, (uint32_t)j, replica), k0, k1);
+    box_muller(w.x, w.y, out.r[2 * j], out.c[2 * j], out.s[2 * j]);
+    box_muller(w.z, w.w, out.r[2 * j + 1], out.c[2 * j + 1], out.s[2 * j + 1]);
+  }
+}
+
+// Normal n[m] (m = 0..23) of a SiteNoise, optionally scaled by a per-site factor.
+__device__ __forceinline__ float normal_at(const SiteNoise& n, int m, float scale = 1.0f) {
+  const int pair = m >> 1;
+  const float rr = n.r[pair] * scale;
+  return (m & 1) ? rr * n.s[pair] : rr * n.c[pair];
+}
+
+}  // namespace rflbm_dev

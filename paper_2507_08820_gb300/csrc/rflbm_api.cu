@@ -1,0 +1,541 @@
+// Host side of the C ABI declared in include/rflbm.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/rflbm.h"
+#include "rflbm_aux.h"
+
+using namespace rflbm_dev;
+
+struct rflbm {
+  rflbm_config_t cfg;
+  Geometry geo;
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  float* buf[2] = {nullptr, nullptr};
+  bool own_buf = false;
+  int cur = 0;            // buffer holding the current state
+  int64_t step = 0;
+  bool initialised = false;
+  StepVariant variant{};
+  CollideParams cp{};
+  double* partials = nullptr;  // stats scratch: kStatOutFields doubles per block + 8 out
+  int stat_blocks = 0;
+  void* staging = nullptr;     // device staging for host<->device transfers
+  size_t staging_bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? RFLBM_ENOMEM : RFLBM_ECUDA, "%s: %s (%s)", what,
+              cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define RFLBM_CUDA(call, what)                  \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+int64_t plane_stride(int64_t n) { return (n + 63) / 64 * 64; }
+
+int validate(const rflbm_config_t* c) {
+  if (!c) return fail(RFLBM_EINVAL, "config is NULL");
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1)
+    return fail(RFLBM_EINVAL, "box edges must be >= 1 (got %d x %d x %d)", c->nx, c->ny, c->nz);
+  const int64_t n = (int64_t)c->nx * c->ny * c->nz;
+  if (n >= (int64_t(1) << 31)) return fail(RFLBM_EINVAL, "box of %lld sites exceeds 2^31 - 1", (long long)n);
+  if (!(c->tau > 0.5) || !std::isfinite(c->tau))
+    return fail(RFLBM_EINVAL, "tau must be a finite value > 1/2 (got %g)", c->tau);
+  if (!(c->kT >= 0.0) || !std::isfinite(c->kT)) return fail(RFLBM_EINVAL, "kT must be >= 0 (got %g)", c->kT);
+  if (!(c->rho0 > 0.0) || !std::isfinite(c->rho0)) return fail(RFLBM_EINVAL, "rho0 must be > 0 (got %g)", c->rho0);
+  if (!(c->omega_g > 0.0 && c->omega_g < 2.0))
+    return fail(RFLBM_EINVAL, "omega_g must lie in (0, 2) (got %g)", c->omega_g);
+  if (c->model != RFLBM_MODEL_REG && c->model != RFLBM_MODEL_BGK)
+    return fail(RFLBM_EINVAL, "unknown model %d", c->model);
+  if (c->storage != RFLBM_STORE_F32) return fail(RFLBM_EINVAL, "unknown storage %d", c->storage);
+  if (c->phi_rho != RFLBM_PHI_LOCAL_RHO && c->phi_rho != RFLBM_PHI_RHO0)
+    return fail(RFLBM_EINVAL, "unknown phi_rho option %d", c->phi_rho);
+  return RFLBM_OK;
+}
+
+void fill_collide_params(rflbm* h) {
+  const rflbm_config_t& c = h->cfg;
+  const double om = 1.0 / c.tau, og = c.omega_g;
+  CollideParams& cp = h->cp;
+  cp.rho0 = (float)c.rho0;
+  cp.omega = (float)om;
+  cp.neq_diag = (float)((1.0 - om) / bnorm(2, 0, 0));
+  cp.neq_off = (float)((1.0 - om) / bnorm(1, 1, 0));
+  cp.ghost_keep = (float)(1.0 - og);
+  cp.sqrt_rho0 = (float)std::sqrt(c.rho0);
+  const double cs2 = 1.0 / 3.0;
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q)
+      for (int r = 0; r < 3; ++r) {
+        if (p + q + r < 2) continue;
+        const int k = mode_of(p, q, r);
+        // the BGK model relaxes every mode at omega (Eq. 12); Reg splits hydro/ghost
+        const double ok = (c.model == RFLBM_MODEL_BGK || k < 10) ? om : og;
+        cp.amp[k - 4] = (float)std::sqrt(c.kT * ok * (2.0 - ok) / (cs2 * bnorm(p, q, r)));
+      }
+  h->variant.model = c.model == RFLBM_MODEL_BGK ? kModelBgk : kModelReg;
+  h->variant.noise = c.kT > 0.0;
+  h->variant.ghost_neq = (c.model == RFLBM_MODEL_REG) && (og != 1.0);
+  h->variant.phi_rho0 = c.phi_rho == RFLBM_PHI_RHO0;
+}
+
+int ensure_staging(rflbm* h, size_t bytes) {
+  if (h->staging_bytes >= bytes) return RFLBM_OK;
+  if (h->staging) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->staging);
+    h->staging = nullptr;
+    h->staging_bytes = 0;
+  }
+  RFLBM_CUDA(cudaMalloc(&h->staging, bytes), "allocating the staging buffer");
+  h->staging_bytes = bytes;
+  return RFLBM_OK;
+}
+
+int check_handle(const rflbm* h) {
+  if (!h) return fail(RFLBM_EINVAL, "handle is NULL");
+  return RFLBM_OK;
+}
+
+int check_ready(const rflbm* h) {
+  if (int e = check_handle(h)) return e;
+  if (!h->initialised) return fail(RFLBM_ESTATE, "state not initialised (call rflbm_init_rest, rflbm_init_field or rflbm_set_populations)");
+  return RFLBM_OK;
+}
+
+int sync(rflbm* h, const char* what) {
+  RFLBM_CUDA(cudaStreamSynchronize(h->stream), what);
+  return RFLBM_OK;
+}
+
+int64_t n_sites(const rflbm* h) { return (int64_t)h->geo.n; }
+
+}  // namespace
+
+extern "C" {
+
+void rflbm_config_default(rflbm_config_t* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->nx = cfg->ny = cfg->nz = 32;
+  cfg->tau = 0.8;
+  cfg->kT = 0.0;
+  cfg->rho0 = 1.0;
+  cfg->seed = 1;
+  cfg->omega_g = 1.0;
+  cfg->model = RFLBM_MODEL_REG;
+  cfg->storage = RFLBM_STORE_F32;
+  cfg->phi_rho = RFLBM_PHI_LOCAL_RHO;
+  cfg->replica = 0;
+  cfg->stream = nullptr;
+  cfg->buffers[0] = cfg->buffers[1] = nullptr;
+  cfg->device = -1;
+}
+
+int64_t rflbm_buffer_bytes(const rflbm_config_t* cfg) {
+  if (int e = validate(cfg)) return e;
+  const int64_t n = (int64_t)cfg->nx * cfg->ny * cfg->nz;
+  return plane_stride(n) * kQ * (int64_t)sizeof(float);
+}
+
+const char* rflbm_last_error(void) { return g_error.c_str(); }
+
+rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
+  if (validate(cfg) != RFLBM_OK) return nullptr;
+  int dev = cfg->device;
+  if (dev < 0) {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+      cuda_fail(e, "querying the current device");
+      return nullptr;
+    }
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || dev >= ndev) {
+    if (e != cudaSuccess) cuda_fail(e, "querying CUDA devices");
+    else fail(RFLBM_EINVAL, "device %d does not exist (%d devices)", dev, ndev);
+    return nullptr;
+  }
+  DeviceGuard guard(dev);
+  rflbm* h = new (std::nothrow) rflbm();
+  if (!h) {
+    fail(RFLBM_ENOMEM, "allocating the handle");
+    return nullptr;
+  }
+  h->cfg = *cfg;
+  h->device = dev;
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  h->stream = (cudaStream_t)cfg->stream;
+  const int64_t n = (int64_t)cfg->nx * cfg->ny * cfg->nz;
+  Geometry& g = h->geo;
+  g.nx = cfg->nx; g.ny = cfg->ny; g.nz = cfg->nz;
+  g.nxy = (uint32_t)cfg->nx * (uint32_t)cfg->ny;
+  g.n = (uint32_t)n;
+  g.ps = plane_stride(n);
+  g.div_nx = make_fastdiv(g.nx);
+  g.div_nxy = make_fastdiv(g.nxy);
+  fill_collide_params(h);
+
+  const size_t bytes = (size_t)g.ps * kQ * sizeof(float);
+  if (cfg->buffers[0] || cfg->buffers[1]) {
+    if (!cfg->buffers[0] || !cfg->buffers[1] ||
+        ((uintptr_t)cfg->buffers[0] % 256) || ((uintptr_t)cfg->buffers[1] % 256)) {
+      fail(RFLBM_EINVAL, "caller buffers must both be given and 256-byte aligned");
+      delete h;
+      return nullptr;
+    }
+    h->buf[0] = (float*)cfg->buffers[0];
+    h->buf[1] = (float*)cfg->buffers[1];
+    h->own_buf = false;
+  } else {
+    h->own_buf = true;
+    for (int b = 0; b < 2; ++b) {
+      e = cudaMalloc((void**)&h->buf[b], bytes);
+      if (e != cudaSuccess) {
+        cuda_fail(e, "allocating a population buffer");
+        rflbm_destroy(h);
+        return nullptr;
+      }
+    }
+  }
+  h->stat_blocks = stats_partial_blocks(g, h->num_sms > 0 ? h->num_sms : 1);
+  e = cudaMalloc((void**)&h->partials,
+                 sizeof(double) * ((size_t)h->stat_blocks * kStatOutFields + 8));
+  if (e != cudaSuccess) {
+    cuda_fail(e, "allocating the reduction scratch");
+    rflbm_destroy(h);
+    return nullptr;
+  }
+  return h;
+}
+
+rflbm_t* rflbm_create(int nx, int ny, int nz, double tau, double kT, double rho0, uint64_t seed) {
+  rflbm_config_t c;
+  rflbm_config_default(&c);
+  c.nx = nx; c.ny = ny; c.nz = nz;
+  c.tau = tau; c.kT = kT; c.rho0 = rho0; c.seed = seed;
+  return rflbm_create_ex(&c);
+}
+
+void rflbm_destroy(rflbm_t* h) {
+  if (!h) return;
+  DeviceGuard guard(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->own_buf) {
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+  }
+  cudaFree(h->partials);
+  cudaFree(h->staging);
+  delete h;
+}
+
+int rflbm_init_rest(rflbm_t* h) {
+  if (int e = check_handle(h)) return e;
+  DeviceGuard guard(h->device);
+  // the shifted rest state is all zeros
+  RFLBM_CUDA(cudaMemsetAsync(h->buf[0], 0, (size_t)h->geo.ps * kQ * sizeof(float), h->stream),
+             "clearing the populations");
+  h->cur = 0;
+  h->step = 0;
+  h->initialised = true;
+  return RFLBM_OK;
+}
+
+int rflbm_init_field(rflbm_t* h, const double* rho, const double* u, int on_device) {
+  if (int e = check_handle(h)) return e;
+  DeviceGuard guard(h->device);
+  const int64_t n = n_sites(h);
+  const double* drho = rho;
+  const double* du = u;
+  if (!on_device && (rho || u)) {
+    if (int e = ensure_staging(h, sizeof(double) * 4 * n)) return e;
+    double* st = (double*)h->staging;
+    if (rho) {
+      RFLBM_CUDA(cudaMemcpyAsync(st, rho, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream), "copying rho");
+      drho = st;
+    }
+    if (u) {
+      RFLBM_CUDA(cudaMemcpyAsync(st + n, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream), "copying u");
+      du = st + n;
+    }
+  }
+  RFLBM_CUDA(launch_init_field(h->geo, h->cp.rho0, drho, du, h->buf[0], h->stream), "launching init_field");
+  h->cur = 0;
+  h->step = 0;
+  h->initialised = true;
+  if (!on_device) return sync(h, "rflbm_init_field");
+  return RFLBM_OK;
+}
+
+int rflbm_step(rflbm_t* h, int64_t n) {
+  if (int e = check_ready(h)) return e;
+  if (n < 0) return fail(RFLBM_EINVAL, "negative step count %lld", (long long)n);
+  DeviceGuard guard(h->device);
+  StepParams p;
+  p.geo = h->geo;
+  p.cp = h->cp;
+  p.key0 = (uint32_t)(h->cfg.seed & 0xffffffffu);
+  p.key1 = (uint32_t)(h->cfg.seed >> 32);
+  p.replica = h->cfg.replica;
+  for (int64_t t = 0; t < n; ++t) {
+    p.src = h->buf[h->cur];
+    p.dst = h->buf[1 - h->cur];
+    p.step = (uint32_t)h->step;
+    cudaError_t e = launch_step_f32(p, h->variant, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the step kernel");
+    h->cur = 1 - h->cur;
+    ++h->step;
+  }
+  return RFLBM_OK;
+}
+
+int rflbm_moments(rflbm_t* h, double* rho, double* u, double* pi, int on_device) {
+  if (int e = check_ready(h)) return e;
+  DeviceGuard guard(h->device);
+  const int64_t n = n_sites(h);
+  double *drho = rho, *du = u, *dpi = pi;
+  if (!on_device) {
+    if (int e = ensure_staging(h, sizeof(double) * 10 * n)) return e;
+    double* st = (double*)h->staging;
+    drho = rho ? st : nullptr;
+    du = u ? st + n : nullptr;
+    dpi = pi ? st + 4 * n : nullptr;
+  }
+  RFLBM_CUDA(launch_moments(h->geo, h->cp.rho0, h->buf[h->cur], drho, du, dpi, h->stream), "launching moments");
+  if (!on_device) {
+    if (rho) RFLBM_CUDA(cudaMemcpyAsync(rho, drho, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream), "copying rho");
+    if (u) RFLBM_CUDA(cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream), "copying u");
+    if (pi) RFLBM_CUDA(cudaMemcpyAsync(pi, dpi, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, h->stream), "copying pi");
+  }
+  return sync(h, "rflbm_moments");
+}
+
+int rflbm_stats(rflbm_t* h, rflbm_stats_t* out) {
+  if (int e = check_ready(h)) return e;
+  if (!out) return fail(RFLBM_EINVAL, "stats output is NULL");
+  DeviceGuard guard(h->device);
+  double* res = h->partials + (size_t)h->stat_blocks * kStatOutFields;
+  RFLBM_CUDA(launch_stats(h->geo, h->cp.rho0, h->buf[h->cur], h->partials, h->stat_blocks, res, h->stream),
+             "launching stats");
+  double host[kStatOutFields];
+  RFLBM_CUDA(cudaMemcpyAsync(host, res, sizeof(host), cudaMemcpyDeviceToHost, h->stream), "copying stats");
+  if (int e = sync(h, "rflbm_stats")) return e;
+  out->step = h->step;
+  out->mass = (double)n_sites(h) * h->cfg.rho0 + host[0];
+  out->momentum[0] = host[1];
+  out->momentum[1] = host[2];
+  out->momentum[2] = host[3];
+  out->max_speed = host[4];
+  out->nonfinite = (int64_t)host[5];
+  if (out->nonfinite > 0)
+    return fail(RFLBM_EUNSTABLE, "%lld sites hold non-finite values at step %lld",
+                (long long)out->nonfinite, (long long)h->step);
+  return RFLBM_OK;
+}
+
+static int get_pops(rflbm_t* h, void* f, int on_device, bool f64) {
+  if (int e = check_ready(h)) return e;
+  if (!f) return fail(RFLBM_EINVAL, "output is NULL");
+  DeviceGuard guard(h->device);
+  const int64_t n = n_sites(h);
+  const size_t bytes = (size_t)kQ * n * (f64 ? sizeof(double) : sizeof(float));
+  void* dst = f;
+  if (!on_device) {
+    if (int e = ensure_staging(h, bytes)) return e;
+    dst = h->staging;
+  }
+  cudaError_t e = f64 ? launch_get_populations_f64(h->geo, h->cp.rho0, h->buf[h->cur], (double*)dst, h->stream)
+                      : launch_get_populations_f32(h->geo, h->cp.rho0, h->buf[h->cur], (float*)dst, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launching get_populations");
+  if (!on_device) RFLBM_CUDA(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, h->stream), "copying populations");
+  return sync(h, "rflbm_get_populations");
+}
+
+static int set_pops(rflbm_t* h, const void* f, int on_device, bool f64) {
+  if (int e = check_handle(h)) return e;
+  if (!f) return fail(RFLBM_EINVAL, "input is NULL");
+  DeviceGuard guard(h->device);
+  const int64_t n = n_sites(h);
+  const size_t bytes = (size_t)kQ * n * (f64 ? sizeof(double) : sizeof(float));
+  const void* src = f;
+  if (!on_device) {
+    if (int e = ensure_staging(h, bytes)) return e;
+    RFLBM_CUDA(cudaMemcpyAsync(h->staging, f, bytes, cudaMemcpyHostToDevice, h->stream), "copying populations");
+    src = h->staging;
+  }
+  // the state after this call is step h->step, held in buffer 0
+  cudaError_t e = f64 ? launch_set_populations_f64(h->geo, h->cp.rho0, (const double*)src, h->buf[0], h->stream)
+                      : launch_set_populations_f32(h->geo, h->cp.rho0, (const float*)src, h->buf[0], h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launching set_populations");
+  h->cur = 0;
+  h->initialised = true;
+  if (!on_device) return sync(h, "rflbm_set_populations");
+  return RFLBM_OK;
+}
+
+int rflbm_get_populations(rflbm_t* h, double* f, int on_device) { return get_pops(h, f, on_device, true); }
+int rflbm_get_populations_f32(rflbm_t* h, float* f, int on_device) { return get_pops(h, f, on_device, false); }
+int rflbm_set_populations(rflbm_t* h, const double* f, int on_device) { return set_pops(h, f, on_device, true); }
+int rflbm_set_populations_f32(rflbm_t* h, const float* f, int on_device) { return set_pops(h, f, on_device, false); }
+
+int rflbm_get_sites(rflbm_t* h, const int64_t* sites, int64_t n, double* f) {
+  if (int e = check_ready(h)) return e;
+  if (n < 0 || (n > 0 && (!sites || !f))) return fail(RFLBM_EINVAL, "invalid site list");
+  if (n == 0) return RFLBM_OK;
+  for (int64_t j = 0; j < n; ++j)
+    if (sites[j] < 0 || sites[j] >= n_sites(h))
+      return fail(RFLBM_EINVAL, "site index %lld out of range [0, %lld)", (long long)sites[j], (long long)n_sites(h));
+  DeviceGuard guard(h->device);
+  const size_t bytes_sites = sizeof(int64_t) * n, bytes_out = sizeof(double) * kQ * n;
+  if (int e = ensure_staging(h, bytes_sites + bytes_out)) return e;
+  int64_t* dsites = (int64_t*)h->staging;
+  double* dout = (double*)((char*)h->staging + bytes_sites);
+  RFLBM_CUDA(cudaMemcpyAsync(dsites, sites, bytes_sites, cudaMemcpyHostToDevice, h->stream), "copying sites");
+  RFLBM_CUDA(launch_get_sites(h->geo, h->cp.rho0, h->buf[h->cur], dsites, n, dout, h->stream), "launching get_sites");
+  RFLBM_CUDA(cudaMemcpyAsync(f, dout, bytes_out, cudaMemcpyDeviceToHost, h->stream), "copying site populations");
+  return sync(h, "rflbm_get_sites");
+}
+
+int64_t rflbm_state_bytes(const rflbm_t* h) {
+  if (int e = check_handle(h)) return e;
+  return h->geo.ps * kQ * (int64_t)sizeof(float);
+}
+
+int rflbm_save_state(rflbm_t* h, void* image, int on_device) {
+  if (int e = check_ready(h)) return e;
+  if (!image) return fail(RFLBM_EINVAL, "image is NULL");
+  DeviceGuard guard(h->device);
+  RFLBM_CUDA(cudaMemcpyAsync(image, h->buf[h->cur], (size_t)rflbm_state_bytes(h),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
+             "copying the state image");
+  return sync(h, "rflbm_save_state");
+}
+
+int rflbm_load_state(rflbm_t* h, const void* image, int on_device) {
+  if (int e = check_handle(h)) return e;
+  if (!image) return fail(RFLBM_EINVAL, "image is NULL");
+  DeviceGuard guard(h->device);
+  RFLBM_CUDA(cudaMemcpyAsync(h->buf[0], image, (size_t)rflbm_state_bytes(h),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream),
+             "copying the state image");
+  h->cur = 0;
+  h->initialised = true;
+  return sync(h, "rflbm_load_state");
+}
+
+int64_t rflbm_get_step(const rflbm_t* h) {
+  if (check_handle(h)) return RFLBM_EINVAL;
+  return h->step;
+}
+
+int rflbm_set_step(rflbm_t* h, int64_t step) {
+  if (int e = check_handle(h)) return e;
+  if (step < 0) return fail(RFLBM_EINVAL, "negative step %lld", (long long)step);
+  h->step = step;
+  return RFLBM_OK;
+}
+
+int rflbm_set_stream(rflbm_t* h, void* stream) {
+  if (int e = check_handle(h)) return e;
+  h->stream = (cudaStream_t)stream;
+  h->cfg.stream = stream;
+  return RFLBM_OK;
+}
+
+int rflbm_synchronize(rflbm_t* h) {
+  if (int e = check_handle(h)) return e;
+  DeviceGuard guard(h->device);
+  return sync(h, "rflbm_synchronize");
+}
+
+int rflbm_get_dims(const rflbm_t* h, int* nx, int* ny, int* nz) {
+  if (int e = check_handle(h)) return e;
+  if (nx) *nx = h->cfg.nx;
+  if (ny) *ny = h->cfg.ny;
+  if (nz) *nz = h->cfg.nz;
+  return RFLBM_OK;
+}
+
+int rflbm_launches_per_step(const rflbm_t* h) {
+  if (int e = check_handle(h)) return e;
+  return 1;
+}
+
+int rflbm_philox4x32_10(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, int64_t n) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) return fail(RFLBM_EINVAL, "invalid arguments");
+  if (n == 0) return RFLBM_OK;
+  uint32_t *dctr = nullptr, *dout = nullptr;
+  const size_t bytes = sizeof(uint32_t) * 4 * n;
+  RFLBM_CUDA(cudaMalloc(&dctr, bytes), "allocating counters");
+  cudaError_t e = cudaMalloc(&dout, bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(dctr, ctr, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_philox(dctr, k0, k1, dout, n, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(dctr);
+  cudaFree(dout);
+  if (e != cudaSuccess) return cuda_fail(e, "rflbm_philox4x32_10");
+  return RFLBM_OK;
+}
+
+int rflbm_site_normals(uint64_t seed, int64_t step, uint32_t replica, const uint32_t* sites,
+                       int64_t n, float* out) {
+  if (n < 0 || (n > 0 && (!sites || !out)) || step < 0) return fail(RFLBM_EINVAL, "invalid arguments");
+  if (n == 0) return RFLBM_OK;
+  uint32_t* ds = nullptr;
+  float* dout = nullptr;
+  RFLBM_CUDA(cudaMalloc(&ds, sizeof(uint32_t) * n), "allocating sites");
+  cudaError_t e = cudaMalloc(&dout, sizeof(float) * 24 * n);
+  if (e == cudaSuccess) e = cudaMemcpy(ds, sites, sizeof(uint32_t) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = launch_site_normals((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), (uint32_t)step,
+                            replica, ds, n, dout, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(float) * 24 * n, cudaMemcpyDeviceToHost);
+  cudaFree(ds);
+  cudaFree(dout);
+  if (e != cudaSuccess) return cuda_fail(e, "rflbm_site_normals");
+  return RFLBM_OK;
+}
+
+}  // extern "C"

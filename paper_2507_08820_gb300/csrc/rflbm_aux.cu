@@ -1,0 +1,253 @@
+// Kernels around the step: initial states, population import/export in the pull layout,
+// FP64 moments and global diagnostics, and the noise-source test kernels.
+#include "rflbm_aux.h"
+
+namespace rflbm_dev {
+
+constexpr int kAuxBlock = 256;
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ uint32_t site_of(int64_t t) { return (uint32_t)t; }
+
+// One 1-D factor of the product-form equilibrium (Eq. 26 factorised over the axes):
+// Psi(0, u) = 2/3 - u^2, Psi(+-1, u) = (1/3 +- u + u^2)/2.
+__device__ __forceinline__ double psi(int c, double u) {
+  return c == 0 ? (2.0 / 3.0 - u * u) : 0.5 * (1.0 / 3.0 + c * u + u * u);
+}
+
+// ---------------------------------------------------------------- initial states
+__global__ void k_init_field(Geometry g, float rho0, const double* __restrict__ rho,
+                             const double* __restrict__ u, float* __restrict__ dst) {
+  const int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+  if (s >= g.n) return;
+  const double r = rho ? rho[s] : (double)rho0;
+  const double ux = u ? u[s] : 0.0, uy = u ? u[g.n + s] : 0.0, uz = u ? u[2 * (int64_t)g.n + s] : 0.0;
+  // scatter f_i(x) to plane i at x - c_i
+  const Neighbours nb = neighbours(site_of(s), g);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const double f = r * psi(cx_of(i), ux) * psi(cy_of(i), uy) * psi(cz_of(i), uz);
+    dst[i * g.ps + pull_site(nb, i)] = (float)(f - weight_of(i) * (double)rho0);
+  }
+}
+
+template <class T>
+__global__ void k_set_populations(Geometry g, float rho0, const T* __restrict__ f,
+                                  float* __restrict__ dst) {
+  const int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+  if (s >= g.n) return;
+  const Neighbours nb = neighbours(site_of(s), g);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const double v = (double)f[i * (int64_t)g.n + s] - weight_of(i) * (double)rho0;
+    dst[i * g.ps + pull_site(nb, i)] = (float)v;
+  }
+}
+
+template <class T>
+__global__ void k_get_populations(Geometry g, float rho0, const float* __restrict__ src,
+                                  T* __restrict__ f) {
+  const int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+  if (s >= g.n) return;
+  const Neighbours nb = neighbours(site_of(s), g);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    f[i * (int64_t)g.n + s] = (T)((double)src[i * g.ps + pull_site(nb, i)] + weight_of(i) * (double)rho0);
+  }
+}
+
+__global__ void k_get_sites(Geometry g, float rho0, const float* __restrict__ src,
+                            const int64_t* __restrict__ sites, int64_t n,
+                            double* __restrict__ f) {
+  const int64_t j = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+  if (j >= n) return;
+  const Neighbours nb = neighbours(site_of(sites[j]), g);
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    f[i * n + j] = (double)src[i * g.ps + pull_site(nb, i)] + weight_of(i) * (double)rho0;
+  }
+}
+
+// Raw moments of order <= 2 of the shifted populations of one site, in FP64.
+struct SiteMoments {
+  double drho, j[3], s[6];  // s: sum g c_a c_b for xx, yy, zz, xy, xz, yz
+};
+
+__device__ __forceinline__ SiteMoments site_moments(const Neighbours& nb, const float* src,
+                                                    int64_t ps) {
+  SiteMoments m = {};
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const double v = (double)src[i * ps + pull_site(nb, i)];
+    const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+    m.drho += v;
+    m.j[0] += cx * v; m.j[1] += cy * v; m.j[2] += cz * v;
+    m.s[0] += cx * cx * v; m.s[1] += cy * cy * v; m.s[2] += cz * cz * v;
+    m.s[3] += cx * cy * v; m.s[4] += cx * cz * v; m.s[5] += cy * cz * v;
+  }
+  return m;
+}
+
+__global__ void k_moments(Geometry g, float rho0, const float* __restrict__ src,
+                          double* __restrict__ rho, double* __restrict__ u,
+                          double* __restrict__ pi) {
+  const int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+  if (s >= g.n) return;
+  const SiteMoments m = site_moments(neighbours(site_of(s), g), src, g.ps);
+  const double r = (double)rho0 + m.drho;
+  if (rho) rho[s] = r;
+  if (u) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a * (int64_t)g.n + s] = m.j[a] / r;
+  }
+  if (pi) {
+    // Pi_ab = sum_i f_i (c_a c_b - delta_ab/3) = sum_i g_i c_a c_b - delta_ab drho/3
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+      pi[a * (int64_t)g.n + s] = m.s[a] - (a < 3 ? m.drho / 3.0 : 0.0);
+  }
+}
+
+// Per-block partial sums: drho, j (3), max |u|, count of non-finite sites.
+constexpr int kStatFields = 6;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void k_stats_partial(Geometry g, float rho0, const float* __restrict__ src,
+                                double* __restrict__ partials) {
+  double acc[kStatFields] = {0, 0, 0, 0, 0, 0};
+  for (int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x; s < g.n;
+       s += (int64_t)gridDim.x * kAuxBlock) {
+    const SiteMoments m = site_moments(neighbours(site_of(s), g), src, g.ps);
+    const double r = (double)rho0 + m.drho;
+    const bool finite = isfinite(m.drho) && isfinite(m.j[0]) && isfinite(m.j[1]) &&
+                        isfinite(m.j[2]);
+    if (finite) {
+      acc[0] += m.drho;
+      acc[1] += m.j[0]; acc[2] += m.j[1]; acc[3] += m.j[2];
+      const double sp = sqrt(m.j[0] * m.j[0] + m.j[1] * m.j[1] + m.j[2] * m.j[2]) / fabs(r);
+      acc[4] = fmax(acc[4], sp);
+    } else {
+      acc[5] += 1.0;
+    }
+  }
+  __shared__ double sh[kAuxBlock / 32][kStatFields];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < kStatFields; ++f) {
+    const double v = (f == 4) ? warp_max(acc[f]) : warp_sum(acc[f]);
+    if (lane == 0) sh[wid][f] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kStatFields) {
+    const int f = threadIdx.x;
+    double v = sh[0][f];
+    for (int w = 1; w < kAuxBlock / 32; ++w) v = (f == 4) ? fmax(v, sh[w][f]) : v + sh[w][f];
+    partials[(int64_t)blockIdx.x * kStatFields + f] = v;
+  }
+}
+
+// Fixed-order final reduction of the partials (deterministic for a fixed grid).
+__global__ void k_stats_final(const double* __restrict__ partials, int nblocks,
+                              double* __restrict__ out) {
+  if (threadIdx.x < kStatFields) {
+    const int f = threadIdx.x;
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+      const double p = partials[(int64_t)b * kStatFields + f];
+      v = (f == 4) ? fmax(v, p) : v + p;
+    }
+    out[f] = v;
+  }
+}
+
+// ---------------------------------------------------------------- noise tests
+__global__ void k_philox(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                         uint32_t* __restrict__ out, int64_t n) {
+  const int64_t j = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+  if (j >= n) return;
+  const uint4 w = philox4x32_10(make_uint4(ctr[4 * j], ctr[4 * j + 1], ctr[4 * j + 2], ctr[4 * j + 3]), k0, k1);
+  out[4 * j] = w.x; out[4 * j + 1] = w.y; out[4 * j + 2] = w.z; out[4 * j + 3] = w.w;
+}
+
+__global__ void k_site_normals(uint32_t k0, uint32_t k1, uint32_t step, uint32_t replica,
+                               const uint32_t* __restrict__ sites, int64_t n,
+                               float* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+  if (j >= n) return;
+  SiteNoise nz;
+  site_noise(sites[j], step, replica, k0, k1, nz);
+#pragma unroll
+  for (int m = 0; m < 24; ++m) out[24 * j + m] = normal_at(nz, m);
+}
+
+// ---------------------------------------------------------------- launchers
+static unsigned blocks_for(int64_t n) { return (unsigned)((n + kAuxBlock - 1) / kAuxBlock); }
+
+cudaError_t launch_init_field(const Geometry& g, float rho0, const double* rho, const double* u,
+                              float* dst, cudaStream_t st) {
+  k_init_field<<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, rho, u, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_set_populations_f64(const Geometry& g, float rho0, const double* f, float* dst,
+                                       cudaStream_t st) {
+  k_set_populations<double><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, f, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_set_populations_f32(const Geometry& g, float rho0, const float* f, float* dst,
+                                       cudaStream_t st) {
+  k_set_populations<float><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, f, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_get_populations_f64(const Geometry& g, float rho0, const float* src, double* f,
+                                       cudaStream_t st) {
+  k_get_populations<double><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, src, f);
+  return cudaGetLastError();
+}
+cudaError_t launch_get_populations_f32(const Geometry& g, float rho0, const float* src, float* f,
+                                       cudaStream_t st) {
+  k_get_populations<float><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, src, f);
+  return cudaGetLastError();
+}
+cudaError_t launch_get_sites(const Geometry& g, float rho0, const float* src, const int64_t* sites,
+                             int64_t n, double* f, cudaStream_t st) {
+  k_get_sites<<<blocks_for(n), kAuxBlock, 0, st>>>(g, rho0, src, sites, n, f);
+  return cudaGetLastError();
+}
+cudaError_t launch_moments(const Geometry& g, float rho0, const float* src, double* rho,
+                           double* u, double* pi, cudaStream_t st) {
+  k_moments<<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, src, rho, u, pi);
+  return cudaGetLastError();
+}
+int stats_partial_blocks(const Geometry& g, int num_sms) {
+  const int64_t want = (g.n + kAuxBlock - 1) / kAuxBlock;
+  const int64_t cap = 4 * (int64_t)num_sms;
+  return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+cudaError_t launch_stats(const Geometry& g, float rho0, const float* src, double* partials,
+                         int nblocks, double* out6, cudaStream_t st) {
+  k_stats_partial<<<nblocks, kAuxBlock, 0, st>>>(g, rho0, src, partials);
+  k_stats_final<<<1, 32, 0, st>>>(partials, nblocks, out6);
+  return cudaGetLastError();
+}
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
+                          int64_t n, cudaStream_t st) {
+  k_philox<<<blocks_for(n), kAuxBlock, 0, st>>>(ctr, k0, k1, out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_site_normals(uint32_t k0, uint32_t k1, uint32_t step, uint32_t replica,
+                                const uint32_t* sites, int64_t n, float* out, cudaStream_t st) {
+  k_site_normals<<<blocks_for(n), kAuxBlock, 0, st>>>(k0, k1, step, replica, sites, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rflbm_dev

@@ -1,0 +1,87 @@
+// Internal declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "collide.cuh"
+
+namespace rflbm_dev {
+
+// Exact unsigned division n / d for n, d < 2^31 by one 32x32->64 multiply:
+// m = floor(2^(31+l) / d) + 1 with l = ceil(log2 d) gives n / d = (n * m) >> (31 + l).
+struct FastDiv {
+  uint32_t d;
+  uint32_t m;
+  uint32_t shift;  // 31 + l
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  const unsigned long long m = ((1ull << (31 + l)) / d) + 1ull;
+  return FastDiv{d, (uint32_t)m, 31u + l};
+}
+
+__device__ __forceinline__ uint32_t fastdiv(uint32_t n, const FastDiv& f) {
+  return (uint32_t)(((unsigned long long)n * f.m) >> f.shift);
+}
+
+// Geometry of a box in the pull layout: plane i of a population buffer holds, at site y,
+// the shifted value f_i(y + c_i, t) - w_i rho0 (the post-collision value of step t - 1
+// at y), so that the pre-collision tile of site x is gathered from x - c_i.
+struct Geometry {
+  uint32_t nx, ny, nz, nxy, n;
+  int64_t ps;  // plane stride in elements (n rounded up to 64)
+  FastDiv div_nx, div_nxy;
+};
+
+// Periodic neighbour coordinates of site s: X[a] is the x coordinate of x - (a - 1),
+// Y[b] and Z[c] the row and slab offsets of y - (b - 1), z - (c - 1).
+struct Neighbours {
+  uint32_t X[3], Y[3], Z[3];
+};
+
+__device__ __forceinline__ Neighbours neighbours(uint32_t s, const Geometry& g) {
+  const uint32_t z = fastdiv(s, g.div_nxy);
+  const uint32_t rem = s - z * g.nxy;
+  const uint32_t y = fastdiv(rem, g.div_nx);
+  const uint32_t x = rem - y * g.nx;
+  const uint32_t xm = (x == 0 ? g.nx : x) - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
+  const uint32_t ym = (y == 0 ? g.ny : y) - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
+  const uint32_t zm = (z == 0 ? g.nz : z) - 1, zp = (z + 1 == g.nz) ? 0 : z + 1;
+  Neighbours nb;
+  nb.X[0] = xp; nb.X[1] = x; nb.X[2] = xm;
+  nb.Y[0] = yp * g.nx; nb.Y[1] = y * g.nx; nb.Y[2] = ym * g.nx;
+  nb.Z[0] = zp * g.nxy; nb.Z[1] = z * g.nxy; nb.Z[2] = zm * g.nxy;
+  return nb;
+}
+
+// Site that population i of site x is pulled from: x - c_i.
+__device__ __forceinline__ uint32_t pull_site(const Neighbours& nb, int i) {
+  return nb.X[cx_of(i) + 1] + nb.Y[cy_of(i) + 1] + nb.Z[cz_of(i) + 1];
+}
+
+struct StepParams {
+  Geometry geo;
+  CollideParams cp;
+  const float* src;
+  float* dst;
+  uint32_t key0, key1, step, replica;
+};
+
+constexpr int kStepBlock = 256;
+
+// Variant flags of the step kernel.
+struct StepVariant {
+  int model;        // kModelReg / kModelBgk
+  bool noise;       // kT > 0
+  bool ghost_neq;   // omega_g != 1 (Reg only)
+  bool phi_rho0;    // Eq. 10 with rho0
+};
+
+// Launches one step of the fused pull kernel on `stream`.
+cudaError_t launch_step_f32(const StepParams& p, const StepVariant& v, cudaStream_t stream);
+
+}  // namespace rflbm_dev

@@ -1,0 +1,317 @@
+"""Thin ctypes binding of the C ABI in include/rflbm.h (argument marshalling only).
+
+Every function has the C name and forwards to librflbm.so; all work runs in the CUDA
+library. Arrays are numpy arrays (host memory, on_device = 0) or objects exposing
+`data_ptr()` (torch CUDA tensors, on_device = 1). A negative status raises RflbmError
+with the library's message. There is no fallback: if the library cannot be loaded the
+import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "librflbm.so")
+
+RFLBM_OK = 0
+RFLBM_EINVAL = -1
+RFLBM_ENOMEM = -2
+RFLBM_ECUDA = -3
+RFLBM_EUNSTABLE = -4
+RFLBM_ETIMEOUT = -5
+RFLBM_ESTATE = -6
+RFLBM_MODEL_REG = 0
+RFLBM_MODEL_BGK = 1
+RFLBM_STORE_F32 = 0
+RFLBM_PHI_LOCAL_RHO = 0
+RFLBM_PHI_RHO0 = 1
+
+
+class RflbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"rflbm error {status}: {message}")
+        self.status = status
+
+
+class rflbm_config_t(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("tau", C.c_double), ("kT", C.c_double), ("rho0", C.c_double),
+        ("seed", C.c_uint64), ("omega_g", C.c_double),
+        ("model", C.c_int), ("storage", C.c_int), ("phi_rho", C.c_int),
+        ("replica", C.c_uint32), ("stream", C.c_void_p),
+        ("buffers", C.c_void_p * 2), ("device", C.c_int),
+    ]
+
+
+class rflbm_stats_t(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64), ("mass", C.c_double), ("momentum", C.c_double * 3),
+        ("max_speed", C.c_double), ("nonfinite", C.c_int64),
+    ]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(
+            f"{_LIB_PATH} is missing: build it with `python -m paper_2507_08820_gb300.build`")
+    return C.CDLL(_LIB_PATH)
+
+
+lib = _load()
+_H = C.c_void_p
+_P = C.c_void_p
+_sig = {
+    "rflbm_config_default": (None, [C.POINTER(rflbm_config_t)]),
+    "rflbm_buffer_bytes": (C.c_int64, [C.POINTER(rflbm_config_t)]),
+    "rflbm_create": (_H, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_uint64]),
+    "rflbm_create_ex": (_H, [C.POINTER(rflbm_config_t)]),
+    "rflbm_destroy": (None, [_H]),
+    "rflbm_last_error": (C.c_char_p, []),
+    "rflbm_init_rest": (C.c_int, [_H]),
+    "rflbm_init_field": (C.c_int, [_H, _P, _P, C.c_int]),
+    "rflbm_step": (C.c_int, [_H, C.c_int64]),
+    "rflbm_moments": (C.c_int, [_H, _P, _P, _P, C.c_int]),
+    "rflbm_stats": (C.c_int, [_H, C.POINTER(rflbm_stats_t)]),
+    "rflbm_get_populations": (C.c_int, [_H, _P, C.c_int]),
+    "rflbm_get_populations_f32": (C.c_int, [_H, _P, C.c_int]),
+    "rflbm_set_populations": (C.c_int, [_H, _P, C.c_int]),
+    "rflbm_set_populations_f32": (C.c_int, [_H, _P, C.c_int]),
+    "rflbm_get_sites": (C.c_int, [_H, _P, C.c_int64, _P]),
+    "rflbm_state_bytes": (C.c_int64, [_H]),
+    "rflbm_save_state": (C.c_int, [_H, _P, C.c_int]),
+    "rflbm_load_state": (C.c_int, [_H, _P, C.c_int]),
+    "rflbm_get_step": (C.c_int64, [_H]),
+    "rflbm_set_step": (C.c_int, [_H, C.c_int64]),
+    "rflbm_set_stream": (C.c_int, [_H, _P]),
+    "rflbm_synchronize": (C.c_int, [_H]),
+    "rflbm_get_dims": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "rflbm_launches_per_step": (C.c_int, [_H]),
+    "rflbm_philox4x32_10": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, C.c_int64]),
+    "rflbm_site_normals": (C.c_int, [C.c_uint64, C.c_int64, C.c_uint32, _P, C.c_int64, _P]),
+}
+for _name, (_res, _args) in _sig.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+def _check(status):
+    if status < 0:
+        raise RflbmError(status, lib.rflbm_last_error().decode())
+    return status
+
+
+def _ptr(a, dtype=None):
+    """(pointer, on_device) of a numpy array or a CUDA tensor; None -> (None, 0)."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    if not isinstance(a, np.ndarray) or not a.flags.c_contiguous:
+        raise ValueError("expected a C-contiguous numpy array or a torch tensor")
+    if dtype is not None and a.dtype != dtype:
+        raise ValueError(f"expected dtype {np.dtype(dtype)}, got {a.dtype}")
+    return a.ctypes.data, 0
+
+
+def _same_side(*pairs):
+    sides = {d for p, d in pairs if p is not None}
+    if len(sides) > 1:
+        raise ValueError("all arrays of one call must be on the same side (host or device)")
+    return sides.pop() if sides else 0
+
+
+# ------------------------------------------------------------------ C ABI, same names
+def rflbm_config_default():
+    cfg = rflbm_config_t()
+    lib.rflbm_config_default(C.byref(cfg))
+    return cfg
+
+
+def rflbm_buffer_bytes(cfg):
+    return _check(lib.rflbm_buffer_bytes(C.byref(cfg)))
+
+
+def rflbm_create(nx, ny, nz, tau, kT, rho0, seed):
+    h = lib.rflbm_create(nx, ny, nz, tau, kT, rho0, seed)
+    if not h:
+        raise RflbmError(-1, lib.rflbm_last_error().decode())
+    return h
+
+
+def rflbm_create_ex(cfg):
+    h = lib.rflbm_create_ex(C.byref(cfg))
+    if not h:
+        raise RflbmError(-1, lib.rflbm_last_error().decode())
+    return h
+
+
+def rflbm_destroy(h):
+    lib.rflbm_destroy(h)
+
+
+def rflbm_last_error():
+    return lib.rflbm_last_error().decode()
+
+
+def rflbm_init_rest(h):
+    return _check(lib.rflbm_init_rest(h))
+
+
+def rflbm_init_field(h, rho=None, u=None):
+    pr, pu = _ptr(rho, np.float64), _ptr(u, np.float64)
+    return _check(lib.rflbm_init_field(h, pr[0], pu[0], _same_side(pr, pu)))
+
+
+def rflbm_step(h, n=1):
+    return _check(lib.rflbm_step(h, int(n)))
+
+
+def rflbm_moments(h, rho=None, u=None, pi=None):
+    ps = [_ptr(a, np.float64) for a in (rho, u, pi)]
+    return _check(lib.rflbm_moments(h, ps[0][0], ps[1][0], ps[2][0], _same_side(*ps)))
+
+
+def rflbm_stats(h):
+    st = rflbm_stats_t()
+    status = lib.rflbm_stats(h, C.byref(st))
+    if status < 0 and status != RFLBM_EUNSTABLE:
+        _check(status)
+    return st, status
+
+
+def rflbm_get_populations(h, f):
+    p, d = _ptr(f, np.float64)
+    return _check(lib.rflbm_get_populations(h, p, d))
+
+
+def rflbm_get_populations_f32(h, f):
+    p, d = _ptr(f, np.float32)
+    return _check(lib.rflbm_get_populations_f32(h, p, d))
+
+
+def rflbm_set_populations(h, f):
+    p, d = _ptr(f, np.float64)
+    return _check(lib.rflbm_set_populations(h, p, d))
+
+
+def rflbm_set_populations_f32(h, f):
+    p, d = _ptr(f, np.float32)
+    return _check(lib.rflbm_set_populations_f32(h, p, d))
+
+
+def rflbm_get_sites(h, sites, out):
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    p, _ = _ptr(out, np.float64)
+    return _check(lib.rflbm_get_sites(h, sites.ctypes.data, sites.size, p))
+
+
+def rflbm_state_bytes(h):
+    return _check(lib.rflbm_state_bytes(h))
+
+
+def rflbm_save_state(h, image):
+    p, d = _ptr(image)
+    return _check(lib.rflbm_save_state(h, p, d))
+
+
+def rflbm_load_state(h, image):
+    p, d = _ptr(image)
+    return _check(lib.rflbm_load_state(h, p, d))
+
+
+def rflbm_get_step(h):
+    return _check(lib.rflbm_get_step(h))
+
+
+def rflbm_set_step(h, step):
+    return _check(lib.rflbm_set_step(h, int(step)))
+
+
+def rflbm_set_stream(h, stream):
+    return _check(lib.rflbm_set_stream(h, stream))
+
+
+def rflbm_synchronize(h):
+    return _check(lib.rflbm_synchronize(h))
+
+
+def rflbm_get_dims(h):
+    nx, ny, nz = C.c_int(), C.c_int(), C.c_int()
+    _check(lib.rflbm_get_dims(h, C.byref(nx), C.byref(ny), C.byref(nz)))
+    return nx.value, ny.value, nz.value
+
+
+def rflbm_launches_per_step(h):
+    return _check(lib.rflbm_launches_per_step(h))
+
+
+def rflbm_philox4x32_10(ctr, k0, k1):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    _check(lib.rflbm_philox4x32_10(ctr.ctypes.data, k0, k1, out.ctypes.data, ctr.shape[0]))
+    return out
+
+
+def rflbm_site_normals(seed, step, replica, sites):
+    sites = np.ascontiguousarray(sites, dtype=np.uint32)
+    out = np.empty((sites.size, 24), dtype=np.float32)
+    _check(lib.rflbm_site_normals(seed, step, replica, sites.ctypes.data, sites.size,
+                                  out.ctypes.data))
+    return out
+
+
+# ------------------------------------------------------------------ convenience
+class Box:
+    """One periodic box (owns a handle). Population buffers are allocated by PyTorch
+    when `torch_buffers` is true, else by the library."""
+
+    def __init__(self, nx, ny, nz, tau, kT=0.0, rho0=1.0, seed=1, omega_g=1.0,
+                 model=RFLBM_MODEL_REG, phi_rho=RFLBM_PHI_LOCAL_RHO, replica=0,
+                 stream=None, torch_buffers=False, device=-1):
+        cfg = rflbm_config_default()
+        cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
+        cfg.tau, cfg.kT, cfg.rho0, cfg.seed = tau, kT, rho0, seed
+        cfg.omega_g, cfg.model, cfg.phi_rho, cfg.replica = omega_g, model, phi_rho, replica
+        cfg.device = device
+        if stream is not None:
+            cfg.stream = stream
+        self._buffers = None
+        if torch_buffers:
+            import torch
+            nbytes = rflbm_buffer_bytes(cfg)
+            dev = torch.device("cuda", device if device >= 0 else torch.cuda.current_device())
+            self._buffers = [torch.empty(nbytes // 4, dtype=torch.float32, device=dev)
+                             for _ in range(2)]
+            cfg.buffers[0] = self._buffers[0].data_ptr()
+            cfg.buffers[1] = self._buffers[1].data_ptr()
+        self.cfg = cfg
+        self.shape = (nx, ny, nz)
+        self.n = nx * ny * nz
+        self.h = rflbm_create_ex(cfg)
+
+    def close(self):
+        if self.h:
+            rflbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def populations(self):
+        f = np.empty((27, self.n))
+        rflbm_get_populations(self.h, f)
+        return f
+
+    def macroscopic(self):
+        rho, u, pi = np.empty(self.n), np.empty((3, self.n)), np.empty((6, self.n))
+        rflbm_moments(self.h, rho, u, pi)
+        return rho, u, pi
