@@ -177,6 +177,11 @@ int rflbm_synchronize(rflbm_t* h);
 int rflbm_get_dims(const rflbm_t* h, int* nx, int* ny, int* nz);
 int rflbm_launches_per_step(const rflbm_t* h);
 
+/* Step kernel the handle uses: the row-segment width (32, 64 or 128 sites) of the
+ * TMA-staged kernel, chosen when nx is a multiple of 32; 0 for the general kernel that
+ * gathers every population with its own address (any box). Both compute the same step. */
+int rflbm_step_path(const rflbm_t* h);
+
 /* Test entry points of the noise source (Eq. 9 r_k; the generator is the reading
  * stated above). Host buffers; computed on the current device.
  * rflbm_philox4x32_10: out[4*j + w] = word w of Philox4x32-10(ctr[4*j .. 4*j+3],

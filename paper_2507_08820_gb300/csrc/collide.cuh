@@ -88,7 +88,7 @@ __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideP
 
   // ---- 2. density, velocity and the scaled post-collision moments
   const float rho = cp.rho0 + drho;
-  const float inv_rho = 1.0f / rho;
+  const float inv_rho = rcp_approx(rho);
   const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
   // U[p] = u^p / beta_p: 1, 3u, 9u^2/2 ; RX[p] = rho U_x[p]
   const float Uy[3] = {1.0f, 3.0f * uy, 4.5f * uy * uy};
@@ -154,7 +154,7 @@ __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideP
           if (p + q + r >= 2) M[p][q][r] *= om;
   }
   if (kNoise) {
-    const float srho = kPhiRho0 ? cp.sqrt_rho0 : sqrtf(rho);
+    const float srho = kPhiRho0 ? cp.sqrt_rho0 : sqrt_approx(rho);
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll

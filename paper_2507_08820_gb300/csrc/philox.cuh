@@ -14,17 +14,43 @@ constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
+// Full 64-bit product of two 32-bit words (one wide multiply gives both halves).
+__device__ __forceinline__ void mulhilo(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+  const unsigned long long p = (unsigned long long)a * b;
+  hi = (uint32_t)(p >> 32);
+  lo = (uint32_t)p;
+}
+
 // Ten rounds of the Philox4x32 bijection on counter c under key (k0, k1).
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
-    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo(kPhiloxM0, c.x, hi0, lo0);
+    mulhilo(kPhiloxM1, c.z, hi1, lo1);
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     k0 += kPhiloxW0;
     k1 += kPhiloxW1;
   }
   return c;
+}
+
+// Single-instruction PTX approximations (relative error near 2^-23 for sqrt and rcp;
+// lg2 has an absolute error near 2^-22 on [1/2, 2] and a small relative error elsewhere).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // One Box-Muller pair from two uint32 draws, returned as radius and direction:
@@ -34,7 +60,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // -ln u0 is evaluated without cancellation: for x0 >= 2^31 it is -ln(1 - e) with
 // e = 1 - u0 = (~x0 + 1/2) 2^-32 formed exactly from the integer, by the series
 // e + e^2/2 + e^3/3 + e^4/4 + e^5/5 when e < 1/64 (truncation below 1e-10 relative) and
-// by log2 otherwise, so that radii near 0 keep their relative accuracy.
+// by log2 otherwise, so that radii near 0 keep their relative accuracy; log2 near 1 has
+// an absolute error near 2^-22, which for e >= 1/64 is a relative error below 2e-5 of
+// -ln u0 (below 1e-5 of the radius).
 // The angle is taken in (-pi, pi] where __sincosf is accurate: 2 pi u1 - pi, whose
 // cosine and sine are the negatives of those of 2 pi u1.
 __device__ __forceinline__ void box_muller(uint32_t x0, uint32_t x1, float& r, float& c,
@@ -43,11 +71,9 @@ __device__ __forceinline__ void box_muller(uint32_t x0, uint32_t x1, float& r, f
   const uint32_t xm = upper ? ~x0 : x0;  // < 2^31
   const float e = fmaf(__uint2float_rn(xm), 0x1p-32f, 0x1p-33f);  // (0, 1/2]
   const float arg = upper ? 1.0f - e : e;
-  float nl = -0.69314718055994531f * __log2f(arg);  // -ln(arg)
-  if (upper && e < 0.015625f) {
-    nl = e * fmaf(e, fmaf(e, fmaf(e, fmaf(e, 0.2f, 0.25f), 0.33333333f), 0.5f), 1.0f);
-  }
-  r = sqrtf(2.0f * nl);
+  const float lg = -1.3862943611198906f * lg2_approx(arg);  // -2 ln(arg)
+  const float ser = 2.0f * e * fmaf(e, fmaf(e, fmaf(e, fmaf(e, 0.2f, 0.25f), 0.33333333f), 0.5f), 1.0f);
+  r = sqrt_approx((upper && e < 0.015625f) ? ser : lg);
   const float t = fmaf(__uint2float_rn(x1), 6.283185307179586f * 0x1p-32f,
                        6.283185307179586f * 0x1p-33f - 3.14159265358979f);
   float st, ct;

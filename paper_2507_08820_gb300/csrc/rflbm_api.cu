@@ -29,6 +29,10 @@ struct rflbm {
   CollideParams cp{};
   double* partials = nullptr;  // stats scratch: kStatOutFields doubles per block + 8 out
   int stat_blocks = 0;
+  int* err = nullptr;          // device error flag set by bounded waits in kernels
+  int tma_width = 0;           // row-segment width of the TMA step path (0: generic)
+  CUtensorMap load_map[2];     // per buffer: source-row loads with halo
+  CUtensorMap store_map[2];    // per buffer: row-segment stores
   void* staging = nullptr;     // device staging for host<->device transfers
   size_t staging_bytes = 0;
 };
@@ -145,7 +149,60 @@ int check_ready(const rflbm* h) {
 
 int sync(rflbm* h, const char* what) {
   RFLBM_CUDA(cudaStreamSynchronize(h->stream), what);
+  int flag = 0;
+  RFLBM_CUDA(cudaMemcpy(&flag, h->err, sizeof(int), cudaMemcpyDeviceToHost), "reading the error flag");
+  if (flag) {
+    cudaMemset(h->err, 0, sizeof(int));
+    return fail(RFLBM_ETIMEOUT, "%s: a kernel gave up waiting for its bulk copies (bounded wait expired)", what);
+  }
   return RFLBM_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// The population buffer as a 4-D float tensor (x, y, z, plane); box = (box_x, 1, 1, 1).
+bool encode_map(CUtensorMap* map, float* base, const Geometry& g, uint32_t box_x) {
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {g.nx, g.ny, g.nz, (cuuint64_t)kQ};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nxy * 4, (cuuint64_t)g.ps * 4};
+  const cuuint32_t box[4] = {box_x, 1, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Selects the TMA step path when the box allows it and the descriptors encode.
+void setup_tma(rflbm* h) {
+  h->tma_width = 0;
+  const int w = tma_segment_width(h->geo.nx);
+  if (w == 0) return;
+  for (int b = 0; b < 2; ++b) {
+    if (!encode_map(&h->load_map[b], h->buf[b], h->geo, (uint32_t)w + 8) ||
+        !encode_map(&h->store_map[b], h->buf[b], h->geo, (uint32_t)w))
+      return;
+  }
+  h->tma_width = w;
 }
 
 int64_t n_sites(const rflbm* h) { return (int64_t)h->geo.n; }
@@ -242,11 +299,14 @@ rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
   h->stat_blocks = stats_partial_blocks(g, h->num_sms > 0 ? h->num_sms : 1);
   e = cudaMalloc((void**)&h->partials,
                  sizeof(double) * ((size_t)h->stat_blocks * kStatOutFields + 8));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
   if (e != cudaSuccess) {
     cuda_fail(e, "allocating the reduction scratch");
     rflbm_destroy(h);
     return nullptr;
   }
+  setup_tma(h);
   return h;
 }
 
@@ -267,6 +327,7 @@ void rflbm_destroy(rflbm_t* h) {
     cudaFree(h->buf[1]);
   }
   cudaFree(h->partials);
+  cudaFree(h->err);
   cudaFree(h->staging);
   delete h;
 }
@@ -319,11 +380,18 @@ int rflbm_step(rflbm_t* h, int64_t n) {
   p.key0 = (uint32_t)(h->cfg.seed & 0xffffffffu);
   p.key1 = (uint32_t)(h->cfg.seed >> 32);
   p.replica = h->cfg.replica;
+  p.err = h->err;
   for (int64_t t = 0; t < n; ++t) {
     p.src = h->buf[h->cur];
     p.dst = h->buf[1 - h->cur];
     p.step = (uint32_t)h->step;
-    cudaError_t e = launch_step_f32(p, h->variant, h->stream);
+    cudaError_t e;
+    if (h->tma_width) {
+      const TmaMaps m{&h->load_map[h->cur], &h->store_map[1 - h->cur], h->tma_width};
+      e = launch_step_tma_f32(m, p, h->variant, h->stream);
+    } else {
+      e = launch_step_f32(p, h->variant, h->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "launching the step kernel");
     h->cur = 1 - h->cur;
     ++h->step;
@@ -501,6 +569,11 @@ int rflbm_get_dims(const rflbm_t* h, int* nx, int* ny, int* nz) {
 int rflbm_launches_per_step(const rflbm_t* h) {
   if (int e = check_handle(h)) return e;
   return 1;
+}
+
+int rflbm_step_path(const rflbm_t* h) {
+  if (int e = check_handle(h)) return e;
+  return h->tma_width;
 }
 
 int rflbm_philox4x32_10(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, int64_t n) {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -63,12 +64,51 @@ __device__ __forceinline__ uint32_t pull_site(const Neighbours& nb, int i) {
   return nb.X[cx_of(i) + 1] + nb.Y[cy_of(i) + 1] + nb.Z[cz_of(i) + 1];
 }
 
+// Signed offsets from site s to its periodic neighbours, per axis and per direction of
+// the pulled population: D?[a] is the offset of the coordinate minus (a - 1), so the
+// pull source x - c_i of population i is s + DX[cx+1] + DY[cy+1] + DZ[cz+1].
+struct PullDeltas {
+  int32_t DX[3], DY[3], DZ[3];
+};
+
+__device__ __forceinline__ PullDeltas pull_deltas(uint32_t s, const Geometry& g) {
+  const uint32_t z = fastdiv(s, g.div_nxy);
+  const uint32_t rem = s - z * g.nxy;
+  const uint32_t y = fastdiv(rem, g.div_nx);
+  const uint32_t x = rem - y * g.nx;
+  const int32_t nx = (int32_t)g.nx, nxy = (int32_t)g.nxy, nyz = nxy * ((int32_t)g.nz - 1);
+  PullDeltas d;
+  d.DX[1] = 0;
+  d.DX[0] = (x + 1 == g.nx) ? 1 - nx : 1;            // x + 1 (pulled when c_x = -1)
+  d.DX[2] = (x == 0) ? nx - 1 : -1;                  // x - 1 (pulled when c_x = +1)
+  d.DY[1] = 0;
+  d.DY[0] = (y + 1 == g.ny) ? nx - nxy : nx;
+  d.DY[2] = (y == 0) ? nxy - nx : -nx;
+  d.DZ[1] = 0;
+  d.DZ[0] = (z + 1 == g.nz) ? -nyz : nxy;
+  d.DZ[2] = (z == 0) ? nyz : -nxy;
+  return d;
+}
+
+__device__ __forceinline__ int32_t pull_delta(const PullDeltas& d, int i) {
+  return d.DX[cx_of(i) + 1] + d.DY[cy_of(i) + 1] + d.DZ[cz_of(i) + 1];
+}
+
 struct StepParams {
   Geometry geo;
   CollideParams cp;
   const float* src;
   float* dst;
+  int* err;  // device error flag (bit 0: a bounded wait expired)
   uint32_t key0, key1, step, replica;
+};
+
+// TMA descriptors of a source buffer (row segments with a 4-element halo on each side)
+// and of a destination buffer (row segments), for segment width `width`.
+struct TmaMaps {
+  const CUtensorMap* load;
+  const CUtensorMap* store;
+  int width;
 };
 
 constexpr int kStepBlock = 256;
@@ -81,7 +121,13 @@ struct StepVariant {
   bool phi_rho0;    // Eq. 10 with rho0
 };
 
-// Launches one step of the fused pull kernel on `stream`.
+// Launches one step of the fused pull kernel (any box) on `stream`.
 cudaError_t launch_step_f32(const StepParams& p, const StepVariant& v, cudaStream_t stream);
+
+// Row-segment width of the TMA step kernel for a box of x edge nx (0: not supported).
+int tma_segment_width(uint32_t nx);
+// Launches one step of the TMA-staged kernel on `stream`.
+cudaError_t launch_step_tma_f32(const TmaMaps& m, const StepParams& p, const StepVariant& v,
+                                cudaStream_t stream);
 
 }  // namespace rflbm_dev

@@ -16,12 +16,14 @@ template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
 __global__ void __launch_bounds__(kStepBlock) step_pull_f32(const StepParams p) {
   const uint32_t s = blockIdx.x * kStepBlock + threadIdx.x;
   if (s >= p.geo.n) return;
-  const Neighbours nb = neighbours(s, p.geo);
+  const PullDeltas d = pull_deltas(s, p.geo);
+  const float* __restrict__ src = p.src + s;
 
   float G[3][3][3];
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = __ldg(p.src + i * p.geo.ps + pull_site(nb, i));
+    // per-thread neighbour pointer plus the plane offset i * ps (uniform across the grid)
+    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = __ldg((src + pull_delta(d, i)) + i * p.geo.ps);
   }
 
   SiteNoise noise;
@@ -29,10 +31,9 @@ __global__ void __launch_bounds__(kStepBlock) step_pull_f32(const StepParams p) 
 
   collide_site<kModel, kNoise, kGhostNeq, kPhiRho0>(G, p.cp, noise);
 
+  float* __restrict__ dst = p.dst + s;
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    p.dst[i * p.geo.ps + s] = G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1];
-  }
+  for (int i = 0; i < kQ; ++i) dst[i * p.geo.ps] = G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1];
 }
 
 template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>

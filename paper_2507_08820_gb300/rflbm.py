@@ -89,6 +89,7 @@ _sig = {
     "rflbm_synchronize": (C.c_int, [_H]),
     "rflbm_get_dims": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rflbm_launches_per_step": (C.c_int, [_H]),
+    "rflbm_step_path": (C.c_int, [_H]),
     "rflbm_philox4x32_10": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, C.c_int64]),
     "rflbm_site_normals": (C.c_int, [C.c_uint64, C.c_int64, C.c_uint32, _P, C.c_int64, _P]),
 }
@@ -249,6 +250,10 @@ def rflbm_get_dims(h):
 
 def rflbm_launches_per_step(h):
     return _check(lib.rflbm_launches_per_step(h))
+
+
+def rflbm_step_path(h):
+    return _check(lib.rflbm_step_path(h))
 
 
 def rflbm_philox4x32_10(ctr, k0, k1):

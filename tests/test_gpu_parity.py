@@ -1,9 +1,13 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerance: populations within 1e-5 relative (float32 GPU vs float64 oracle after up to
-100 steps); the Philox integer stream bit-exact; the float32 normals within 2e-5
-absolute. Every test starts the oracle from the exact float32-rounded state the GPU
-holds (read back through the ABI), so that only the step's arithmetic is compared.
+100 steps), the error of f_i taken relative to max(|f_i|, w_i rho0): thermal
+fluctuations carry some populations through zero (at kT = 1e-4 the corner populations
+of a 32^3 box span -0.26 w_i .. 2.2 w_i), where a bare |df_i| / |f_i| has no meaning, so
+the population's rest value is the floor of the scale. The Philox integer stream is
+bit-exact and the float32 normals agree within 2e-5 absolute. Every test starts the oracle from the exact float32-rounded
+state the GPU holds (read back through the ABI), so that only the step's arithmetic is
+compared.
 """
 import numpy as np
 import pytest
@@ -32,8 +36,10 @@ def _state(shape, seed, drho=0.02, du=0.03, amp=2e-4):
     return np.ascontiguousarray(o.equilibrium_state(rho, u) + W.population_perturbation(n, seed + 1, amp))
 
 
-def _rel(got, want):
-    return float(np.max(np.abs(got - want) / np.abs(want)))
+def _rel(got, want, rho0=1.0):
+    """Largest relative population error |df_i| / max(|f_i|, w_i rho0)."""
+    scale = np.maximum(np.abs(want), o.weights()[:, None] * rho0)
+    return float(np.max(np.abs(got - want) / scale))
 
 
 def _run_pair(R, shape, steps, tau=0.8, kT=1e-4, seed=3, t0=0, model="reg", omega_g=1.0,
@@ -92,22 +98,33 @@ def test_normals_accurate_for_extreme_radius_draws(R):
 
 
 # ------------------------------------------------------------------- one step, ragged boxes
-SHAPES = [(1, 1, 1), (2, 3, 4), (5, 1, 7), (17, 9, 5), (33, 31, 7)]
+# (shape, step kernel): general gather kernel (0) for x edges that are not multiples of 32,
+# else the TMA-staged kernel with its row-segment width (single- and multi-segment rows)
+SHAPES = [((1, 1, 1), 0), ((2, 3, 4), 0), ((5, 1, 7), 0), ((17, 9, 5), 0), ((33, 31, 7), 0),
+          ((32, 3, 2), 32), ((96, 4, 3), 32), ((64, 5, 3), 64), ((128, 2, 2), 128),
+          ((256, 3, 1), 128), ((32, 1, 1), 32)]
 
 
-@pytest.mark.parametrize("shape", SHAPES)
-def test_one_step_reg_flbm(R, shape):
+@pytest.mark.parametrize("shape,path", SHAPES)
+def test_one_step_reg_flbm(R, shape, path):
+    box = R.Box(*shape, tau=0.8)
+    assert R.rflbm_step_path(box.h) == path
+    box.close()
     got, want, _ = _run_pair(R, shape, steps=1, t0=17)
     assert _rel(got, want) < POP_RTOL
 
 
-@pytest.mark.parametrize("variant", [
+VARIANTS = [
     dict(kT=0.0), dict(model="bgk"), dict(model="bgk", kT=0.0), dict(omega_g=0.7),
     dict(omega_g=1.4, kT=0.0), dict(phi_rho="rho0"), dict(tau=0.5001), dict(tau=0.51),
     dict(tau=5.0), dict(tau=100.0), dict(kT=1e-3, tau=0.6), dict(model="bgk", tau=0.505),
-])
-def test_one_step_variants(R, variant):
-    got, want, _ = _run_pair(R, (13, 6, 5), steps=2, t0=3, **variant)
+]
+
+
+@pytest.mark.parametrize("shape", [(13, 6, 5), (64, 6, 5)])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_one_step_variants(R, variant, shape):
+    got, want, _ = _run_pair(R, shape, steps=2, t0=3, **variant)
     assert _rel(got, want) < POP_RTOL, variant
 
 
@@ -132,8 +149,10 @@ def test_config_32cubed_100_steps_from_rest(R):
     assert np.max(np.abs(u - wu)) < 3 * POP_RTOL
     assert np.max(np.abs(pi - wpi)) < 3 * POP_RTOL
     assert status == R.RFLBM_OK and st.nonfinite == 0 and st.step == 100
+    # float32 storage: each site-step rounds its 27 stored values (~2^-24 |g_i|,
+    # |g_i| ~ 3e-3); over 32^3 sites x 100 steps the sums random-walk to ~1e-6
     assert abs(st.mass - n) / n < 1e-9
-    assert np.max(np.abs(np.array(st.momentum))) < 1e-6
+    assert np.max(np.abs(np.array(st.momentum))) < 1e-5
     # the fluid did heat up: per-site density variance of order rho0 kT / cs2
     assert 0.3 < np.var(rho) / (kT * 3.0) < 1.5
 
@@ -274,4 +293,6 @@ def test_full_size_128cubed_sampled_sites(R):
         got[i] = after[i, dst]
     assert _rel(got, fstar) < POP_RTOL
     assert abs(st1.mass - st0.mass) / st0.mass < 1e-10
-    assert np.max(np.abs(np.array(st1.momentum) - np.array(st0.momentum))) < 1e-6
+    # float32 rounding of the 27 stored values of each site (~2^-24 |g_i|, |g_i| < 1e-2)
+    # summed with random signs over 2.1e6 sites: a drift of order 1e-6 per step
+    assert np.max(np.abs(np.array(st1.momentum) - np.array(st0.momentum))) < 1e-5
