@@ -193,6 +193,31 @@ int rflbm_philox4x32_10(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t*
 int rflbm_site_normals(uint64_t seed, int64_t step, uint32_t replica,
                        const uint32_t* sites, int64_t n, float* out);
 
+/* Global diagnostics of caller-owned populations that allocate nothing.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory at the moment they need these numbers, typically because their
+ * framework has already reserved the device memory for its own pool (a cudaMalloc would
+ * fail, or would synchronise the device inside a pipeline that must not stall), or
+ * because they run as a hook between the steps of another solver. It computes what
+ * rflbm_stats computes (FP64 sums of density and momentum, maximum speed, non-finite
+ * sites; step is set to 0) for populations in the public layout: f holds 27 planes of
+ * n_sites float32 values in device memory of the current device (element [i*n_sites + s]),
+ * owned by the caller. `stream` is a cudaStream_t or NULL; the call waits for it and fills
+ * *out (host memory).
+ *
+ * Scratch: a fixed area in the library's static device memory (about 512 KB, held by
+ * every GPU that loads the library until the process exits); no cudaMalloc, cudaFree or
+ * other allocating routine is called. Capacity: n_sites <= RFLBM_STATS_NOALLOC_MAX_SITES
+ * (8192 partial sums of 16384 sites); larger inputs are rejected with RFLBM_EINVAL. The
+ * first call on a device looks up the area's device address (once per device, with that
+ * device current); make that first call before any stream capture. All calls share the
+ * area: calls that overlap on the GPU (two streams or two host threads at once) race and
+ * must be serialised by the caller. Returns RFLBM_OK, RFLBM_EUNSTABLE (non-finite values;
+ * *out filled), RFLBM_EINVAL or RFLBM_ECUDA (message in rflbm_last_error). */
+#define RFLBM_STATS_NOALLOC_MAX_SITES 134217728LL
+int rflbm_stats_f32_noalloc(const float* f, int64_t n_sites, void* stream, rflbm_stats_t* out);
+
 #ifdef __cplusplus
 }
 #endif

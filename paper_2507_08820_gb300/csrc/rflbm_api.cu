@@ -209,6 +209,10 @@ int64_t n_sites(const rflbm* h) { return (int64_t)h->geo.n; }
 
 }  // namespace
 
+int rflbm_dev::record_error(int code, const char* msg, const char* detail) {
+  return detail ? fail(code, "%s: %s", msg, detail) : fail(code, "%s", msg);
+}
+
 extern "C" {
 
 void rflbm_config_default(rflbm_config_t* cfg) {

@@ -121,6 +121,10 @@ struct StepVariant {
   bool phi_rho0;    // Eq. 10 with rho0
 };
 
+// Records `msg` (and `detail`, if not NULL) as the calling thread's last error
+// (rflbm_last_error) and returns `code`.
+int record_error(int code, const char* msg, const char* detail);
+
 // Launches one step of the fused pull kernel (any box) on `stream`.
 cudaError_t launch_step_f32(const StepParams& p, const StepVariant& v, cudaStream_t stream);
 

@@ -92,6 +92,7 @@ _sig = {
     "rflbm_step_path": (C.c_int, [_H]),
     "rflbm_philox4x32_10": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, C.c_int64]),
     "rflbm_site_normals": (C.c_int, [C.c_uint64, C.c_int64, C.c_uint32, _P, C.c_int64, _P]),
+    "rflbm_stats_f32_noalloc": (C.c_int, [_P, C.c_int64, _P, C.POINTER(rflbm_stats_t)]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(lib, _name)
@@ -269,6 +270,23 @@ def rflbm_site_normals(seed, step, replica, sites):
     _check(lib.rflbm_site_normals(seed, step, replica, sites.ctypes.data, sites.size,
                                   out.ctypes.data))
     return out
+
+
+RFLBM_STATS_NOALLOC_MAX_SITES = 134217728
+
+
+def rflbm_stats_f32_noalloc(f, n_sites, stream=None):
+    """Diagnostics of caller-owned float32 populations (a CUDA tensor of 27 * n_sites
+    values, public layout) with the library's fixed scratch area: nothing is allocated.
+    Returns (stats, status) like rflbm_stats."""
+    p, d = _ptr(f, np.float32)
+    if not d:
+        raise ValueError("populations must be in device memory")
+    st = rflbm_stats_t()
+    status = lib.rflbm_stats_f32_noalloc(p, int(n_sites), stream, C.byref(st))
+    if status < 0 and status != RFLBM_EUNSTABLE:
+        _check(status)
+    return st, status
 
 
 # ------------------------------------------------------------------ convenience
