@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Reg-FLBM D3Q27 MLUPS + % HBM roofline, FP32 vs mixed at fixed FDT error"
 BYTES_PER_SITE_F32 = 216          # 27 float32 read + 27 float32 written per site update
 FALLBACK_HBM_GBS = 6800.0
-PROFILE = os.path.join(ROOT, "profiles", "step_pull_f32_128cubed.md")
+PROFILES = os.path.join(ROOT, "profiles")
 
 
 def parse_args():
@@ -82,11 +82,19 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def kernel_name(path, kT, model):
+    noise = "noise" if kT > 0 else "no noise"
+    m = "BGK" if model else "Reg"
+    if path:
+        return f"step_tma_f32<{path}, {m}, {noise}>", f"step_tma_f32_{path}"
+    return f"step_pull_f32<{m}, {noise}>", "step_pull_f32"
+
+
+def profiled_traffic(profile_stem, edge):
     """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
     when the summary is missing or was taken on different kernel sources."""
     try:
-        text = open(PROFILE).read()
+        text = open(os.path.join(PROFILES, f"{profile_stem}_{edge}cubed.md")).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(sources ([0-9a-f]+)\)", text)
@@ -253,6 +261,7 @@ def gb300_arm(args):
     box = R.Box(e, e, e, tau=args.tau, kT=args.kT, seed=1, replica=info.rank,
                 stream=stream.cuda_stream, torch_buffers=True, device=info.local_rank)
     R.rflbm_init_rest(box.h)
+    path = R.rflbm_step_path(box.h)
     R.rflbm_step(box.h, args.warmup)
     R.rflbm_synchronize(box.h)
 
@@ -301,10 +310,10 @@ def gb300_arm(args):
     per_launch_s = ms * 1e-3 / args.steps
     achieved = BYTES_PER_SITE_F32 * n / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
+    kname, kstem = kernel_name(path, args.kT, 0)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(),
-                "peak_source": f"hbm_gbs of {peak_kind}",
-                "kernel": "step_pull_f32<Reg, noise>",
+                "frac": achieved / peak, "traffic": profiled_traffic(kstem, e),
+                "peak_source": f"hbm_gbs of {peak_kind}", "kernel": kname,
                 "algorithmic_bytes_per_launch": BYTES_PER_SITE_F32 * n}
     cpu = None
     if not args.no_cpu_baseline:
