@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--kT", type=float, default=1e-4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--kernel", choices=["auto", "gather", "tma", "persistent"], default="auto")
     return ap.parse_args()
 
 
@@ -82,10 +83,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_name(path, kT, model):
+def kernel_name(kind, path, kT, model):
     noise = "noise" if kT > 0 else "no noise"
     m = "BGK" if model else "Reg"
-    if path:
+    if kind == 3:
+        return f"step_tma_persistent_f32<{path}, {m}, {noise}>", f"step_tma_persistent_f32_{path}"
+    if kind == 2:
         return f"step_tma_f32<{path}, {m}, {noise}>", f"step_tma_f32_{path}"
     return f"step_pull_f32<{m}, {noise}>", "step_pull_f32"
 
@@ -258,10 +261,13 @@ def gb300_arm(args):
     e = args.edge
     n = e ** 3
     stream = torch.cuda.Stream(device=dev)
+    kernel = {"auto": R.RFLBM_KERNEL_AUTO, "gather": R.RFLBM_KERNEL_GATHER,
+              "tma": R.RFLBM_KERNEL_TMA, "persistent": R.RFLBM_KERNEL_TMA_PERSISTENT}[args.kernel]
     box = R.Box(e, e, e, tau=args.tau, kT=args.kT, seed=1, replica=info.rank,
-                stream=stream.cuda_stream, torch_buffers=True, device=info.local_rank)
+                stream=stream.cuda_stream, torch_buffers=True, device=info.local_rank,
+                kernel=kernel)
     R.rflbm_init_rest(box.h)
-    path = R.rflbm_step_path(box.h)
+    kind, path = R.rflbm_step_path(box.h)
     R.rflbm_step(box.h, args.warmup)
     R.rflbm_synchronize(box.h)
 
@@ -294,7 +300,7 @@ def gb300_arm(args):
     if not args.no_variants and info.world == 1:
         for name, kw in (("reg_lbm_kT0", dict(kT=0.0)),
                          ("bgk_flbm", dict(kT=args.kT, model=R.RFLBM_MODEL_BGK))):
-            vb = R.Box(e, e, e, tau=args.tau, seed=1, stream=stream.cuda_stream, **kw)
+            vb = R.Box(e, e, e, tau=args.tau, seed=1, stream=stream.cuda_stream, kernel=kernel, **kw)
             R.rflbm_init_rest(vb.h)
             R.rflbm_step(vb.h, 50)
             k = max(10, args.steps // 4)
@@ -310,7 +316,7 @@ def gb300_arm(args):
     per_launch_s = ms * 1e-3 / args.steps
     achieved = BYTES_PER_SITE_F32 * n / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
-    kname, kstem = kernel_name(path, args.kT, 0)
+    kname, kstem = kernel_name(kind, path, args.kT, 0)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(kstem, e),
                 "peak_source": f"hbm_gbs of {peak_kind}", "kernel": kname,

@@ -68,6 +68,16 @@ typedef enum {
   RFLBM_PHI_RHO0 = 1       /* rho in Eq. 10 is the reference density rho0 */
 } rflbm_phi_rho;
 
+/* Step kernels. All compute the same step; they differ in how the 27 neighbours are
+ * fetched. The TMA kernels need nx to be a multiple of 32 (row segments of 128, 64 or 32
+ * sites); on other boxes every choice runs the general kernel. */
+typedef enum {
+  RFLBM_KERNEL_AUTO = 0,           /* TMA when the box allows it, else the general kernel */
+  RFLBM_KERNEL_GATHER = 1,         /* one thread per site, 27 addressed loads */
+  RFLBM_KERNEL_TMA = 2,            /* one CTA per row segment, TMA tensor loads/stores */
+  RFLBM_KERNEL_TMA_PERSISTENT = 3  /* persistent CTAs, double-buffered TMA row segments */
+} rflbm_kernel;
+
 typedef struct {
   int nx, ny, nz;        /* box edges, each >= 1; N = nx*ny*nz < 2^31 */
   double tau;            /* hydrodynamic relaxation time tau_h = 1/omega_h > 1/2 */
@@ -84,6 +94,7 @@ typedef struct {
                             rflbm_buffer_bytes(cfg) bytes each, 256-byte aligned;
                             NULL: the library allocates and frees them */
   int device;            /* CUDA device ordinal, -1 = the current device */
+  int kernel;            /* rflbm_kernel */
 } rflbm_config_t;
 
 typedef struct {
@@ -96,7 +107,7 @@ typedef struct {
 
 /* Fills cfg with the defaults: 32^3, tau 0.8, kT 0, rho0 1, seed 1, omega_g 1, Reg model,
  * float32 storage, local rho in Eq. 10, replica 0, default stream, library buffers,
- * current device. */
+ * current device, automatic kernel choice. */
 void rflbm_config_default(rflbm_config_t* cfg);
 
 /* Bytes of one population buffer for cfg (two are used, ping-pong), or a negative
@@ -177,10 +188,9 @@ int rflbm_synchronize(rflbm_t* h);
 int rflbm_get_dims(const rflbm_t* h, int* nx, int* ny, int* nz);
 int rflbm_launches_per_step(const rflbm_t* h);
 
-/* Step kernel the handle uses: the row-segment width (32, 64 or 128 sites) of the
- * TMA-staged kernel, chosen when nx is a multiple of 32; 0 for the general kernel that
- * gathers every population with its own address (any box). Both compute the same step. */
-int rflbm_step_path(const rflbm_t* h);
+/* Step kernel the handle runs (an rflbm_kernel value other than AUTO); *width, if not
+ * NULL, receives the row-segment width of the TMA kernels (0 for the general kernel). */
+int rflbm_step_path(const rflbm_t* h, int* width);
 
 /* Test entry points of the noise source (Eq. 9 r_k; the generator is the reading
  * stated above). Host buffers; computed on the current device.

@@ -154,17 +154,26 @@ __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideP
           if (p + q + r >= 2) M[p][q][r] *= om;
   }
   if (kNoise) {
+    // Box-Muller pair m gives the normals r_k of modes k = 2m + 4 (cosine) and 2m + 5 (sine)
     const float srho = kPhiRho0 ? cp.sqrt_rho0 : sqrt_approx(rho);
 #pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          if (p + q + r < 2) continue;
-          const int k = mode_of(p, q, r);
-          M[p][q][r] = fmaf(cp.amp[k - 4], normal_at(noise, k - 4, srho), M[p][q][r]);
+    for (int m = 0; m < 12; ++m) {
+      const int k0 = 2 * m + 4, k1 = 2 * m + 5;
+      float& M0 = M[p_of(k0)][q_of(k0)][r_of(k0)];
+      const float rr = noise.r[m] * srho;
+      if (k1 < kQ && same_amplitude(k0, k1)) {
+        float& M1 = M[p_of(k1)][q_of(k1)][r_of(k1)];
+        const float a = rr * cp.amp[k0 - 4];
+        M0 = fmaf(a, noise.c[m], M0);
+        M1 = fmaf(a, noise.s[m], M1);
+      } else {
+        M0 = fmaf(cp.amp[k0 - 4], rr * noise.c[m], M0);
+        if (k1 < kQ) {
+          float& M1 = M[p_of(k1 < kQ ? k1 : 0)][q_of(k1 < kQ ? k1 : 0)][r_of(k1 < kQ ? k1 : 0)];
+          M1 = fmaf(cp.amp[(k1 < kQ ? k1 : 4) - 4], rr * noise.s[m], M1);
         }
+      }
+    }
   }
 
   // ---- 3. back transform (sweep z, then y, then x) and the lattice weights

@@ -45,11 +45,41 @@ __host__ __device__ constexpr double beta1d(int p) {
 __host__ __device__ constexpr double bnorm(int p, int q, int r) {
   return beta1d(p) * beta1d(q) * beta1d(r);
 }
+// Hermite exponents (p, q, r) of the Table II mode k.
+__host__ __device__ constexpr int p_of(int k) {
+  constexpr int t[kQ] = {0, 1, 0, 0, 2, 0, 0, 1, 1, 0, 2, 2, 1, 1, 0, 0, 1, 2, 2, 0, 1, 1, 2, 2, 2, 1, 2};
+  return t[k];
+}
+__host__ __device__ constexpr int q_of(int k) {
+  constexpr int t[kQ] = {0, 0, 1, 0, 0, 2, 0, 1, 0, 1, 1, 0, 2, 0, 1, 2, 1, 2, 0, 2, 1, 2, 1, 1, 2, 2, 2};
+  return t[k];
+}
+__host__ __device__ constexpr int r_of(int k) {
+  constexpr int t[kQ] = {0, 0, 0, 1, 0, 0, 2, 0, 1, 1, 0, 1, 0, 2, 2, 1, 1, 0, 2, 2, 2, 1, 1, 2, 1, 2, 2};
+  return t[k];
+}
+// Modes k and l relax at the same rate and have the same norm: equal noise amplitudes.
+__host__ __device__ constexpr bool same_amplitude(int k, int l) {
+  return bnorm(p_of(k), q_of(k), r_of(k)) == bnorm(p_of(l), q_of(l), r_of(l)) &&
+         ((k < 10) == (l < 10));
+}
+
 // Table II index k of the mode with Hermite exponents (p, q, r).
 __host__ __device__ constexpr int mode_of(int p, int q, int r) {
   constexpr int t[kQ] = {0, 3, 6, 2, 9, 14, 5, 15, 19, 1, 8, 13, 7, 16, 20,
                          12, 21, 25, 4, 11, 18, 10, 22, 23, 17, 24, 26};
   return t[9 * p + 3 * q + r];
 }
+
+// The two mode tables are inverse to each other, and the weights sum to one.
+__host__ __device__ constexpr bool tables_consistent() {
+  double wsum = 0.0;
+  for (int k = 0; k < kQ; ++k) {
+    if (mode_of(p_of(k), q_of(k), r_of(k)) != k) return false;
+    wsum += weight_of(k);
+  }
+  return wsum > 1.0 - 1e-12 && wsum < 1.0 + 1e-12;
+}
+static_assert(tables_consistent(), "D3Q27 tables are inconsistent");
 
 }  // namespace rflbm_dev

@@ -59,10 +59,9 @@ __device__ __forceinline__ float lg2_approx(float x) {
 //
 // -ln u0 is evaluated without cancellation: for x0 >= 2^31 it is -ln(1 - e) with
 // e = 1 - u0 = (~x0 + 1/2) 2^-32 formed exactly from the integer, by the series
-// e + e^2/2 + e^3/3 + e^4/4 + e^5/5 when e < 1/64 (truncation below 1e-10 relative) and
-// by log2 otherwise, so that radii near 0 keep their relative accuracy; log2 near 1 has
-// an absolute error near 2^-22, which for e >= 1/64 is a relative error below 2e-5 of
-// -ln u0 (below 1e-5 of the radius).
+// e + e^2/2 + e^3/3 when e < 2^-8 (truncation below 2e-8 relative) and by log2 otherwise,
+// so that radii near 0 keep their relative accuracy; log2 near 1 has an absolute error
+// near 2^-22, which for e >= 2^-8 is a radius error below 2e-6 absolute.
 // The angle is taken in (-pi, pi] where __sincosf is accurate: 2 pi u1 - pi, whose
 // cosine and sine are the negatives of those of 2 pi u1.
 __device__ __forceinline__ void box_muller(uint32_t x0, uint32_t x1, float& r, float& c,
@@ -72,8 +71,8 @@ __device__ __forceinline__ void box_muller(uint32_t x0, uint32_t x1, float& r, f
   const float e = fmaf(__uint2float_rn(xm), 0x1p-32f, 0x1p-33f);  // (0, 1/2]
   const float arg = upper ? 1.0f - e : e;
   const float lg = -1.3862943611198906f * lg2_approx(arg);  // -2 ln(arg)
-  const float ser = 2.0f * e * fmaf(e, fmaf(e, fmaf(e, fmaf(e, 0.2f, 0.25f), 0.33333333f), 0.5f), 1.0f);
-  r = sqrt_approx((upper && e < 0.015625f) ? ser : lg);
+  const float ser = e * fmaf(e, fmaf(e, 0.66666667f, 1.0f), 2.0f);  // 2e + e^2 + 2e^3/3
+  r = sqrt_approx((upper && e < 0.00390625f) ? ser : lg);
   const float t = fmaf(__uint2float_rn(x1), 6.283185307179586f * 0x1p-32f,
                        6.283185307179586f * 0x1p-33f - 3.14159265358979f);
   float st, ct;
@@ -87,6 +86,18 @@ __device__ __forceinline__ void box_muller(uint32_t x0, uint32_t x1, float& r, f
 struct SiteNoise {
   float r[12], c[12], s[12];
 };
+
+// Calls j0 <= j < j1 of site_noise (the draws can be split around other work).
+template <int j0, int j1>
+__device__ __forceinline__ void site_noise_part(uint32_t site, uint32_t step, uint32_t replica,
+                                                uint32_t k0, uint32_t k1, SiteNoise& out) {
+#pragma unroll
+  for (int j = j0; j < j1; ++j) {
+    const uint4 w = philox4x32_10(make_uint4(site, step, (uint32_t)j, replica), k0, k1);
+    box_muller(w.x, w.y, out.r[2 * j], out.c[2 * j], out.s[2 * j]);
+    box_muller(w.z, w.w, out.r[2 * j + 1], out.c[2 * j + 1], out.s[2 * j + 1]);
+  }
+}
 
 __device__ __forceinline__ void site_noise(uint32_t site, uint32_t step, uint32_t replica,
                                            uint32_t k0, uint32_t k1, SiteNoise& out) {

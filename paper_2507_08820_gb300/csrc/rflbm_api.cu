@@ -31,6 +31,7 @@ struct rflbm {
   int stat_blocks = 0;
   int* err = nullptr;          // device error flag set by bounded waits in kernels
   int tma_width = 0;           // row-segment width of the TMA step path (0: generic)
+  int kernel = RFLBM_KERNEL_GATHER;  // the step kernel in use
   CUtensorMap load_map[2];     // per buffer: source-row loads with halo
   CUtensorMap store_map[2];    // per buffer: row-segment stores
   void* staging = nullptr;     // device staging for host<->device transfers
@@ -94,6 +95,8 @@ int validate(const rflbm_config_t* c) {
   if (c->storage != RFLBM_STORE_F32) return fail(RFLBM_EINVAL, "unknown storage %d", c->storage);
   if (c->phi_rho != RFLBM_PHI_LOCAL_RHO && c->phi_rho != RFLBM_PHI_RHO0)
     return fail(RFLBM_EINVAL, "unknown phi_rho option %d", c->phi_rho);
+  if (c->kernel < RFLBM_KERNEL_AUTO || c->kernel > RFLBM_KERNEL_TMA_PERSISTENT)
+    return fail(RFLBM_EINVAL, "unknown kernel choice %d", c->kernel);
   return RFLBM_OK;
 }
 
@@ -195,14 +198,16 @@ bool encode_map(CUtensorMap* map, float* base, const Geometry& g, uint32_t box_x
 // Selects the TMA step path when the box allows it and the descriptors encode.
 void setup_tma(rflbm* h) {
   h->tma_width = 0;
+  h->kernel = RFLBM_KERNEL_GATHER;
   const int w = tma_segment_width(h->geo.nx);
-  if (w == 0) return;
+  if (w == 0 || h->cfg.kernel == RFLBM_KERNEL_GATHER) return;
   for (int b = 0; b < 2; ++b) {
     if (!encode_map(&h->load_map[b], h->buf[b], h->geo, (uint32_t)w + 8) ||
         !encode_map(&h->store_map[b], h->buf[b], h->geo, (uint32_t)w))
       return;
   }
   h->tma_width = w;
+  h->kernel = h->cfg.kernel == RFLBM_KERNEL_TMA_PERSISTENT ? RFLBM_KERNEL_TMA_PERSISTENT : RFLBM_KERNEL_TMA;
 }
 
 int64_t n_sites(const rflbm* h) { return (int64_t)h->geo.n; }
@@ -231,6 +236,7 @@ void rflbm_config_default(rflbm_config_t* cfg) {
   cfg->stream = nullptr;
   cfg->buffers[0] = cfg->buffers[1] = nullptr;
   cfg->device = -1;
+  cfg->kernel = RFLBM_KERNEL_AUTO;
 }
 
 int64_t rflbm_buffer_bytes(const rflbm_config_t* cfg) {
@@ -298,6 +304,15 @@ rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
         rflbm_destroy(h);
         return nullptr;
       }
+    }
+  }
+  // zero both buffers: the plane padding is then deterministic in state images
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMemset(h->buf[b], 0, bytes);
+    if (e != cudaSuccess) {
+      cuda_fail(e, "clearing a population buffer");
+      rflbm_destroy(h);
+      return nullptr;
     }
   }
   h->stat_blocks = stats_partial_blocks(g, h->num_sms > 0 ? h->num_sms : 1);
@@ -391,7 +406,8 @@ int rflbm_step(rflbm_t* h, int64_t n) {
     p.step = (uint32_t)h->step;
     cudaError_t e;
     if (h->tma_width) {
-      const TmaMaps m{&h->load_map[h->cur], &h->store_map[1 - h->cur], h->tma_width};
+      const TmaMaps m{&h->load_map[h->cur], &h->store_map[1 - h->cur], h->tma_width,
+                      h->kernel == RFLBM_KERNEL_TMA_PERSISTENT ? h->num_sms : 0};
       e = launch_step_tma_f32(m, p, h->variant, h->stream);
     } else {
       e = launch_step_f32(p, h->variant, h->stream);
@@ -575,9 +591,10 @@ int rflbm_launches_per_step(const rflbm_t* h) {
   return 1;
 }
 
-int rflbm_step_path(const rflbm_t* h) {
+int rflbm_step_path(const rflbm_t* h, int* width) {
   if (int e = check_handle(h)) return e;
-  return h->tma_width;
+  if (width) *width = h->tma_width;
+  return h->kernel;
 }
 
 int rflbm_philox4x32_10(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, int64_t n) {

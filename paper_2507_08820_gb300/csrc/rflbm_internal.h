@@ -109,6 +109,7 @@ struct TmaMaps {
   const CUtensorMap* load;
   const CUtensorMap* store;
   int width;
+  int persistent_sms;  // > 0: persistent double-buffered kernel over this many SMs
 };
 
 constexpr int kStepBlock = 256;

@@ -27,6 +27,10 @@ RFLBM_MODEL_BGK = 1
 RFLBM_STORE_F32 = 0
 RFLBM_PHI_LOCAL_RHO = 0
 RFLBM_PHI_RHO0 = 1
+RFLBM_KERNEL_AUTO = 0
+RFLBM_KERNEL_GATHER = 1
+RFLBM_KERNEL_TMA = 2
+RFLBM_KERNEL_TMA_PERSISTENT = 3
 
 
 class RflbmError(RuntimeError):
@@ -42,7 +46,7 @@ class rflbm_config_t(C.Structure):
         ("seed", C.c_uint64), ("omega_g", C.c_double),
         ("model", C.c_int), ("storage", C.c_int), ("phi_rho", C.c_int),
         ("replica", C.c_uint32), ("stream", C.c_void_p),
-        ("buffers", C.c_void_p * 2), ("device", C.c_int),
+        ("buffers", C.c_void_p * 2), ("device", C.c_int), ("kernel", C.c_int),
     ]
 
 
@@ -89,7 +93,7 @@ _sig = {
     "rflbm_synchronize": (C.c_int, [_H]),
     "rflbm_get_dims": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rflbm_launches_per_step": (C.c_int, [_H]),
-    "rflbm_step_path": (C.c_int, [_H]),
+    "rflbm_step_path": (C.c_int, [_H, C.POINTER(C.c_int)]),
     "rflbm_philox4x32_10": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, C.c_int64]),
     "rflbm_site_normals": (C.c_int, [C.c_uint64, C.c_int64, C.c_uint32, _P, C.c_int64, _P]),
     "rflbm_stats_f32_noalloc": (C.c_int, [_P, C.c_int64, _P, C.POINTER(rflbm_stats_t)]),
@@ -254,7 +258,10 @@ def rflbm_launches_per_step(h):
 
 
 def rflbm_step_path(h):
-    return _check(lib.rflbm_step_path(h))
+    """(kernel, row-segment width) of the step kernel the handle runs."""
+    w = C.c_int()
+    k = _check(lib.rflbm_step_path(h, C.byref(w)))
+    return k, w.value
 
 
 def rflbm_philox4x32_10(ctr, k0, k1):
@@ -296,12 +303,13 @@ class Box:
 
     def __init__(self, nx, ny, nz, tau, kT=0.0, rho0=1.0, seed=1, omega_g=1.0,
                  model=RFLBM_MODEL_REG, phi_rho=RFLBM_PHI_LOCAL_RHO, replica=0,
-                 stream=None, torch_buffers=False, device=-1):
+                 stream=None, torch_buffers=False, device=-1, kernel=RFLBM_KERNEL_AUTO):
         cfg = rflbm_config_default()
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
         cfg.tau, cfg.kT, cfg.rho0, cfg.seed = tau, kT, rho0, seed
         cfg.omega_g, cfg.model, cfg.phi_rho, cfg.replica = omega_g, model, phi_rho, replica
         cfg.device = device
+        cfg.kernel = kernel
         if stream is not None:
             cfg.stream = stream
         self._buffers = None

@@ -43,10 +43,11 @@ def _rel(got, want, rho0=1.0):
 
 
 def _run_pair(R, shape, steps, tau=0.8, kT=1e-4, seed=3, t0=0, model="reg", omega_g=1.0,
-              phi_rho="local", f0=None):
+              phi_rho="local", f0=None, kernel=0):
     box = R.Box(*shape, tau=tau, kT=kT, seed=seed, omega_g=omega_g,
                 model=R.RFLBM_MODEL_BGK if model == "bgk" else R.RFLBM_MODEL_REG,
-                phi_rho=R.RFLBM_PHI_RHO0 if phi_rho == "rho0" else R.RFLBM_PHI_LOCAL_RHO)
+                phi_rho=R.RFLBM_PHI_RHO0 if phi_rho == "rho0" else R.RFLBM_PHI_LOCAL_RHO,
+                kernel=kernel)
     R.rflbm_set_populations(box.h, _state(shape, seed=11) if f0 is None else f0)
     R.rflbm_set_step(box.h, t0)
     start = box.populations()
@@ -98,20 +99,53 @@ def test_normals_accurate_for_extreme_radius_draws(R):
 
 
 # ------------------------------------------------------------------- one step, ragged boxes
-# (shape, step kernel): general gather kernel (0) for x edges that are not multiples of 32,
-# else the TMA-staged kernel with its row-segment width (single- and multi-segment rows)
+# (shape, TMA row-segment width): the TMA kernels need x edges that are multiples of 32
+# (single- and multi-segment rows below); other boxes run the general gather kernel
 SHAPES = [((1, 1, 1), 0), ((2, 3, 4), 0), ((5, 1, 7), 0), ((17, 9, 5), 0), ((33, 31, 7), 0),
           ((32, 3, 2), 32), ((96, 4, 3), 32), ((64, 5, 3), 64), ((128, 2, 2), 128),
-          ((256, 3, 1), 128), ((32, 1, 1), 32)]
+          ((256, 3, 1), 128), ((32, 1, 1), 32), ((128, 9, 7), 128)]
+KERNELS = ["gather", "tma", "persistent"]
 
 
-@pytest.mark.parametrize("shape,path", SHAPES)
-def test_one_step_reg_flbm(R, shape, path):
-    box = R.Box(*shape, tau=0.8)
-    assert R.rflbm_step_path(box.h) == path
+def _kernel_id(R, name):
+    return {"gather": R.RFLBM_KERNEL_GATHER, "tma": R.RFLBM_KERNEL_TMA,
+            "persistent": R.RFLBM_KERNEL_TMA_PERSISTENT}[name]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape,width", SHAPES)
+def test_one_step_reg_flbm(R, shape, width, kernel):
+    kid = _kernel_id(R, kernel)
+    box = R.Box(*shape, tau=0.8, kernel=kid)
+    tma = width > 0 and kid != R.RFLBM_KERNEL_GATHER
+    assert R.rflbm_step_path(box.h) == ((kid, width) if tma else (R.RFLBM_KERNEL_GATHER, 0))
     box.close()
-    got, want, _ = _run_pair(R, shape, steps=1, t0=17)
+    got, want, _ = _run_pair(R, shape, steps=3, t0=17, kernel=kid)
     assert _rel(got, want) < POP_RTOL
+
+
+def test_auto_kernel_choice(R):
+    box = R.Box(128, 4, 4, tau=0.8)
+    assert R.rflbm_step_path(box.h) == (R.RFLBM_KERNEL_TMA, 128)
+    box.close()
+    box = R.Box(48, 4, 4, tau=0.8)
+    assert R.rflbm_step_path(box.h) == (R.RFLBM_KERNEL_GATHER, 0)
+    box.close()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_kernels_agree_bitwise(R, kernel):
+    """The three step kernels run the same per-site arithmetic on the same inputs."""
+    shape = (64, 10, 6)
+    f0 = _state(shape, seed=31)
+    out = {}
+    for name in ("gather", kernel):
+        box = R.Box(*shape, tau=0.7, kT=1e-4, seed=2, kernel=_kernel_id(R, name))
+        R.rflbm_set_populations(box.h, f0)
+        R.rflbm_step(box.h, 4)
+        out[name] = box.populations()
+        box.close()
+    assert np.allclose(out[kernel], out["gather"], rtol=1e-6, atol=0)
 
 
 VARIANTS = [
@@ -121,10 +155,10 @@ VARIANTS = [
 ]
 
 
-@pytest.mark.parametrize("shape", [(13, 6, 5), (64, 6, 5)])
+@pytest.mark.parametrize("shape,kernel", [((13, 6, 5), 0), ((64, 6, 5), 2), ((64, 6, 5), 3)])
 @pytest.mark.parametrize("variant", VARIANTS)
-def test_one_step_variants(R, variant, shape):
-    got, want, _ = _run_pair(R, shape, steps=2, t0=3, **variant)
+def test_one_step_variants(R, variant, shape, kernel):
+    got, want, _ = _run_pair(R, shape, steps=2, t0=3, kernel=kernel, **variant)
     assert _rel(got, want) < POP_RTOL, variant
 
 
