@@ -192,6 +192,31 @@ int rflbm_launches_per_step(const rflbm_t* h);
  * NULL, receives the row-segment width of the TMA kernels (0 for the general kernel). */
 int rflbm_step_path(const rflbm_t* h, int* width);
 
+/* Equilibrium-statistics diagnostics of the current (pre-collision) state, FP64
+ * accumulation, synchronous. They serve the fluctuation-dissipation checks of Sec. III:
+ * at equilibrium every mode of Table II fluctuates per site with variance
+ * rho0 kT b_k / cs2, and the static structure factors of rho, rho u and Pi are flat.
+ *
+ * rflbm_mode_sums: sum[k] = sum over sites of m_k - rho0 delta_k0 and sumsq[k] = sum of its
+ *   square, for the 27 modes m_k = sum_i e_ki f_i of Table II (Eq. 5); 27 doubles each in
+ *   host memory. Per-site values are formed in float32.
+ * rflbm_structure_factor: for one field (rflbm_field, per site), F(k) = sum_x phi(x)
+ *   exp(-i k.x) by a 3-D FFT (cuFFT), S(k) = |F(k)|^2 / N, summed over the spherical
+ *   shells n = round(|k| L / 2 pi), L = max(nx, ny, nz): s_sum[n] = sum of S over the
+ *   wave vectors of shell n, count[n] = their number (n < nshell; both host arrays of
+ *   nshell doubles; the k = 0 vector is in shell 0). Work buffers (two N-sized FP64 arrays
+ *   and the FFT plan) are allocated on first use and kept by the handle.
+ * rflbm_shell_count: the number of shells that covers every wave vector of the box. */
+typedef enum {
+  RFLBM_FIELD_RHO = 0,  /* rho - rho0 */
+  RFLBM_FIELD_JX = 1, RFLBM_FIELD_JY = 2, RFLBM_FIELD_JZ = 3,  /* rho u */
+  RFLBM_FIELD_PXX = 4, RFLBM_FIELD_PYY = 5, RFLBM_FIELD_PZZ = 6,  /* Pi = a^(2) (Sec. III) */
+  RFLBM_FIELD_PXY = 7, RFLBM_FIELD_PXZ = 8, RFLBM_FIELD_PYZ = 9
+} rflbm_field;
+int rflbm_mode_sums(rflbm_t* h, double* sum, double* sumsq);
+int rflbm_structure_factor(rflbm_t* h, int field, int nshell, double* s_sum, double* count);
+int rflbm_shell_count(const rflbm_t* h);
+
 /* Test entry points of the noise source (Eq. 9 r_k; the generator is the reading
  * stated above). Host buffers; computed on the current device.
  * rflbm_philox4x32_10: out[4*j + w] = word w of Philox4x32-10(ctr[4*j .. 4*j+3],

@@ -75,7 +75,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in results:
             sys.stderr.write(log)
     tmp = LIB + ".tmp"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcufft",
+           "-Xlinker", "-rpath," + os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"linking librflbm.so failed:\n{res.stdout}\n{res.stderr}")

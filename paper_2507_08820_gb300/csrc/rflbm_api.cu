@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/rflbm.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -9,8 +10,11 @@
 #include <string>
 #include <vector>
 
+#include <cufft.h>
+
 #include "../../include/rflbm.h"
 #include "rflbm_aux.h"
+#include "rflbm_diag.h"
 
 using namespace rflbm_dev;
 
@@ -34,6 +38,13 @@ struct rflbm {
   int kernel = RFLBM_KERNEL_GATHER;  // the step kernel in use
   CUtensorMap load_map[2];     // per buffer: source-row loads with halo
   CUtensorMap store_map[2];    // per buffer: row-segment stores
+  // diagnostics (allocated on first use)
+  double* diag_partials = nullptr;
+  size_t diag_partials_bytes = 0;
+  double* diag_field = nullptr;   // one FP64 field (N)
+  void* diag_spec = nullptr;      // its D2Z spectrum
+  cufftHandle fft_plan = 0;
+  bool fft_ready = false;
   void* staging = nullptr;     // device staging for host<->device transfers
   size_t staging_bytes = 0;
 };
@@ -347,6 +358,10 @@ void rflbm_destroy(rflbm_t* h) {
   }
   cudaFree(h->partials);
   cudaFree(h->err);
+  cudaFree(h->diag_partials);
+  cudaFree(h->diag_field);
+  cudaFree(h->diag_spec);
+  if (h->fft_ready) cufftDestroy(h->fft_plan);
   cudaFree(h->staging);
   delete h;
 }
@@ -524,6 +539,76 @@ int rflbm_get_sites(rflbm_t* h, const int64_t* sites, int64_t n, double* f) {
   RFLBM_CUDA(launch_get_sites(h->geo, h->cp.rho0, h->buf[h->cur], dsites, n, dout, h->stream), "launching get_sites");
   RFLBM_CUDA(cudaMemcpyAsync(f, dout, bytes_out, cudaMemcpyDeviceToHost, h->stream), "copying site populations");
   return sync(h, "rflbm_get_sites");
+}
+
+static int ensure_diag_partials(rflbm* h, size_t bytes) {
+  if (h->diag_partials_bytes >= bytes) return RFLBM_OK;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->diag_partials);
+  h->diag_partials = nullptr;
+  h->diag_partials_bytes = 0;
+  RFLBM_CUDA(cudaMalloc((void**)&h->diag_partials, bytes), "allocating diagnostics scratch");
+  h->diag_partials_bytes = bytes;
+  return RFLBM_OK;
+}
+
+int rflbm_mode_sums(rflbm_t* h, double* sum, double* sumsq) {
+  if (int e = check_ready(h)) return e;
+  if (!sum || !sumsq) return fail(RFLBM_EINVAL, "outputs are NULL");
+  DeviceGuard guard(h->device);
+  const int64_t rows = mode_sum_blocks(h->geo);
+  if (int e = ensure_diag_partials(h, sizeof(double) * (size_t)(rows + 1) * 2 * kQ)) return e;
+  double* out = h->diag_partials + rows * 2 * kQ;
+  RFLBM_CUDA(launch_mode_sums(h->geo, h->buf[h->cur], h->diag_partials, out, h->stream), "launching mode sums");
+  double host[2 * kQ];
+  RFLBM_CUDA(cudaMemcpyAsync(host, out, sizeof(host), cudaMemcpyDeviceToHost, h->stream), "copying mode sums");
+  if (int e = sync(h, "rflbm_mode_sums")) return e;
+  for (int k = 0; k < kQ; ++k) {
+    sum[k] = host[k];
+    sumsq[k] = host[kQ + k];
+  }
+  return RFLBM_OK;
+}
+
+int rflbm_shell_count(const rflbm_t* h) {
+  if (int e = check_handle(h)) return e;
+  const double L = (double)std::max(h->geo.nx, std::max(h->geo.ny, h->geo.nz));
+  return (int)std::llround(L * std::sqrt(3.0) / 2.0) + 1;
+}
+
+int rflbm_structure_factor(rflbm_t* h, int field, int nshell, double* s_sum, double* count) {
+  if (int e = check_ready(h)) return e;
+  if (field < RFLBM_FIELD_RHO || field > RFLBM_FIELD_PYZ) return fail(RFLBM_EINVAL, "unknown field %d", field);
+  if (nshell < 1 || nshell > 3072) return fail(RFLBM_EINVAL, "nshell must lie in [1, 3072] (got %d)", nshell);
+  if (!s_sum || !count) return fail(RFLBM_EINVAL, "outputs are NULL");
+  DeviceGuard guard(h->device);
+  const Geometry& g = h->geo;
+  const size_t nspec = (size_t)g.nz * g.ny * (g.nx / 2 + 1);
+  if (!h->fft_ready) {
+    RFLBM_CUDA(cudaMalloc((void**)&h->diag_field, sizeof(double) * g.n), "allocating the field buffer");
+    RFLBM_CUDA(cudaMalloc(&h->diag_spec, sizeof(cufftDoubleComplex) * nspec), "allocating the spectrum");
+    if (cufftPlan3d(&h->fft_plan, (int)g.nz, (int)g.ny, (int)g.nx, CUFFT_D2Z) != CUFFT_SUCCESS)
+      return fail(RFLBM_ECUDA, "cufftPlan3d failed for %u x %u x %u", g.nx, g.ny, g.nz);
+    h->fft_ready = true;
+  }
+  if (cufftSetStream(h->fft_plan, h->stream) != CUFFT_SUCCESS) return fail(RFLBM_ECUDA, "cufftSetStream failed");
+  const int blocks = std::max(1, std::min(4 * std::max(h->num_sms, 1), (int)((nspec + 255) / 256)));
+  if (int e = ensure_diag_partials(h, sizeof(double) * (size_t)(blocks + 1) * 2 * nshell)) return e;
+  double* out = h->diag_partials + (size_t)blocks * 2 * nshell;
+  RFLBM_CUDA(launch_field(g, h->buf[h->cur], field, h->diag_field, h->stream), "launching the field kernel");
+  if (cufftExecD2Z(h->fft_plan, h->diag_field, (cufftDoubleComplex*)h->diag_spec) != CUFFT_SUCCESS)
+    return fail(RFLBM_ECUDA, "cufftExecD2Z failed");
+  RFLBM_CUDA(launch_shell_bins(g, h->diag_spec, nshell, blocks, h->diag_partials, out, h->stream),
+             "launching the shell binning");
+  std::vector<double> host((size_t)2 * nshell);
+  RFLBM_CUDA(cudaMemcpyAsync(host.data(), out, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, h->stream),
+             "copying the shell sums");
+  if (int e = sync(h, "rflbm_structure_factor")) return e;
+  for (int n = 0; n < nshell; ++n) {
+    s_sum[n] = host[n];
+    count[n] = host[nshell + n];
+  }
+  return RFLBM_OK;
 }
 
 int64_t rflbm_state_bytes(const rflbm_t* h) {

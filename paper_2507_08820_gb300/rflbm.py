@@ -31,6 +31,7 @@ RFLBM_KERNEL_AUTO = 0
 RFLBM_KERNEL_GATHER = 1
 RFLBM_KERNEL_TMA = 2
 RFLBM_KERNEL_TMA_PERSISTENT = 3
+FIELDS = ("rho", "jx", "jy", "jz", "pxx", "pyy", "pzz", "pxy", "pxz", "pyz")
 
 
 class RflbmError(RuntimeError):
@@ -97,6 +98,9 @@ _sig = {
     "rflbm_philox4x32_10": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, C.c_int64]),
     "rflbm_site_normals": (C.c_int, [C.c_uint64, C.c_int64, C.c_uint32, _P, C.c_int64, _P]),
     "rflbm_stats_f32_noalloc": (C.c_int, [_P, C.c_int64, _P, C.POINTER(rflbm_stats_t)]),
+    "rflbm_mode_sums": (C.c_int, [_H, _P, _P]),
+    "rflbm_structure_factor": (C.c_int, [_H, C.c_int, C.c_int, _P, _P]),
+    "rflbm_shell_count": (C.c_int, [_H]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(lib, _name)
@@ -262,6 +266,27 @@ def rflbm_step_path(h):
     w = C.c_int()
     k = _check(lib.rflbm_step_path(h, C.byref(w)))
     return k, w.value
+
+
+def rflbm_mode_sums(h):
+    """(sum, sumsq): 27 doubles each, see include/rflbm.h."""
+    s1, s2 = np.zeros(27), np.zeros(27)
+    _check(lib.rflbm_mode_sums(h, s1.ctypes.data, s2.ctypes.data))
+    return s1, s2
+
+
+def rflbm_shell_count(h):
+    return _check(lib.rflbm_shell_count(h))
+
+
+def rflbm_structure_factor(h, field, nshell=None):
+    """(s_sum, count) per shell for field (index or name in FIELDS)."""
+    if isinstance(field, str):
+        field = FIELDS.index(field)
+    nshell = rflbm_shell_count(h) if nshell is None else nshell
+    s, c = np.zeros(nshell), np.zeros(nshell)
+    _check(lib.rflbm_structure_factor(h, int(field), int(nshell), s.ctypes.data, c.ctypes.data))
+    return s, c
 
 
 def rflbm_philox4x32_10(ctr, k0, k1):
