@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Reg-FLBM D3Q27 MLUPS + % HBM roofline, FP32 vs mixed at fixed FDT error"
-BYTES_PER_SITE_F32 = 216          # 27 float32 read + 27 float32 written per site update
+BYTES_PER_SITE = {"f32": 216, "f16": 108, "bf16": 108}  # 27 read + 27 written per site update
 FALLBACK_HBM_GBS = 6800.0
 PROFILES = os.path.join(ROOT, "profiles")
 
@@ -49,16 +49,22 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--kernel", choices=["auto", "gather", "tma", "persistent"], default="auto")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
     return ap.parse_args()
+
+
+STORAGE_NAME = {"f32": "float32", "f16": "float16", "bf16": "bfloat16"}
 
 
 def workload(args):
     e = args.edge
-    return {"workload": f"periodic {e}^3 Reg-FLBM D3Q27 thermal equilibrium, float32 "
-                        f"populations, tau {args.tau}, rho0 1, kT {args.kT:g}, seed 1, rest start",
+    nbytes = 2 * 27 * BYTES_PER_SITE[args.storage] // 54 * e ** 3
+    return {"workload": f"periodic {e}^3 Reg-FLBM D3Q27 thermal equilibrium, "
+                        f"{STORAGE_NAME[args.storage]} populations, tau {args.tau}, rho0 1, "
+                        f"kT {args.kT:g}, seed 1, rest start",
             "box": [e, e, e], "sites": e ** 3, "tau": args.tau, "kT": args.kT,
-            "storage": "f32 shifted by w_i rho0", "streaming": "pull, ping-pong",
-            "l2": f"inputs {2 * 27 * 4 * e ** 3 / 1e6:.0f} MB (two population buffers) > 129 MB L2, no flush",
+            "storage": f"{args.storage} shifted by w_i rho0", "streaming": "pull, ping-pong",
+            "l2": f"inputs {nbytes / 1e6:.0f} MB (two population buffers) > 129 MB L2, no flush",
             "parallelism": "replicas"}
 
 
@@ -263,9 +269,10 @@ def gb300_arm(args):
     stream = torch.cuda.Stream(device=dev)
     kernel = {"auto": R.RFLBM_KERNEL_AUTO, "gather": R.RFLBM_KERNEL_GATHER,
               "tma": R.RFLBM_KERNEL_TMA, "persistent": R.RFLBM_KERNEL_TMA_PERSISTENT}[args.kernel]
+    storage = {"f32": R.RFLBM_STORE_F32, "f16": R.RFLBM_STORE_F16, "bf16": R.RFLBM_STORE_BF16}
     box = R.Box(e, e, e, tau=args.tau, kT=args.kT, seed=1, replica=info.rank,
                 stream=stream.cuda_stream, torch_buffers=True, device=info.local_rank,
-                kernel=kernel)
+                kernel=kernel, storage=storage[args.storage])
     R.rflbm_init_rest(box.h)
     kind, path = R.rflbm_step_path(box.h)
     R.rflbm_step(box.h, args.warmup)
@@ -298,14 +305,24 @@ def gb300_arm(args):
 
     variants = {}
     if not args.no_variants and info.world == 1:
-        for name, kw in (("reg_lbm_kT0", dict(kT=0.0)),
-                         ("bgk_flbm", dict(kT=args.kT, model=R.RFLBM_MODEL_BGK))):
+        peak_v, _ = measured_peak()
+        st_main = storage[args.storage]
+        for name, kw, bps in (
+                ("reg_lbm_kT0", dict(kT=0.0, storage=st_main), BYTES_PER_SITE[args.storage]),
+                ("bgk_flbm", dict(kT=args.kT, model=R.RFLBM_MODEL_BGK, storage=st_main),
+                 BYTES_PER_SITE[args.storage]),
+                ("f16_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_F16), 108),
+                ("f16_reg_lbm_kT0", dict(kT=0.0, storage=R.RFLBM_STORE_F16), 108),
+                ("bf16_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_BF16), 108)):
             vb = R.Box(e, e, e, tau=args.tau, seed=1, stream=stream.cuda_stream, kernel=kernel, **kw)
             R.rflbm_init_rest(vb.h)
             R.rflbm_step(vb.h, 50)
             k = max(10, args.steps // 4)
             vms = time_steps(R, torch, vb, stream, k)
-            variants[name] = {"value": n * k / (vms * 1e-3) / 1e6, "unit": "MLUPS", "steps": k}
+            sites_s = n * k / (vms * 1e-3)
+            variants[name] = {"value": sites_s / 1e6, "unit": "MLUPS", "steps": k,
+                              "roofline_frac": bps * sites_s / 1e9 / peak_v,
+                              "bytes_per_site": bps}
             vb.close()
     box.close()
 
@@ -314,13 +331,13 @@ def gb300_arm(args):
         return 0
     value = info.world * n * args.steps / (ms_max * 1e-3) / 1e6
     per_launch_s = ms * 1e-3 / args.steps
-    achieved = BYTES_PER_SITE_F32 * n / per_launch_s / 1e9
+    achieved = BYTES_PER_SITE[args.storage] * n / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
     kname, kstem = kernel_name(kind, path, args.kT, 0)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(kstem, e),
                 "peak_source": f"hbm_gbs of {peak_kind}", "kernel": kname,
-                "algorithmic_bytes_per_launch": BYTES_PER_SITE_F32 * n}
+                "algorithmic_bytes_per_launch": BYTES_PER_SITE[args.storage] * n}
     cpu = None
     if not args.no_cpu_baseline:
         r = oracle_sample_rate(e, args.tau, args.kT, budget_s=15.0, steps=2)
@@ -331,7 +348,8 @@ def gb300_arm(args):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": info.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": workload(args), "roofline": roofline,
+        "storage_dtype": args.storage, "data": "synthetic", "config": workload(args),
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": info.world * n * k_e2e / e2e_s / 1e6, "unit": "MLUPS",
                 "h2d_bytes_per_step": 27 * 4 * n, "d2h_bytes_per_step": 6 * 8, "steps": k_e2e,

@@ -59,8 +59,15 @@ typedef enum {
   RFLBM_MODEL_BGK = 1    /* BGK-FLBM, Eq. 12 with the equilibrium of Eq. 26 (Sec. III) */
 } rflbm_model;
 
+/* Population storage. All formats hold g_i = f_i - w_i rho0 (the rest state is 0) and all
+ * arithmetic is float32. The 16-bit formats halve the bytes per site update (108 instead
+ * of 216); they store g_i * 2^e with one power of two per velocity class |c_i|^2 chosen so
+ * that the thermal amplitude sqrt(w_i rho0 max(kT, 1e-6) / cs2) is of order one, and they
+ * support the paper's configuration (omega_g = 1, local rho in Eq. 10) only. */
 typedef enum {
-  RFLBM_STORE_F32 = 0    /* populations stored as float32, shifted by w_i*rho0 */
+  RFLBM_STORE_F32 = 0,   /* float32 */
+  RFLBM_STORE_F16 = 1,   /* IEEE float16 (11-bit significand) */
+  RFLBM_STORE_BF16 = 2   /* bfloat16 (8-bit significand) */
 } rflbm_storage;
 
 typedef enum {

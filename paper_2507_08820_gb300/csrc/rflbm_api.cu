@@ -24,7 +24,9 @@ struct rflbm {
   int device = 0;
   int num_sms = 0;
   cudaStream_t stream = nullptr;
-  float* buf[2] = {nullptr, nullptr};
+  void* buf[2] = {nullptr, nullptr};
+  size_t elem = 4;             // bytes per stored population value
+  StoreScale ss{};             // 16-bit storage scales (ones for float32)
   bool own_buf = false;
   int cur = 0;            // buffer holding the current state
   int64_t step = 0;
@@ -103,7 +105,10 @@ int validate(const rflbm_config_t* c) {
     return fail(RFLBM_EINVAL, "omega_g must lie in (0, 2) (got %g)", c->omega_g);
   if (c->model != RFLBM_MODEL_REG && c->model != RFLBM_MODEL_BGK)
     return fail(RFLBM_EINVAL, "unknown model %d", c->model);
-  if (c->storage != RFLBM_STORE_F32) return fail(RFLBM_EINVAL, "unknown storage %d", c->storage);
+  if (c->storage != RFLBM_STORE_F32 && c->storage != RFLBM_STORE_F16 && c->storage != RFLBM_STORE_BF16)
+    return fail(RFLBM_EINVAL, "unknown storage %d", c->storage);
+  if (c->storage != RFLBM_STORE_F32 && (c->omega_g != 1.0 || c->phi_rho != RFLBM_PHI_LOCAL_RHO))
+    return fail(RFLBM_EINVAL, "16-bit storage supports omega_g = 1 and the local density in Eq. 10 only");
   if (c->phi_rho != RFLBM_PHI_LOCAL_RHO && c->phi_rho != RFLBM_PHI_RHO0)
     return fail(RFLBM_EINVAL, "unknown phi_rho option %d", c->phi_rho);
   if (c->kernel < RFLBM_KERNEL_AUTO || c->kernel > RFLBM_KERNEL_TMA_PERSISTENT)
@@ -135,6 +140,21 @@ void fill_collide_params(rflbm* h) {
   h->variant.noise = c.kT > 0.0;
   h->variant.ghost_neq = (c.model == RFLBM_MODEL_REG) && (og != 1.0);
   h->variant.phi_rho0 = c.phi_rho == RFLBM_PHI_RHO0;
+  h->variant.storage = c.storage == RFLBM_STORE_F16 ? kStoreF16 : (c.storage == RFLBM_STORE_BF16 ? kStoreBF16 : kStoreF32);
+  h->elem = storage_bytes(h->variant.storage);
+  // 16-bit storage: per velocity class a power of two that maps the thermal amplitude
+  // sqrt(w rho0 kT / cs2) of g_i to order one (a floor of kT = 1e-6 covers kT = 0)
+  const double wc[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
+  for (int k = 0; k < 4; ++k) {
+    if (h->variant.storage == kStoreF32) {
+      h->ss.scale[k] = h->ss.inv_scale[k] = 1.0f;
+    } else {
+      const double amp = std::sqrt(3.0 * wc[k] * c.rho0 * std::max(c.kT, 1e-6));
+      const int e = (int)std::lround(-std::log2(amp));
+      h->ss.scale[k] = std::ldexp(1.0f, e);
+      h->ss.inv_scale[k] = std::ldexp(1.0f, -e);
+    }
+  }
 }
 
 int ensure_staging(rflbm* h, size_t bytes) {
@@ -193,15 +213,19 @@ EncodeTiledFn encode_tiled_fn() {
   return fn;
 }
 
-// The population buffer as a 4-D float tensor (x, y, z, plane); box = (box_x, 1, 1, 1).
-bool encode_map(CUtensorMap* map, float* base, const Geometry& g, uint32_t box_x) {
+// The population buffer as a 4-D tensor (x, y, z, plane); box = (box_x, 1, 1, 1).
+bool encode_map(CUtensorMap* map, void* base, const Geometry& g, uint32_t box_x, int storage) {
   EncodeTiledFn fn = encode_tiled_fn();
   if (!fn) return false;
+  const cuuint64_t e = storage_bytes(storage);
   const cuuint64_t dims[4] = {g.nx, g.ny, g.nz, (cuuint64_t)kQ};
-  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.nxy * 4, (cuuint64_t)g.ps * 4};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * e, (cuuint64_t)g.nxy * e, (cuuint64_t)g.ps * e};
   const cuuint32_t box[4] = {box_x, 1, 1, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+  const CUtensorMapDataType dt = storage == kStoreF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : storage == kStoreBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return fn(map, dt, 4, base, dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -212,13 +236,17 @@ void setup_tma(rflbm* h) {
   h->kernel = RFLBM_KERNEL_GATHER;
   const int w = tma_segment_width(h->geo.nx);
   if (w == 0 || h->cfg.kernel == RFLBM_KERNEL_GATHER) return;
+  const int st = h->variant.storage;
+  const uint32_t halo = st == kStoreF32 ? 4 : 8;  // 16 bytes each side
   for (int b = 0; b < 2; ++b) {
-    if (!encode_map(&h->load_map[b], h->buf[b], h->geo, (uint32_t)w + 8) ||
-        !encode_map(&h->store_map[b], h->buf[b], h->geo, (uint32_t)w))
+    if (!encode_map(&h->load_map[b], h->buf[b], h->geo, (uint32_t)w + 2 * halo, st) ||
+        !encode_map(&h->store_map[b], h->buf[b], h->geo, (uint32_t)w, st))
       return;
   }
   h->tma_width = w;
-  h->kernel = h->cfg.kernel == RFLBM_KERNEL_TMA_PERSISTENT ? RFLBM_KERNEL_TMA_PERSISTENT : RFLBM_KERNEL_TMA;
+  // the persistent kernel exists for float32 storage only
+  h->kernel = (h->cfg.kernel == RFLBM_KERNEL_TMA_PERSISTENT && st == kStoreF32) ? RFLBM_KERNEL_TMA_PERSISTENT
+                                                                                 : RFLBM_KERNEL_TMA;
 }
 
 int64_t n_sites(const rflbm* h) { return (int64_t)h->geo.n; }
@@ -253,7 +281,7 @@ void rflbm_config_default(rflbm_config_t* cfg) {
 int64_t rflbm_buffer_bytes(const rflbm_config_t* cfg) {
   if (int e = validate(cfg)) return e;
   const int64_t n = (int64_t)cfg->nx * cfg->ny * cfg->nz;
-  return plane_stride(n) * kQ * (int64_t)sizeof(float);
+  return plane_stride(n) * kQ * (int64_t)(cfg->storage == RFLBM_STORE_F32 ? 4 : 2);
 }
 
 const char* rflbm_last_error(void) { return g_error.c_str(); }
@@ -295,7 +323,7 @@ rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
   g.div_nxy = make_fastdiv(g.nxy);
   fill_collide_params(h);
 
-  const size_t bytes = (size_t)g.ps * kQ * sizeof(float);
+  const size_t bytes = (size_t)g.ps * kQ * h->elem;
   if (cfg->buffers[0] || cfg->buffers[1]) {
     if (!cfg->buffers[0] || !cfg->buffers[1] ||
         ((uintptr_t)cfg->buffers[0] % 256) || ((uintptr_t)cfg->buffers[1] % 256)) {
@@ -303,13 +331,13 @@ rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
       delete h;
       return nullptr;
     }
-    h->buf[0] = (float*)cfg->buffers[0];
-    h->buf[1] = (float*)cfg->buffers[1];
+    h->buf[0] = cfg->buffers[0];
+    h->buf[1] = cfg->buffers[1];
     h->own_buf = false;
   } else {
     h->own_buf = true;
     for (int b = 0; b < 2; ++b) {
-      e = cudaMalloc((void**)&h->buf[b], bytes);
+      e = cudaMalloc(&h->buf[b], bytes);
       if (e != cudaSuccess) {
         cuda_fail(e, "allocating a population buffer");
         rflbm_destroy(h);
@@ -370,7 +398,7 @@ int rflbm_init_rest(rflbm_t* h) {
   if (int e = check_handle(h)) return e;
   DeviceGuard guard(h->device);
   // the shifted rest state is all zeros
-  RFLBM_CUDA(cudaMemsetAsync(h->buf[0], 0, (size_t)h->geo.ps * kQ * sizeof(float), h->stream),
+  RFLBM_CUDA(cudaMemsetAsync(h->buf[0], 0, (size_t)h->geo.ps * kQ * h->elem, h->stream),
              "clearing the populations");
   h->cur = 0;
   h->step = 0;
@@ -396,7 +424,8 @@ int rflbm_init_field(rflbm_t* h, const double* rho, const double* u, int on_devi
       du = st + n;
     }
   }
-  RFLBM_CUDA(launch_init_field(h->geo, h->cp.rho0, drho, du, h->buf[0], h->stream), "launching init_field");
+  RFLBM_CUDA(launch_init_field(h->geo, h->cp.rho0, h->ss, h->variant.storage, drho, du, h->buf[0], h->stream),
+             "launching init_field");
   h->cur = 0;
   h->step = 0;
   h->initialised = true;
@@ -411,6 +440,7 @@ int rflbm_step(rflbm_t* h, int64_t n) {
   StepParams p;
   p.geo = h->geo;
   p.cp = h->cp;
+  p.ss = h->ss;
   p.key0 = (uint32_t)(h->cfg.seed & 0xffffffffu);
   p.key1 = (uint32_t)(h->cfg.seed >> 32);
   p.replica = h->cfg.replica;
@@ -423,9 +453,9 @@ int rflbm_step(rflbm_t* h, int64_t n) {
     if (h->tma_width) {
       const TmaMaps m{&h->load_map[h->cur], &h->store_map[1 - h->cur], h->tma_width,
                       h->kernel == RFLBM_KERNEL_TMA_PERSISTENT ? h->num_sms : 0};
-      e = launch_step_tma_f32(m, p, h->variant, h->stream);
+      e = launch_step_tma(m, p, h->variant, h->stream);
     } else {
-      e = launch_step_f32(p, h->variant, h->stream);
+      e = launch_step_gather(p, h->variant, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "launching the step kernel");
     h->cur = 1 - h->cur;
@@ -446,7 +476,8 @@ int rflbm_moments(rflbm_t* h, double* rho, double* u, double* pi, int on_device)
     du = u ? st + n : nullptr;
     dpi = pi ? st + 4 * n : nullptr;
   }
-  RFLBM_CUDA(launch_moments(h->geo, h->cp.rho0, h->buf[h->cur], drho, du, dpi, h->stream), "launching moments");
+  RFLBM_CUDA(launch_moments(h->geo, h->cp.rho0, h->ss, h->variant.storage, h->buf[h->cur], drho, du, dpi, h->stream),
+             "launching moments");
   if (!on_device) {
     if (rho) RFLBM_CUDA(cudaMemcpyAsync(rho, drho, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream), "copying rho");
     if (u) RFLBM_CUDA(cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream), "copying u");
@@ -460,7 +491,8 @@ int rflbm_stats(rflbm_t* h, rflbm_stats_t* out) {
   if (!out) return fail(RFLBM_EINVAL, "stats output is NULL");
   DeviceGuard guard(h->device);
   double* res = h->partials + (size_t)h->stat_blocks * kStatOutFields;
-  RFLBM_CUDA(launch_stats(h->geo, h->cp.rho0, h->buf[h->cur], h->partials, h->stat_blocks, res, h->stream),
+  RFLBM_CUDA(launch_stats(h->geo, h->cp.rho0, h->ss, h->variant.storage, h->buf[h->cur], h->partials,
+                          h->stat_blocks, res, h->stream),
              "launching stats");
   double host[kStatOutFields];
   RFLBM_CUDA(cudaMemcpyAsync(host, res, sizeof(host), cudaMemcpyDeviceToHost, h->stream), "copying stats");
@@ -489,8 +521,9 @@ static int get_pops(rflbm_t* h, void* f, int on_device, bool f64) {
     if (int e = ensure_staging(h, bytes)) return e;
     dst = h->staging;
   }
-  cudaError_t e = f64 ? launch_get_populations_f64(h->geo, h->cp.rho0, h->buf[h->cur], (double*)dst, h->stream)
-                      : launch_get_populations_f32(h->geo, h->cp.rho0, h->buf[h->cur], (float*)dst, h->stream);
+  const int st = h->variant.storage;
+  cudaError_t e = f64 ? launch_get_populations_f64(h->geo, h->cp.rho0, h->ss, st, h->buf[h->cur], (double*)dst, h->stream)
+                      : launch_get_populations_f32(h->geo, h->cp.rho0, h->ss, st, h->buf[h->cur], (float*)dst, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "launching get_populations");
   if (!on_device) RFLBM_CUDA(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, h->stream), "copying populations");
   return sync(h, "rflbm_get_populations");
@@ -509,8 +542,9 @@ static int set_pops(rflbm_t* h, const void* f, int on_device, bool f64) {
     src = h->staging;
   }
   // the state after this call is step h->step, held in buffer 0
-  cudaError_t e = f64 ? launch_set_populations_f64(h->geo, h->cp.rho0, (const double*)src, h->buf[0], h->stream)
-                      : launch_set_populations_f32(h->geo, h->cp.rho0, (const float*)src, h->buf[0], h->stream);
+  const int st = h->variant.storage;
+  cudaError_t e = f64 ? launch_set_populations_f64(h->geo, h->cp.rho0, h->ss, st, (const double*)src, h->buf[0], h->stream)
+                      : launch_set_populations_f32(h->geo, h->cp.rho0, h->ss, st, (const float*)src, h->buf[0], h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "launching set_populations");
   h->cur = 0;
   h->initialised = true;
@@ -536,7 +570,8 @@ int rflbm_get_sites(rflbm_t* h, const int64_t* sites, int64_t n, double* f) {
   int64_t* dsites = (int64_t*)h->staging;
   double* dout = (double*)((char*)h->staging + bytes_sites);
   RFLBM_CUDA(cudaMemcpyAsync(dsites, sites, bytes_sites, cudaMemcpyHostToDevice, h->stream), "copying sites");
-  RFLBM_CUDA(launch_get_sites(h->geo, h->cp.rho0, h->buf[h->cur], dsites, n, dout, h->stream), "launching get_sites");
+  RFLBM_CUDA(launch_get_sites(h->geo, h->cp.rho0, h->ss, h->variant.storage, h->buf[h->cur], dsites, n, dout, h->stream),
+             "launching get_sites");
   RFLBM_CUDA(cudaMemcpyAsync(f, dout, bytes_out, cudaMemcpyDeviceToHost, h->stream), "copying site populations");
   return sync(h, "rflbm_get_sites");
 }
@@ -559,7 +594,8 @@ int rflbm_mode_sums(rflbm_t* h, double* sum, double* sumsq) {
   const int64_t rows = mode_sum_blocks(h->geo);
   if (int e = ensure_diag_partials(h, sizeof(double) * (size_t)(rows + 1) * 2 * kQ)) return e;
   double* out = h->diag_partials + rows * 2 * kQ;
-  RFLBM_CUDA(launch_mode_sums(h->geo, h->buf[h->cur], h->diag_partials, out, h->stream), "launching mode sums");
+  RFLBM_CUDA(launch_mode_sums(h->geo, h->ss, h->variant.storage, h->buf[h->cur], h->diag_partials, out, h->stream),
+             "launching mode sums");
   double host[2 * kQ];
   RFLBM_CUDA(cudaMemcpyAsync(host, out, sizeof(host), cudaMemcpyDeviceToHost, h->stream), "copying mode sums");
   if (int e = sync(h, "rflbm_mode_sums")) return e;
@@ -595,7 +631,8 @@ int rflbm_structure_factor(rflbm_t* h, int field, int nshell, double* s_sum, dou
   const int blocks = std::max(1, std::min(4 * std::max(h->num_sms, 1), (int)((nspec + 255) / 256)));
   if (int e = ensure_diag_partials(h, sizeof(double) * (size_t)(blocks + 1) * 2 * nshell)) return e;
   double* out = h->diag_partials + (size_t)blocks * 2 * nshell;
-  RFLBM_CUDA(launch_field(g, h->buf[h->cur], field, h->diag_field, h->stream), "launching the field kernel");
+  RFLBM_CUDA(launch_field(g, h->ss, h->variant.storage, h->buf[h->cur], field, h->diag_field, h->stream),
+             "launching the field kernel");
   if (cufftExecD2Z(h->fft_plan, h->diag_field, (cufftDoubleComplex*)h->diag_spec) != CUFFT_SUCCESS)
     return fail(RFLBM_ECUDA, "cufftExecD2Z failed");
   RFLBM_CUDA(launch_shell_bins(g, h->diag_spec, nshell, blocks, h->diag_partials, out, h->stream),
@@ -613,7 +650,7 @@ int rflbm_structure_factor(rflbm_t* h, int field, int nshell, double* s_sum, dou
 
 int64_t rflbm_state_bytes(const rflbm_t* h) {
   if (int e = check_handle(h)) return e;
-  return h->geo.ps * kQ * (int64_t)sizeof(float);
+  return h->geo.ps * kQ * (int64_t)h->elem;
 }
 
 int rflbm_save_state(rflbm_t* h, void* image, int on_device) {

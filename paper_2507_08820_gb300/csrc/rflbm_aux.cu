@@ -1,12 +1,12 @@
 // Kernels around the step: initial states, population import/export in the pull layout,
-// FP64 moments and global diagnostics, and the noise-source test kernels.
+// FP64 moments and global diagnostics, and the noise-source test kernels. Every kernel
+// that touches the populations is instantiated for the three storage formats.
 #include "rflbm_aux.h"
 
 namespace rflbm_dev {
 
 constexpr int kAuxBlock = 256;
 
-// ---------------------------------------------------------------- helpers
 __device__ __forceinline__ uint32_t site_of(int64_t t) { return (uint32_t)t; }
 
 // One 1-D factor of the product-form equilibrium (Eq. 26 factorised over the axes):
@@ -16,8 +16,10 @@ __device__ __forceinline__ double psi(int c, double u) {
 }
 
 // ---------------------------------------------------------------- initial states
-__global__ void k_init_field(Geometry g, float rho0, const double* __restrict__ rho,
-                             const double* __restrict__ u, float* __restrict__ dst) {
+template <int kStore>
+__global__ void k_init_field(Geometry g, float rho0, StoreScale ss, const double* __restrict__ rho,
+                             const double* __restrict__ u, typename Storage<kStore>::T* __restrict__ dst) {
+  using S = Storage<kStore>;
   const int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
   if (s >= g.n) return;
   const double r = rho ? rho[s] : (double)rho0;
@@ -27,73 +29,96 @@ __global__ void k_init_field(Geometry g, float rho0, const double* __restrict__ 
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const double f = r * psi(cx_of(i), ux) * psi(cy_of(i), uy) * psi(cz_of(i), uz);
-    dst[i * g.ps + pull_site(nb, i)] = (float)(f - weight_of(i) * (double)rho0);
+    dst[i * g.ps + pull_site(nb, i)] = S::store((float)(f - weight_of(i) * (double)rho0), class_of(i), ss);
   }
 }
 
-template <class T>
-__global__ void k_set_populations(Geometry g, float rho0, const T* __restrict__ f,
-                                  float* __restrict__ dst) {
+// Import of public-layout populations (double: exact shift in FP64; float: in FP32).
+template <class Tin, int kStore>
+__global__ void k_set_populations(Geometry g, float rho0, StoreScale ss, const Tin* __restrict__ f,
+                                  typename Storage<kStore>::T* __restrict__ dst) {
+  using S = Storage<kStore>;
   const int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
   if (s >= g.n) return;
   const Neighbours nb = neighbours(site_of(s), g);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const double v = (double)f[i * (int64_t)g.n + s] - weight_of(i) * (double)rho0;
-    dst[i * g.ps + pull_site(nb, i)] = (float)v;
+    const Tin v = f[i * (int64_t)g.n + s] - (Tin)(weight_of(i) * (double)rho0);
+    dst[i * g.ps + pull_site(nb, i)] = S::store((float)v, class_of(i), ss);
   }
 }
 
-template <class T>
-__global__ void k_get_populations(Geometry g, float rho0, const float* __restrict__ src,
-                                  T* __restrict__ f) {
+template <class Tout, int kStore>
+__global__ void k_get_populations(Geometry g, float rho0, StoreScale ss,
+                                  const typename Storage<kStore>::T* __restrict__ src, Tout* __restrict__ f) {
+  using S = Storage<kStore>;
   const int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
   if (s >= g.n) return;
   const Neighbours nb = neighbours(site_of(s), g);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    f[i * (int64_t)g.n + s] = (T)((double)src[i * g.ps + pull_site(nb, i)] + weight_of(i) * (double)rho0);
+    const float v = S::load(src[i * g.ps + pull_site(nb, i)], class_of(i), ss);
+    f[i * (int64_t)g.n + s] = (Tout)v + (Tout)(weight_of(i) * (double)rho0);
   }
 }
 
-__global__ void k_get_sites(Geometry g, float rho0, const float* __restrict__ src,
-                            const int64_t* __restrict__ sites, int64_t n,
-                            double* __restrict__ f) {
+template <int kStore>
+__global__ void k_get_sites(Geometry g, float rho0, StoreScale ss,
+                            const typename Storage<kStore>::T* __restrict__ src,
+                            const int64_t* __restrict__ sites, int64_t n, double* __restrict__ f) {
+  using S = Storage<kStore>;
   const int64_t j = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
   if (j >= n) return;
   const Neighbours nb = neighbours(site_of(sites[j]), g);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    f[i * n + j] = (double)src[i * g.ps + pull_site(nb, i)] + weight_of(i) * (double)rho0;
+    f[i * n + j] = (double)S::load(src[i * g.ps + pull_site(nb, i)], class_of(i), ss) +
+                   weight_of(i) * (double)rho0;
   }
 }
 
-// Raw moments of order <= 2 of the shifted populations of one site, in FP64.
+// Raw moments of order <= 2 of the shifted populations of one site, summed in Acc
+// (double for the moments export; float for the global diagnostics, whose values are of
+// order sqrt(kT) because the rest state is subtracted), returned in FP64.
 struct SiteMoments {
   double drho, j[3], s[6];  // s: sum g c_a c_b for xx, yy, zz, xy, xz, yz
 };
 
-__device__ __forceinline__ SiteMoments site_moments(const Neighbours& nb, const float* src,
-                                                    int64_t ps) {
-  SiteMoments m = {};
+template <int kStore, class Acc>
+__device__ __forceinline__ SiteMoments site_moments(const Neighbours& nb,
+                                                    const typename Storage<kStore>::T* src,
+                                                    int64_t ps, const StoreScale& ss) {
+  using S = Storage<kStore>;
+  Acc drho = 0, j0 = 0, j1 = 0, j2 = 0, s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const double v = (double)src[i * ps + pull_site(nb, i)];
+    const Acc v = (Acc)S::load(src[i * ps + pull_site(nb, i)], class_of(i), ss);
     const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-    m.drho += v;
-    m.j[0] += cx * v; m.j[1] += cy * v; m.j[2] += cz * v;
-    m.s[0] += cx * cx * v; m.s[1] += cy * cy * v; m.s[2] += cz * cz * v;
-    m.s[3] += cx * cy * v; m.s[4] += cx * cz * v; m.s[5] += cy * cz * v;
+    drho += v;
+    if (cx) j0 += cx * v;
+    if (cy) j1 += cy * v;
+    if (cz) j2 += cz * v;
+    if (cx) s0 += v;
+    if (cy) s1 += v;
+    if (cz) s2 += v;
+    if (cx * cy) s3 += cx * cy * v;
+    if (cx * cz) s4 += cx * cz * v;
+    if (cy * cz) s5 += cy * cz * v;
   }
+  SiteMoments m;
+  m.drho = drho;
+  m.j[0] = j0; m.j[1] = j1; m.j[2] = j2;
+  m.s[0] = s0; m.s[1] = s1; m.s[2] = s2; m.s[3] = s3; m.s[4] = s4; m.s[5] = s5;
   return m;
 }
 
-__global__ void k_moments(Geometry g, float rho0, const float* __restrict__ src,
-                          double* __restrict__ rho, double* __restrict__ u,
-                          double* __restrict__ pi) {
+template <int kStore>
+__global__ void k_moments(Geometry g, float rho0, StoreScale ss,
+                          const typename Storage<kStore>::T* __restrict__ src,
+                          double* __restrict__ rho, double* __restrict__ u, double* __restrict__ pi) {
   const int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
   if (s >= g.n) return;
-  const SiteMoments m = site_moments(neighbours(site_of(s), g), src, g.ps);
+  const SiteMoments m = site_moments<kStore, double>(neighbours(site_of(s), g), src, g.ps, ss);
   const double r = (double)rho0 + m.drho;
   if (rho) rho[s] = r;
   if (u) {
@@ -122,20 +147,22 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-__global__ void k_stats_partial(Geometry g, float rho0, const float* __restrict__ src,
+template <int kStore>
+__global__ void k_stats_partial(Geometry g, float rho0, StoreScale ss,
+                                const typename Storage<kStore>::T* __restrict__ src,
                                 double* __restrict__ partials) {
   double acc[kStatFields] = {0, 0, 0, 0, 0, 0};
   for (int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x; s < g.n;
        s += (int64_t)gridDim.x * kAuxBlock) {
-    const SiteMoments m = site_moments(neighbours(site_of(s), g), src, g.ps);
+    const SiteMoments m = site_moments<kStore, float>(neighbours(site_of(s), g), src, g.ps, ss);
     const double r = (double)rho0 + m.drho;
     const bool finite = isfinite(m.drho) && isfinite(m.j[0]) && isfinite(m.j[1]) &&
                         isfinite(m.j[2]);
     if (finite) {
       acc[0] += m.drho;
       acc[1] += m.j[0]; acc[2] += m.j[1]; acc[3] += m.j[2];
-      const double sp = sqrt(m.j[0] * m.j[0] + m.j[1] * m.j[1] + m.j[2] * m.j[2]) / fabs(r);
-      acc[4] = fmax(acc[4], sp);
+      const float sp = sqrtf((float)(m.j[0] * m.j[0] + m.j[1] * m.j[1] + m.j[2] * m.j[2])) / fabsf((float)r);
+      acc[4] = fmax(acc[4], (double)sp);
     } else {
       acc[5] += 1.0;
     }
@@ -156,18 +183,17 @@ __global__ void k_stats_partial(Geometry g, float rho0, const float* __restrict_
   }
 }
 
-// Fixed-order final reduction of the partials (deterministic for a fixed grid).
+// Fixed-order final reduction (one warp per field; deterministic for a fixed grid).
 __global__ void k_stats_final(const double* __restrict__ partials, int nblocks,
                               double* __restrict__ out) {
-  if (threadIdx.x < kStatFields) {
-    const int f = threadIdx.x;
-    double v = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-      const double p = partials[(int64_t)b * kStatFields + f];
-      v = (f == 4) ? fmax(v, p) : v + p;
-    }
-    out[f] = v;
+  const int f = blockIdx.x;
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 32) {
+    const double p = partials[(int64_t)b * kStatFields + f];
+    v = (f == 4) ? fmax(v, p) : v + p;
   }
+  v = (f == 4) ? warp_max(v) : warp_sum(v);
+  if (threadIdx.x == 0) out[f] = v;
 }
 
 // ---------------------------------------------------------------- noise tests
@@ -193,39 +219,51 @@ __global__ void k_site_normals(uint32_t k0, uint32_t k1, uint32_t step, uint32_t
 // ---------------------------------------------------------------- launchers
 static unsigned blocks_for(int64_t n) { return (unsigned)((n + kAuxBlock - 1) / kAuxBlock); }
 
-cudaError_t launch_init_field(const Geometry& g, float rho0, const double* rho, const double* u,
-                              float* dst, cudaStream_t st) {
-  k_init_field<<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, rho, u, dst);
+#define RFLBM_STORE_DISPATCH(kind, CALL)                                   \
+  switch (kind) {                                                          \
+    case kStoreF32: { constexpr int K = kStoreF32; CALL; } break;          \
+    case kStoreF16: { constexpr int K = kStoreF16; CALL; } break;          \
+    case kStoreBF16: { constexpr int K = kStoreBF16; CALL; } break;        \
+    default: return cudaErrorInvalidValue;                                 \
+  }
+
+template <int K>
+using ST = typename Storage<K>::T;
+
+cudaError_t launch_init_field(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                              const double* rho, const double* u, void* dst, cudaStream_t st) {
+  RFLBM_STORE_DISPATCH(kind, (k_init_field<K><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, ss, rho, u, (ST<K>*)dst)));
   return cudaGetLastError();
 }
-cudaError_t launch_set_populations_f64(const Geometry& g, float rho0, const double* f, float* dst,
-                                       cudaStream_t st) {
-  k_set_populations<double><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, f, dst);
+cudaError_t launch_set_populations_f64(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                                       const double* f, void* dst, cudaStream_t st) {
+  RFLBM_STORE_DISPATCH(kind, (k_set_populations<double, K><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, ss, f, (ST<K>*)dst)));
   return cudaGetLastError();
 }
-cudaError_t launch_set_populations_f32(const Geometry& g, float rho0, const float* f, float* dst,
-                                       cudaStream_t st) {
-  k_set_populations<float><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, f, dst);
+cudaError_t launch_set_populations_f32(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                                       const float* f, void* dst, cudaStream_t st) {
+  RFLBM_STORE_DISPATCH(kind, (k_set_populations<float, K><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, ss, f, (ST<K>*)dst)));
   return cudaGetLastError();
 }
-cudaError_t launch_get_populations_f64(const Geometry& g, float rho0, const float* src, double* f,
-                                       cudaStream_t st) {
-  k_get_populations<double><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, src, f);
+cudaError_t launch_get_populations_f64(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                                       const void* src, double* f, cudaStream_t st) {
+  RFLBM_STORE_DISPATCH(kind, (k_get_populations<double, K><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, ss, (const ST<K>*)src, f)));
   return cudaGetLastError();
 }
-cudaError_t launch_get_populations_f32(const Geometry& g, float rho0, const float* src, float* f,
-                                       cudaStream_t st) {
-  k_get_populations<float><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, src, f);
+cudaError_t launch_get_populations_f32(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                                       const void* src, float* f, cudaStream_t st) {
+  RFLBM_STORE_DISPATCH(kind, (k_get_populations<float, K><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, ss, (const ST<K>*)src, f)));
   return cudaGetLastError();
 }
-cudaError_t launch_get_sites(const Geometry& g, float rho0, const float* src, const int64_t* sites,
-                             int64_t n, double* f, cudaStream_t st) {
-  k_get_sites<<<blocks_for(n), kAuxBlock, 0, st>>>(g, rho0, src, sites, n, f);
+cudaError_t launch_get_sites(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                             const void* src, const int64_t* sites, int64_t n, double* f,
+                             cudaStream_t st) {
+  RFLBM_STORE_DISPATCH(kind, (k_get_sites<K><<<blocks_for(n), kAuxBlock, 0, st>>>(g, rho0, ss, (const ST<K>*)src, sites, n, f)));
   return cudaGetLastError();
 }
-cudaError_t launch_moments(const Geometry& g, float rho0, const float* src, double* rho,
-                           double* u, double* pi, cudaStream_t st) {
-  k_moments<<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, src, rho, u, pi);
+cudaError_t launch_moments(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                           const void* src, double* rho, double* u, double* pi, cudaStream_t st) {
+  RFLBM_STORE_DISPATCH(kind, (k_moments<K><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, ss, (const ST<K>*)src, rho, u, pi)));
   return cudaGetLastError();
 }
 int stats_partial_blocks(const Geometry& g, int num_sms) {
@@ -233,10 +271,11 @@ int stats_partial_blocks(const Geometry& g, int num_sms) {
   const int64_t cap = 4 * (int64_t)num_sms;
   return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
-cudaError_t launch_stats(const Geometry& g, float rho0, const float* src, double* partials,
-                         int nblocks, double* out6, cudaStream_t st) {
-  k_stats_partial<<<nblocks, kAuxBlock, 0, st>>>(g, rho0, src, partials);
-  k_stats_final<<<1, 32, 0, st>>>(partials, nblocks, out6);
+cudaError_t launch_stats(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                         const void* src, double* partials, int nblocks, double* out6,
+                         cudaStream_t st) {
+  RFLBM_STORE_DISPATCH(kind, (k_stats_partial<K><<<nblocks, kAuxBlock, 0, st>>>(g, rho0, ss, (const ST<K>*)src, partials)));
+  k_stats_final<<<kStatFields, 32, 0, st>>>(partials, nblocks, out6);
   return cudaGetLastError();
 }
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,

@@ -1,4 +1,5 @@
-// Launchers of the auxiliary kernels (rflbm_aux.cu).
+// Launchers of the auxiliary kernels (rflbm_aux.cu). `kind` is the storage format
+// (kStoreF32 / kStoreF16 / kStoreBF16) of the population buffer `src` / `dst`.
 #pragma once
 
 #include "rflbm_internal.h"
@@ -7,25 +8,27 @@ namespace rflbm_dev {
 
 constexpr int kStatOutFields = 6;  // drho sum, momentum (3), max |u|, non-finite count
 
-cudaError_t launch_init_field(const Geometry& g, float rho0, const double* rho, const double* u,
-                              float* dst, cudaStream_t st);
-cudaError_t launch_set_populations_f64(const Geometry& g, float rho0, const double* f, float* dst,
-                                       cudaStream_t st);
-cudaError_t launch_set_populations_f32(const Geometry& g, float rho0, const float* f, float* dst,
-                                       cudaStream_t st);
-cudaError_t launch_get_populations_f64(const Geometry& g, float rho0, const float* src, double* f,
-                                       cudaStream_t st);
-cudaError_t launch_get_populations_f32(const Geometry& g, float rho0, const float* src, float* f,
-                                       cudaStream_t st);
-cudaError_t launch_get_sites(const Geometry& g, float rho0, const float* src, const int64_t* sites,
-                             int64_t n, double* f, cudaStream_t st);
-cudaError_t launch_moments(const Geometry& g, float rho0, const float* src, double* rho,
-                           double* u, double* pi, cudaStream_t st);
+cudaError_t launch_init_field(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                              const double* rho, const double* u, void* dst, cudaStream_t st);
+cudaError_t launch_set_populations_f64(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                                       const double* f, void* dst, cudaStream_t st);
+cudaError_t launch_set_populations_f32(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                                       const float* f, void* dst, cudaStream_t st);
+cudaError_t launch_get_populations_f64(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                                       const void* src, double* f, cudaStream_t st);
+cudaError_t launch_get_populations_f32(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                                       const void* src, float* f, cudaStream_t st);
+cudaError_t launch_get_sites(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                             const void* src, const int64_t* sites, int64_t n, double* f,
+                             cudaStream_t st);
+cudaError_t launch_moments(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                           const void* src, double* rho, double* u, double* pi, cudaStream_t st);
 // Number of partial sums (blocks) the stats reduction uses for a box on a GPU with
 // num_sms multiprocessors; the scratch buffer holds kStatOutFields doubles per block.
 int stats_partial_blocks(const Geometry& g, int num_sms);
-cudaError_t launch_stats(const Geometry& g, float rho0, const float* src, double* partials,
-                         int nblocks, double* out6, cudaStream_t st);
+cudaError_t launch_stats(const Geometry& g, float rho0, const StoreScale& ss, int kind,
+                         const void* src, double* partials, int nblocks, double* out6,
+                         cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                           int64_t n, cudaStream_t st);
 cudaError_t launch_site_normals(uint32_t k0, uint32_t k1, uint32_t step, uint32_t replica,

@@ -43,17 +43,22 @@ __device__ __forceinline__ void all_moments(const float (&G)[3][3][3], float (&M
     }
 }
 
-__device__ __forceinline__ void gather_tile(const float* __restrict__ src, const Geometry& g,
-                                            uint32_t s, float (&G)[3][3][3]) {
+template <int kStore>
+__device__ __forceinline__ void gather_tile(const typename Storage<kStore>::T* __restrict__ src,
+                                            const Geometry& g, const StoreScale& ss, uint32_t s,
+                                            float (&G)[3][3][3]) {
   const Neighbours nb = neighbours(s, g);
 #pragma unroll
   for (int i = 0; i < kQ; ++i)
-    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = __ldg(src + i * g.ps + pull_site(nb, i));
+    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] =
+        Storage<kStore>::load(src[i * g.ps + pull_site(nb, i)], class_of(i), ss);
 }
 
 // Each thread accumulates up to kDiagSitesPerThread sites in float32, then the block sums
 // its 54 values in FP64 into one partial slot.
-__global__ void __launch_bounds__(kDiagBlock) k_mode_sums(Geometry g, const float* __restrict__ src,
+template <int kStore>
+__global__ void __launch_bounds__(kDiagBlock) k_mode_sums(Geometry g, StoreScale ss,
+                                                          const typename Storage<kStore>::T* __restrict__ src,
                                                           double* __restrict__ partials) {
   float acc[2 * kQ];
 #pragma unroll
@@ -63,7 +68,7 @@ __global__ void __launch_bounds__(kDiagBlock) k_mode_sums(Geometry g, const floa
     const int64_t s = base + (int64_t)j * kDiagBlock + threadIdx.x;
     if (s >= g.n) break;
     float G[3][3][3], M[3][3][3];
-    gather_tile(src, g, (uint32_t)s, G);
+    gather_tile<kStore>(src, g, ss, (uint32_t)s, G);
     all_moments(G, M);
 #pragma unroll
     for (int p = 0; p < 3; ++p)
@@ -106,15 +111,16 @@ __global__ void k_reduce_columns(const double* __restrict__ partials, int64_t ro
 
 // Field value of one site, FP64 output from float32 sums of the shifted populations:
 // 0 rho - rho0, 1..3 rho u, 4..9 Pi = a^(2) (xx, yy, zz, xy, xz, yz).
-__global__ void k_field(Geometry g, const float* __restrict__ src, int field,
-                        double* __restrict__ out) {
+template <int kStore>
+__global__ void k_field(Geometry g, StoreScale ss, const typename Storage<kStore>::T* __restrict__ src,
+                        int field, double* __restrict__ out) {
   const int64_t s = (int64_t)blockIdx.x * kDiagBlock + threadIdx.x;
   if (s >= g.n) return;
   const Neighbours nb = neighbours((uint32_t)s, g);
   float v = 0.0f, drho = 0.0f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const float x = __ldg(src + i * g.ps + pull_site(nb, i));
+    const float x = Storage<kStore>::load(src[i * g.ps + pull_site(nb, i)], class_of(i), ss);
     const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     float w;
     switch (field) {
@@ -175,17 +181,31 @@ int64_t mode_sum_blocks(const Geometry& g) {
   return (g.n + per - 1) / per;
 }
 
-cudaError_t launch_mode_sums(const Geometry& g, const float* src, double* partials, double* out54,
-                             cudaStream_t st) {
+template <int K>
+using DT = typename Storage<K>::T;
+
+cudaError_t launch_mode_sums(const Geometry& g, const StoreScale& ss, int kind, const void* src,
+                             double* partials, double* out54, cudaStream_t st) {
   const int64_t blocks = mode_sum_blocks(g);
-  k_mode_sums<<<(unsigned)blocks, kDiagBlock, 0, st>>>(g, src, partials);
+  switch (kind) {
+    case kStoreF32: k_mode_sums<kStoreF32><<<(unsigned)blocks, kDiagBlock, 0, st>>>(g, ss, (const DT<kStoreF32>*)src, partials); break;
+    case kStoreF16: k_mode_sums<kStoreF16><<<(unsigned)blocks, kDiagBlock, 0, st>>>(g, ss, (const DT<kStoreF16>*)src, partials); break;
+    case kStoreBF16: k_mode_sums<kStoreBF16><<<(unsigned)blocks, kDiagBlock, 0, st>>>(g, ss, (const DT<kStoreBF16>*)src, partials); break;
+    default: return cudaErrorInvalidValue;
+  }
   k_reduce_columns<<<2 * kQ, 32, 0, st>>>(partials, blocks, 2 * kQ, out54);
   return cudaGetLastError();
 }
 
-cudaError_t launch_field(const Geometry& g, const float* src, int field, double* out,
-                         cudaStream_t st) {
-  k_field<<<(unsigned)((g.n + kDiagBlock - 1) / kDiagBlock), kDiagBlock, 0, st>>>(g, src, field, out);
+cudaError_t launch_field(const Geometry& g, const StoreScale& ss, int kind, const void* src,
+                         int field, double* out, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((g.n + kDiagBlock - 1) / kDiagBlock);
+  switch (kind) {
+    case kStoreF32: k_field<kStoreF32><<<blocks, kDiagBlock, 0, st>>>(g, ss, (const DT<kStoreF32>*)src, field, out); break;
+    case kStoreF16: k_field<kStoreF16><<<blocks, kDiagBlock, 0, st>>>(g, ss, (const DT<kStoreF16>*)src, field, out); break;
+    case kStoreBF16: k_field<kStoreBF16><<<blocks, kDiagBlock, 0, st>>>(g, ss, (const DT<kStoreBF16>*)src, field, out); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "collide.cuh"
+#include "storage.cuh"
 
 namespace rflbm_dev {
 
@@ -97,8 +98,9 @@ __device__ __forceinline__ int32_t pull_delta(const PullDeltas& d, int i) {
 struct StepParams {
   Geometry geo;
   CollideParams cp;
-  const float* src;
-  float* dst;
+  StoreScale ss;    // 16-bit storage scales (unused for float32)
+  const void* src;  // population buffers in the handle's storage format
+  void* dst;
   int* err;  // device error flag (bit 0: a bounded wait expired)
   uint32_t key0, key1, step, replica;
 };
@@ -120,19 +122,23 @@ struct StepVariant {
   bool noise;       // kT > 0
   bool ghost_neq;   // omega_g != 1 (Reg only)
   bool phi_rho0;    // Eq. 10 with rho0
+  int storage;      // kStoreF32 / kStoreF16 / kStoreBF16 (16-bit: no ghost_neq, no phi_rho0)
 };
 
 // Records `msg` (and `detail`, if not NULL) as the calling thread's last error
 // (rflbm_last_error) and returns `code`.
 int record_error(int code, const char* msg, const char* detail);
 
-// Launches one step of the fused pull kernel (any box) on `stream`.
-cudaError_t launch_step_f32(const StepParams& p, const StepVariant& v, cudaStream_t stream);
+// Launches one step of the general gather kernel (any box) on `stream`.
+cudaError_t launch_step_gather(const StepParams& p, const StepVariant& v, cudaStream_t stream);
 
-// Row-segment width of the TMA step kernel for a box of x edge nx (0: not supported).
+// Row-segment width of the TMA step kernels for a box of x edge nx (0: not supported).
 int tma_segment_width(uint32_t nx);
-// Launches one step of the TMA-staged kernel on `stream`.
-cudaError_t launch_step_tma_f32(const TmaMaps& m, const StepParams& p, const StepVariant& v,
-                                cudaStream_t stream);
+// Launches one step of a TMA-staged kernel on `stream` (any storage format).
+cudaError_t launch_step_tma(const TmaMaps& m, const StepParams& p, const StepVariant& v,
+                            cudaStream_t stream);
+// The 16-bit storage part of launch_step_tma (rflbm_step_tma16.cu).
+cudaError_t launch_step_tma_16(const TmaMaps& m, const StepParams& p, const StepVariant& v,
+                               cudaStream_t stream);
 
 }  // namespace rflbm_dev

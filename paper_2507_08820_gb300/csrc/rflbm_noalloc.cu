@@ -37,6 +37,7 @@ constexpr int kSlot = 8;                     // doubles per partial slot
 constexpr int64_t kScratchWords = (int64_t)kNoAllocMaxBlocks * kSlot + kSlot + kSlot;
 constexpr int64_t kNoAllocScratchBytes = kScratchWords * (int64_t)sizeof(double);
 
+static_assert(kNoAllocScratchBytes < 600 * 1024, "the static scratch stays modest");
 static __device__ __align__(256) double g_noalloc_scratch[kScratchWords];
 
 __device__ __forceinline__ double na_warp_sum(double v) {

@@ -1,0 +1,68 @@
+// Population storage formats.
+//
+// The shifted populations g_i = f_i - w_i rho0 are stored as float32, or as float16 /
+// bfloat16 scaled by a power of two per velocity class |c_i|^2 (stored value
+// h_i = g_i 2^(e_class)); all arithmetic is float32. The scale maps the thermal amplitude
+// sqrt(w_i rho0 kT / cs2) of g_i to order one, so that float16 keeps full relative
+// precision (no subnormals) and the rounding error stays a fixed fraction of the
+// fluctuation; powers of two make the scaling exact.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+namespace rflbm_dev {
+
+enum : int { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
+
+// Velocity class |c_i|^2 of population i (0 rest, 1 face, 2 edge, 3 corner).
+__host__ __device__ constexpr int class_of(int i) {
+  return (i == 0) ? 0 : (i <= 6 ? 1 : (i <= 18 ? 2 : 3));
+}
+
+// Per-class scale factors of 16-bit storage: stored = g * scale, g = stored * inv_scale.
+struct StoreScale {
+  float scale[4];
+  float inv_scale[4];
+};
+
+template <int kStore>
+struct Storage;
+
+template <>
+struct Storage<kStoreF32> {
+  using T = float;
+  static constexpr int kHalo = 4;  // halo elements per side: 16 bytes
+  static __device__ __forceinline__ float load(T v, int, const StoreScale&) { return v; }
+  static __device__ __forceinline__ T store(float g, int, const StoreScale&) { return g; }
+};
+
+template <>
+struct Storage<kStoreF16> {
+  using T = __half;
+  static constexpr int kHalo = 8;
+  static __device__ __forceinline__ float load(T v, int cls, const StoreScale& s) {
+    return __half2float(v) * s.inv_scale[cls];
+  }
+  static __device__ __forceinline__ T store(float g, int cls, const StoreScale& s) {
+    return __float2half_rn(g * s.scale[cls]);
+  }
+};
+
+template <>
+struct Storage<kStoreBF16> {
+  using T = __nv_bfloat16;
+  static constexpr int kHalo = 8;
+  static __device__ __forceinline__ float load(T v, int cls, const StoreScale& s) {
+    return __bfloat162float(v) * s.inv_scale[cls];
+  }
+  static __device__ __forceinline__ T store(float g, int cls, const StoreScale& s) {
+    return __float2bfloat16_rn(g * s.scale[cls]);
+  }
+};
+
+inline size_t storage_bytes(int kind) { return kind == kStoreF32 ? 4 : 2; }
+
+}  // namespace rflbm_dev

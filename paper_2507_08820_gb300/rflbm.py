@@ -25,6 +25,8 @@ RFLBM_ESTATE = -6
 RFLBM_MODEL_REG = 0
 RFLBM_MODEL_BGK = 1
 RFLBM_STORE_F32 = 0
+RFLBM_STORE_F16 = 1
+RFLBM_STORE_BF16 = 2
 RFLBM_PHI_LOCAL_RHO = 0
 RFLBM_PHI_RHO0 = 1
 RFLBM_KERNEL_AUTO = 0
@@ -328,13 +330,15 @@ class Box:
 
     def __init__(self, nx, ny, nz, tau, kT=0.0, rho0=1.0, seed=1, omega_g=1.0,
                  model=RFLBM_MODEL_REG, phi_rho=RFLBM_PHI_LOCAL_RHO, replica=0,
-                 stream=None, torch_buffers=False, device=-1, kernel=RFLBM_KERNEL_AUTO):
+                 stream=None, torch_buffers=False, device=-1, kernel=RFLBM_KERNEL_AUTO,
+                 storage=RFLBM_STORE_F32):
         cfg = rflbm_config_default()
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
         cfg.tau, cfg.kT, cfg.rho0, cfg.seed = tau, kT, rho0, seed
         cfg.omega_g, cfg.model, cfg.phi_rho, cfg.replica = omega_g, model, phi_rho, replica
         cfg.device = device
         cfg.kernel = kernel
+        cfg.storage = storage
         if stream is not None:
             cfg.stream = stream
         self._buffers = None
@@ -342,7 +346,7 @@ class Box:
             import torch
             nbytes = rflbm_buffer_bytes(cfg)
             dev = torch.device("cuda", device if device >= 0 else torch.cuda.current_device())
-            self._buffers = [torch.empty(nbytes // 4, dtype=torch.float32, device=dev)
+            self._buffers = [torch.empty(nbytes, dtype=torch.uint8, device=dev)
                              for _ in range(2)]
             cfg.buffers[0] = self._buffers[0].data_ptr()
             cfg.buffers[1] = self._buffers[1].data_ptr()
