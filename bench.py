@@ -324,6 +324,28 @@ def gb300_arm(args):
                               "roofline_frac": bps * sites_s / 1e9 / peak_v,
                               "bytes_per_site": bps}
             vb.close()
+        # batched ensemble: 64 replicas of uneven sizes, one persistent launch per call
+        from paper_2507_08820_gb300 import workloads as W
+        reps = W.replica_ensemble(64, seed=0)
+        sites = sum(r["nx"] * r["ny"] * r["nz"] for r in reps)
+        for name, st_b, bps in (("batch64_f32", R.RFLBM_STORE_F32, 216),
+                                ("batch64_f16", R.RFLBM_STORE_F16, 108)):
+            bh = R.rflbm_batch_create(reps, storage=st_b, tile=0)
+            R.rflbm_batch_init_rest(bh)
+            R.rflbm_batch_run(bh, 20)
+            R.rflbm_batch_synchronize(bh)
+            k = max(20, args.steps // 20)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(torch.cuda.default_stream())
+            R.rflbm_batch_run(bh, k)
+            ev1.record(torch.cuda.default_stream())
+            ev1.synchronize()
+            sites_s = sites * k / (ev0.elapsed_time(ev1) * 1e-3)
+            tile, per_sm, _ = R.rflbm_batch_tuning(bh)
+            variants[name] = {"value": sites_s / 1e6, "unit": "MLUPS", "steps": k,
+                              "replicas": len(reps), "sites": sites, "tile": tile,
+                              "roofline_frac": bps * sites_s / 1e9 / peak_v, "bytes_per_site": bps}
+            R.rflbm_batch_destroy(bh)
     box.close()
 
     if info.rank != 0:

@@ -257,6 +257,35 @@ int rflbm_site_normals(uint64_t seed, int64_t step, uint32_t replica,
  * area: calls that overlap on the GPU (two streams or two host threads at once) race and
  * must be serialised by the caller. Returns RFLBM_OK, RFLBM_EUNSTABLE (non-finite values;
  * *out filled), RFLBM_EINVAL or RFLBM_ECUDA (message in rflbm_last_error). */
+/* Batched ensembles: many independent periodic boxes ("replicas") of uneven sizes, seeds,
+ * tau and kT, advanced together by one persistent kernel launch per call (replayed from a
+ * CUDA graph). Each replica runs the Reg-FLBM step of a single box (Eq. 25, omega_g = 1,
+ * local rho in Eq. 10) with Philox key = its seed and replica word 0, so it reproduces the
+ * run of rflbm_create(nx, ny, nz, tau, kT, rho0, seed) in the same storage format.
+ * The work is split into tiles of `tile` sites (128, 256 or 512; 0 = chosen by timing a
+ * few steps of each on the ensemble at creation) handed out by a global queue; a tile of
+ * step t waits (bounded) for its replica's step t - 1, and a wait that expires makes the
+ * call report RFLBM_ETIMEOUT. The library allocates and owns all device memory. */
+typedef struct rflbm_batch rflbm_batch_t;
+typedef struct {
+  int nx, ny, nz;   /* box edges (N = nx*ny*nz < 2^31) */
+  double tau, kT;   /* relaxation time > 1/2, thermal energy >= 0 */
+  uint64_t seed;    /* Philox key */
+} rflbm_replica_t;
+rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho0, int storage,
+                                  int tile);
+void rflbm_batch_destroy(rflbm_batch_t* b);
+/* Tile size in use, resident CTAs per SM of the persistent kernel, tiles per step. */
+int rflbm_batch_tuning(const rflbm_batch_t* b, int* tile, int* ctas_per_sm, int64_t* tiles_per_step);
+/* Every replica at rest, step 0. */
+int rflbm_batch_init_rest(rflbm_batch_t* b);
+/* n steps of every replica (asynchronous on the default stream). */
+int rflbm_batch_run(rflbm_batch_t* b, int64_t n);
+int rflbm_batch_synchronize(rflbm_batch_t* b);
+/* Populations (27*N doubles, public layout) and diagnostics of replica r. Synchronous. */
+int rflbm_batch_get_populations(rflbm_batch_t* b, int r, double* f);
+int rflbm_batch_stats(rflbm_batch_t* b, int r, rflbm_stats_t* out);
+
 #define RFLBM_STATS_NOALLOC_MAX_SITES 134217728LL
 int rflbm_stats_f32_noalloc(const float* f, int64_t n_sites, void* stream, rflbm_stats_t* out);
 

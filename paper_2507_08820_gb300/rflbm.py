@@ -53,6 +53,11 @@ class rflbm_config_t(C.Structure):
     ]
 
 
+class rflbm_replica_t(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("tau", C.c_double), ("kT", C.c_double), ("seed", C.c_uint64)]
+
+
 class rflbm_stats_t(C.Structure):
     _fields_ = [
         ("step", C.c_int64), ("mass", C.c_double), ("momentum", C.c_double * 3),
@@ -101,6 +106,14 @@ _sig = {
     "rflbm_site_normals": (C.c_int, [C.c_uint64, C.c_int64, C.c_uint32, _P, C.c_int64, _P]),
     "rflbm_stats_f32_noalloc": (C.c_int, [_P, C.c_int64, _P, C.POINTER(rflbm_stats_t)]),
     "rflbm_mode_sums": (C.c_int, [_H, _P, _P]),
+    "rflbm_batch_create": (_H, [_P, C.c_int, C.c_double, C.c_int, C.c_int]),
+    "rflbm_batch_destroy": (None, [_H]),
+    "rflbm_batch_tuning": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "rflbm_batch_init_rest": (C.c_int, [_H]),
+    "rflbm_batch_run": (C.c_int, [_H, C.c_int64]),
+    "rflbm_batch_synchronize": (C.c_int, [_H]),
+    "rflbm_batch_get_populations": (C.c_int, [_H, C.c_int, _P]),
+    "rflbm_batch_stats": (C.c_int, [_H, C.c_int, C.POINTER(rflbm_stats_t)]),
     "rflbm_structure_factor": (C.c_int, [_H, C.c_int, C.c_int, _P, _P]),
     "rflbm_shell_count": (C.c_int, [_H]),
 }
@@ -318,6 +331,53 @@ def rflbm_stats_f32_noalloc(f, n_sites, stream=None):
         raise ValueError("populations must be in device memory")
     st = rflbm_stats_t()
     status = lib.rflbm_stats_f32_noalloc(p, int(n_sites), stream, C.byref(st))
+    if status < 0 and status != RFLBM_EUNSTABLE:
+        _check(status)
+    return st, status
+
+
+def rflbm_batch_create(replicas, rho0=1.0, storage=RFLBM_STORE_F32, tile=0):
+    """replicas: list of dicts with nx, ny, nz, tau, kT, seed."""
+    arr = (rflbm_replica_t * len(replicas))()
+    for a, r in zip(arr, replicas):
+        a.nx, a.ny, a.nz = r["nx"], r["ny"], r["nz"]
+        a.tau, a.kT, a.seed = r["tau"], r["kT"], r["seed"]
+    h = lib.rflbm_batch_create(C.cast(arr, C.c_void_p), len(replicas), rho0, storage, tile)
+    if not h:
+        raise RflbmError(-1, lib.rflbm_last_error().decode())
+    return h
+
+
+def rflbm_batch_destroy(b):
+    lib.rflbm_batch_destroy(b)
+
+
+def rflbm_batch_tuning(b):
+    t, c, n = C.c_int(), C.c_int(), C.c_int64()
+    _check(lib.rflbm_batch_tuning(b, C.byref(t), C.byref(c), C.byref(n)))
+    return t.value, c.value, n.value
+
+
+def rflbm_batch_init_rest(b):
+    return _check(lib.rflbm_batch_init_rest(b))
+
+
+def rflbm_batch_run(b, n):
+    return _check(lib.rflbm_batch_run(b, int(n)))
+
+
+def rflbm_batch_synchronize(b):
+    return _check(lib.rflbm_batch_synchronize(b))
+
+
+def rflbm_batch_get_populations(b, r, f):
+    p, _ = _ptr(f, np.float64)
+    return _check(lib.rflbm_batch_get_populations(b, int(r), p))
+
+
+def rflbm_batch_stats(b, r):
+    st = rflbm_stats_t()
+    status = lib.rflbm_batch_stats(b, int(r), C.byref(st))
     if status < 0 and status != RFLBM_EUNSTABLE:
         _check(status)
     return st, status

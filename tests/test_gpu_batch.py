@@ -1,0 +1,92 @@
+"""Batched ensembles: many replicas of uneven sizes, seeds, tau and kT in one persistent
+launch reproduce their single-box runs; the ensemble of the batched configuration
+(64 replicas, edges in {16,24,32,48,64,96}, kT log-uniform in [1e-5, 1e-3], tau uniform in
+[0.55, 1.2], rest start, 1000 steps) runs in float32 and float16 storage."""
+import numpy as np
+import pytest
+
+from paper_2507_08820_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [dict(nx=16, ny=16, nz=16, tau=0.6, kT=1e-4, seed=3),
+         dict(nx=24, ny=24, nz=24, tau=0.9, kT=1e-3, seed=4),
+         dict(nx=32, ny=32, nz=32, tau=1.1, kT=1e-5, seed=5),
+         dict(nx=20, ny=12, nz=9, tau=0.55, kT=2e-4, seed=6),
+         dict(nx=64, ny=8, nz=4, tau=0.8, kT=0.0, seed=7),
+         dict(nx=1, ny=1, nz=1, tau=0.7, kT=1e-4, seed=8)]
+
+
+@pytest.fixture(scope="module")
+def R():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_08820_gb300 import build
+    build.build()
+    from paper_2507_08820_gb300 import rflbm
+    return rflbm
+
+
+def _single(R, rep, steps, storage):
+    box = R.Box(rep["nx"], rep["ny"], rep["nz"], tau=rep["tau"], kT=rep["kT"], seed=rep["seed"],
+                storage=storage, kernel=R.RFLBM_KERNEL_GATHER)
+    R.rflbm_init_rest(box.h)
+    R.rflbm_step(box.h, steps)
+    f = box.populations()
+    box.close()
+    return f
+
+
+def _batch_pops(R, b, reps, r):
+    n = reps[r]["nx"] * reps[r]["ny"] * reps[r]["nz"]
+    f = np.empty((27, n))
+    R.rflbm_batch_get_populations(b, r, f)
+    return f
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("tile", [128, 256, 512])
+def test_replicas_reproduce_their_single_box_runs(R, storage, tile):
+    b = R.rflbm_batch_create(SMALL, storage=storage, tile=tile)
+    assert R.rflbm_batch_tuning(b)[0] == tile
+    R.rflbm_batch_init_rest(b)
+    for n in (3, 4, 3):  # several calls: odd/even buffer parity and the step index
+        R.rflbm_batch_run(b, n)
+    R.rflbm_batch_synchronize(b)
+    for r, rep in enumerate(SMALL):
+        got = _batch_pops(R, b, SMALL, r)
+        want = _single(R, rep, 10, storage)
+        assert np.array_equal(got, want), r
+    R.rflbm_batch_destroy(b)
+
+
+def test_autotuner_and_errors(R):
+    b = R.rflbm_batch_create(SMALL[:3], tile=0)
+    tile, per_sm, tiles = R.rflbm_batch_tuning(b)
+    assert tile in (128, 256, 512) and per_sm >= 1 and tiles > 0
+    with pytest.raises(R.RflbmError) as e:
+        R.rflbm_batch_run(b, 1)  # not initialised
+    assert e.value.status == R.RFLBM_ESTATE
+    R.rflbm_batch_destroy(b)
+    with pytest.raises(R.RflbmError):
+        R.rflbm_batch_create([dict(nx=8, ny=8, nz=8, tau=0.4, kT=0.0, seed=1)])
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_ensemble_of_64_replicas_1000_steps(R, storage):
+    reps = W.replica_ensemble(64, seed=0)
+    b = R.rflbm_batch_create(reps, storage=storage, tile=0)
+    R.rflbm_batch_init_rest(b)
+    R.rflbm_batch_run(b, 1000)
+    R.rflbm_batch_synchronize(b)
+    for r, rep in enumerate(reps):
+        st, status = R.rflbm_batch_stats(b, r)
+        n = rep["nx"] * rep["ny"] * rep["nz"]
+        assert status == R.RFLBM_OK and st.step == 1000
+        assert abs(st.mass - n) / n < (1e-7 if storage == 0 else 1e-4)
+    # the smallest and the largest replica against their single-box runs
+    sizes = [rep["nx"] for rep in reps]
+    for r in (int(np.argmin(sizes)), int(np.argmax(sizes))):
+        assert np.array_equal(_batch_pops(R, b, reps, r), _single(R, reps[r], 1000, storage)), r
+    R.rflbm_batch_destroy(b)
