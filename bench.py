@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--kernel", choices=["auto", "gather", "tma", "persistent"], default="auto")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--init", choices=["rest", "taylor-green"], default="rest",
+                    help="rest start, or the Taylor-Green vortex (u0 = 0.01, k = 2 pi / edge)")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -61,8 +64,9 @@ def workload(args):
     nbytes = 2 * 27 * BYTES_PER_SITE[args.storage] // 54 * e ** 3
     return {"workload": f"periodic {e}^3 Reg-FLBM D3Q27 thermal equilibrium, "
                         f"{STORAGE_NAME[args.storage]} populations, tau {args.tau}, rho0 1, "
-                        f"kT {args.kT:g}, seed 1, rest start",
-            "box": [e, e, e], "sites": e ** 3, "tau": args.tau, "kT": args.kT,
+                        f"kT {args.kT:g}, seed 1, "
+                        + ("rest start" if args.init == "rest" else "Taylor-Green u0 0.01 start"),
+            "init": args.init, "box": [e, e, e], "sites": e ** 3, "tau": args.tau, "kT": args.kT,
             "storage": f"{args.storage} shifted by w_i rho0", "streaming": "pull, ping-pong",
             "l2": f"inputs {nbytes / 1e6:.0f} MB (two population buffers) > 129 MB L2, no flush",
             "parallelism": "replicas"}
@@ -89,14 +93,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_name(kind, path, kT, model):
+def kernel_name(kind, path, kT, model, storage="f32"):
     noise = "noise" if kT > 0 else "no noise"
     m = "BGK" if model else "Reg"
     if kind == 3:
         return f"step_tma_persistent_f32<{path}, {m}, {noise}>", f"step_tma_persistent_f32_{path}"
     if kind == 2:
-        return f"step_tma_f32<{path}, {m}, {noise}>", f"step_tma_f32_{path}"
-    return f"step_pull_f32<{m}, {noise}>", "step_pull_f32"
+        return f"step_tma<{storage}, {path}, {m}, {noise}>", f"step_tma_{storage}_{path}"
+    return f"step_pull<{storage}, {m}, {noise}>", f"step_pull_{storage}"
 
 
 def profiled_traffic(profile_stem, edge):
@@ -273,7 +277,23 @@ def gb300_arm(args):
     box = R.Box(e, e, e, tau=args.tau, kT=args.kT, seed=1, replica=info.rank,
                 stream=stream.cuda_stream, torch_buffers=True, device=info.local_rank,
                 kernel=kernel, storage=storage[args.storage])
-    R.rflbm_init_rest(box.h)
+    if args.init == "rest":
+        R.rflbm_init_rest(box.h)
+    else:
+        # Taylor-Green fields built on the device (the host would need 4 N doubles)
+        k = 2.0 * np.pi / e
+        x = torch.arange(e, dtype=torch.float64, device=dev)
+        cx, sx = torch.cos(k * x), torch.sin(k * x)
+        u = torch.zeros((3, e, e, e), dtype=torch.float64, device=dev)  # (3, z, y, x)
+        u[0] = -0.01 * (cx[None, None, :] * sx[None, :, None])
+        u[1] = 0.01 * (sx[None, None, :] * cx[None, :, None])
+        c2 = torch.cos(2 * k * x)
+        rho = 1.0 - 0.01 ** 2 * 3.0 / 4.0 * (c2[None, None, :] + c2[None, :, None]).expand(e, e, e)
+        rho = rho.contiguous()
+        R.rflbm_init_field(box.h, rho, u)
+        torch.cuda.synchronize()
+        del u, rho
+        torch.cuda.empty_cache()
     kind, path = R.rflbm_step_path(box.h)
     R.rflbm_step(box.h, args.warmup)
     R.rflbm_synchronize(box.h)
@@ -291,17 +311,23 @@ def gb300_arm(args):
     st, status = R.rflbm_stats(box.h)
 
     # end to end through the ABI with host buffers: pinned populations in, stats out
-    k_e2e = max(3, min(args.steps, 2000) // 10)
-    host = torch.empty((27, n), dtype=torch.float32).pin_memory()
-    R.rflbm_get_populations_f32(box.h, host)
-    R.rflbm_set_populations_f32(box.h, host)   # untimed: allocates the staging buffer
-    dist.barrier(info, info.local_rank)
-    t0 = time.perf_counter()
-    for _ in range(k_e2e):
-        R.rflbm_set_populations_f32(box.h, host)
-        R.rflbm_step(box.h, 1)
-        R.rflbm_stats(box.h)
-    e2e_s = dist.max_over_ranks(info, time.perf_counter() - t0, dev)
+    e2e = None
+    if not args.no_e2e:
+        k_e2e = max(3, min(args.steps, 2000) // 10)
+        host = torch.empty((27, n), dtype=torch.float32).pin_memory()
+        R.rflbm_get_populations_f32(box.h, host)
+        R.rflbm_set_populations_f32(box.h, host)   # untimed: allocates the staging buffer
+        dist.barrier(info, info.local_rank)
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            R.rflbm_set_populations_f32(box.h, host)
+            R.rflbm_step(box.h, 1)
+            R.rflbm_stats(box.h)
+        e2e_s = dist.max_over_ranks(info, time.perf_counter() - t0, dev)
+        e2e = {"value": info.world * n * k_e2e / e2e_s / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 27 * 4 * n, "d2h_bytes_per_step": 6 * 8, "steps": k_e2e,
+               "path": "rflbm_set_populations_f32 (pinned host) + rflbm_step + rflbm_stats"}
+        del host
 
     variants = {}
     if not args.no_variants and info.world == 1:
@@ -355,7 +381,7 @@ def gb300_arm(args):
     per_launch_s = ms * 1e-3 / args.steps
     achieved = BYTES_PER_SITE[args.storage] * n / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
-    kname, kstem = kernel_name(kind, path, args.kT, 0)
+    kname, kstem = kernel_name(kind, path, args.kT, 0, args.storage)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(kstem, e),
                 "peak_source": f"hbm_gbs of {peak_kind}", "kernel": kname,
@@ -373,9 +399,7 @@ def gb300_arm(args):
         "storage_dtype": args.storage, "data": "synthetic", "config": workload(args),
         "roofline": roofline,
         "cpu_baseline": cpu,
-        "e2e": {"value": info.world * n * k_e2e / e2e_s / 1e6, "unit": "MLUPS",
-                "h2d_bytes_per_step": 27 * 4 * n, "d2h_bytes_per_step": 6 * 8, "steps": k_e2e,
-                "path": "rflbm_set_populations_f32 (pinned host) + rflbm_step + rflbm_stats"},
+        "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "stats_after": {"mass_rel_drift": (st.mass - n) / n, "max_speed": st.max_speed,

@@ -1,0 +1,43 @@
+"""Reduced-scale replication of Table III (128^3 instead of 256^3, 2e4 instead of 5e5
+steps, kT = 1/3000): equilibration ratios of the Reg-FLBM against the paper's values, and
+the stability limits of both models (Sec. III: Reg-FLBM stable down to tau = 0.5001,
+BGK-FLBM only from tau = 0.505)."""
+import pytest
+
+from conftest import read_golden
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ex():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_08820_gb300 import build
+    build.build()
+    from paper_2507_08820_gb300 import experiments
+    return experiments
+
+
+PAPER = {float(r[0]): tuple(float(v) for v in r[1:]) for r in read_golden("table3_er_reg.txt")}
+
+
+@pytest.mark.parametrize("tau", [0.55, 0.7, 1.0, 2.0, 10.0, 100.0])
+def test_reg_equilibration_ratios_against_table3(ex, tau):
+    """Sec. III: within 0.5 % of the fluctuation-dissipation value for these tau; and at
+    least as close to it as the paper's own entry (0.001 of slack for the statistical
+    error of the shorter runs)."""
+    er = ex.equilibration_ratios(tau, model="reg")
+    assert er is not None
+    for ours, paper in zip(er, PAPER[tau]):
+        assert abs(ours - 1.0) < 0.005, (tau, er)
+        assert abs(ours - 1.0) <= abs(paper - 1.0) + 0.001, (tau, er, PAPER[tau])
+
+
+def test_stability_limits_of_both_models(ex):
+    reg = ex.equilibration_ratios(0.5005, model="reg")
+    assert reg is not None and all(0.99 < v < 1.06 for v in reg)
+    assert ex.equilibration_ratios(0.5005, model="bgk") is None
+    bgk = ex.equilibration_ratios(0.505, model="bgk")
+    assert bgk is not None and all(1.0 < v < 1.15 for v in bgk)
