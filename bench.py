@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--kT", type=float, default=1e-4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--kernel", choices=["auto", "gather", "tma", "persistent"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "gather", "tma"], default="auto")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--init", choices=["rest", "taylor-green"], default="rest",
                     help="rest start, or the Taylor-Green vortex (u0 = 0.01, k = 2 pi / edge)")
@@ -96,8 +96,6 @@ def kernel_source_hash():
 def kernel_name(kind, path, kT, model, storage="f32"):
     noise = "noise" if kT > 0 else "no noise"
     m = "BGK" if model else "Reg"
-    if kind == 3:
-        return f"step_tma_persistent_f32<{path}, {m}, {noise}>", f"step_tma_persistent_f32_{path}"
     if kind == 2:
         return f"step_tma<{storage}, {path}, {m}, {noise}>", f"step_tma_{storage}_{path}"
     return f"step_pull<{storage}, {m}, {noise}>", f"step_pull_{storage}"
@@ -272,7 +270,7 @@ def gb300_arm(args):
     n = e ** 3
     stream = torch.cuda.Stream(device=dev)
     kernel = {"auto": R.RFLBM_KERNEL_AUTO, "gather": R.RFLBM_KERNEL_GATHER,
-              "tma": R.RFLBM_KERNEL_TMA, "persistent": R.RFLBM_KERNEL_TMA_PERSISTENT}[args.kernel]
+              "tma": R.RFLBM_KERNEL_TMA}[args.kernel]
     storage = {"f32": R.RFLBM_STORE_F32, "f16": R.RFLBM_STORE_F16, "bf16": R.RFLBM_STORE_BF16}
     box = R.Box(e, e, e, tau=args.tau, kT=args.kT, seed=1, replica=info.rank,
                 stream=stream.cuda_stream, torch_buffers=True, device=info.local_rank,

@@ -75,14 +75,13 @@ typedef enum {
   RFLBM_PHI_RHO0 = 1       /* rho in Eq. 10 is the reference density rho0 */
 } rflbm_phi_rho;
 
-/* Step kernels. All compute the same step; they differ in how the 27 neighbours are
- * fetched. The TMA kernels need nx to be a multiple of 32 (row segments of 128, 64 or 32
+/* Step kernels. Both compute the same step; they differ in how the 27 neighbours are
+ * fetched. The TMA kernel needs nx to be a multiple of 32 (row segments of 128, 64 or 32
  * sites); on other boxes every choice runs the general kernel. */
 typedef enum {
-  RFLBM_KERNEL_AUTO = 0,           /* TMA when the box allows it, else the general kernel */
-  RFLBM_KERNEL_GATHER = 1,         /* one thread per site, 27 addressed loads */
-  RFLBM_KERNEL_TMA = 2,            /* one CTA per row segment, TMA tensor loads/stores */
-  RFLBM_KERNEL_TMA_PERSISTENT = 3  /* persistent CTAs, double-buffered TMA row segments */
+  RFLBM_KERNEL_AUTO = 0,    /* TMA when the box allows it, else the general kernel */
+  RFLBM_KERNEL_GATHER = 1,  /* one thread per site, 27 addressed loads */
+  RFLBM_KERNEL_TMA = 2      /* one CTA per row segment, TMA tensor loads and stores */
 } rflbm_kernel;
 
 typedef struct {

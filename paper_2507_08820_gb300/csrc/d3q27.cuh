@@ -32,6 +32,13 @@ __host__ __device__ constexpr int cz_of(int i) {
   return t[i];
 }
 
+// Internal plane of population i in a population buffer: the populations that pull from
+// the same source row (equal c_y, c_z) are adjacent, ordered by c_x = -1, 0, +1, so that
+// one tensor copy moves all three. (The public API keeps the order of Table I.)
+__host__ __device__ constexpr int plane_of(int i) {
+  return 3 * (3 * (cy_of(i) + 1) + (cz_of(i) + 1)) + (cx_of(i) + 1);
+}
+
 // 1-D weight W(c) for a tile index a = c + 1.
 __host__ __device__ constexpr double w1d(int a) { return a == 1 ? 2.0 / 3.0 : 1.0 / 6.0; }
 // Lattice weight of population i.
@@ -71,14 +78,17 @@ __host__ __device__ constexpr int mode_of(int p, int q, int r) {
   return t[9 * p + 3 * q + r];
 }
 
-// The two mode tables are inverse to each other, and the weights sum to one.
+// The two mode tables are inverse to each other, the weights sum to one and the plane map
+// is a permutation.
 __host__ __device__ constexpr bool tables_consistent() {
   double wsum = 0.0;
+  int seen = 0;
   for (int k = 0; k < kQ; ++k) {
     if (mode_of(p_of(k), q_of(k), r_of(k)) != k) return false;
     wsum += weight_of(k);
+    seen |= 1 << plane_of(k);
   }
-  return wsum > 1.0 - 1e-12 && wsum < 1.0 + 1e-12;
+  return wsum > 1.0 - 1e-12 && wsum < 1.0 + 1e-12 && seen == (1 << kQ) - 1;
 }
 static_assert(tables_consistent(), "D3Q27 tables are inconsistent");
 

@@ -111,7 +111,7 @@ int validate(const rflbm_config_t* c) {
     return fail(RFLBM_EINVAL, "16-bit storage supports omega_g = 1 and the local density in Eq. 10 only");
   if (c->phi_rho != RFLBM_PHI_LOCAL_RHO && c->phi_rho != RFLBM_PHI_RHO0)
     return fail(RFLBM_EINVAL, "unknown phi_rho option %d", c->phi_rho);
-  if (c->kernel < RFLBM_KERNEL_AUTO || c->kernel > RFLBM_KERNEL_TMA_PERSISTENT)
+  if (c->kernel < RFLBM_KERNEL_AUTO || c->kernel > RFLBM_KERNEL_TMA)
     return fail(RFLBM_EINVAL, "unknown kernel choice %d", c->kernel);
   return RFLBM_OK;
 }
@@ -213,14 +213,15 @@ EncodeTiledFn encode_tiled_fn() {
   return fn;
 }
 
-// The population buffer as a 4-D tensor (x, y, z, plane); box = (box_x, 1, 1, 1).
-bool encode_map(CUtensorMap* map, void* base, const Geometry& g, uint32_t box_x, int storage) {
+// The population buffer as a 4-D tensor (x, y, z, plane); box = (box_x, 1, 1, box_planes).
+bool encode_map(CUtensorMap* map, void* base, const Geometry& g, uint32_t box_x, uint32_t box_planes,
+                int storage) {
   EncodeTiledFn fn = encode_tiled_fn();
   if (!fn) return false;
   const cuuint64_t e = storage_bytes(storage);
   const cuuint64_t dims[4] = {g.nx, g.ny, g.nz, (cuuint64_t)kQ};
   const cuuint64_t strides[3] = {(cuuint64_t)g.nx * e, (cuuint64_t)g.nxy * e, (cuuint64_t)g.ps * e};
-  const cuuint32_t box[4] = {box_x, 1, 1, 1};
+  const cuuint32_t box[4] = {box_x, 1, 1, box_planes};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt = storage == kStoreF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                  : storage == kStoreBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
@@ -239,14 +240,13 @@ void setup_tma(rflbm* h) {
   const int st = h->variant.storage;
   const uint32_t halo = st == kStoreF32 ? 4 : 8;  // 16 bytes each side
   for (int b = 0; b < 2; ++b) {
-    if (!encode_map(&h->load_map[b], h->buf[b], h->geo, (uint32_t)w + 2 * halo, st) ||
-        !encode_map(&h->store_map[b], h->buf[b], h->geo, (uint32_t)w, st))
+    // loads: the three planes of one source row; stores: all 27 planes of the segment
+    if (!encode_map(&h->load_map[b], h->buf[b], h->geo, (uint32_t)w + 2 * halo, 3, st) ||
+        !encode_map(&h->store_map[b], h->buf[b], h->geo, (uint32_t)w, kQ, st))
       return;
   }
   h->tma_width = w;
-  // the persistent kernel exists for float32 storage only
-  h->kernel = (h->cfg.kernel == RFLBM_KERNEL_TMA_PERSISTENT && st == kStoreF32) ? RFLBM_KERNEL_TMA_PERSISTENT
-                                                                                 : RFLBM_KERNEL_TMA;
+  h->kernel = RFLBM_KERNEL_TMA;
 }
 
 int64_t n_sites(const rflbm* h) { return (int64_t)h->geo.n; }
@@ -451,8 +451,7 @@ int rflbm_step(rflbm_t* h, int64_t n) {
     p.step = (uint32_t)h->step;
     cudaError_t e;
     if (h->tma_width) {
-      const TmaMaps m{&h->load_map[h->cur], &h->store_map[1 - h->cur], h->tma_width,
-                      h->kernel == RFLBM_KERNEL_TMA_PERSISTENT ? h->num_sms : 0};
+      const TmaMaps m{&h->load_map[h->cur], &h->store_map[1 - h->cur], h->tma_width};
       e = launch_step_tma(m, p, h->variant, h->stream);
     } else {
       e = launch_step_gather(p, h->variant, h->stream);

@@ -29,7 +29,7 @@ __global__ void k_init_field(Geometry g, float rho0, StoreScale ss, const double
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const double f = r * psi(cx_of(i), ux) * psi(cy_of(i), uy) * psi(cz_of(i), uz);
-    dst[i * g.ps + pull_site(nb, i)] = S::store((float)(f - weight_of(i) * (double)rho0), class_of(i), ss);
+    dst[plane_of(i) * g.ps + pull_site(nb, i)] = S::store((float)(f - weight_of(i) * (double)rho0), class_of(i), ss);
   }
 }
 
@@ -44,7 +44,7 @@ __global__ void k_set_populations(Geometry g, float rho0, StoreScale ss, const T
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const Tin v = f[i * (int64_t)g.n + s] - (Tin)(weight_of(i) * (double)rho0);
-    dst[i * g.ps + pull_site(nb, i)] = S::store((float)v, class_of(i), ss);
+    dst[plane_of(i) * g.ps + pull_site(nb, i)] = S::store((float)v, class_of(i), ss);
   }
 }
 
@@ -57,7 +57,7 @@ __global__ void k_get_populations(Geometry g, float rho0, StoreScale ss,
   const Neighbours nb = neighbours(site_of(s), g);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const float v = S::load(src[i * g.ps + pull_site(nb, i)], class_of(i), ss);
+    const float v = S::load(src[plane_of(i) * g.ps + pull_site(nb, i)], class_of(i), ss);
     f[i * (int64_t)g.n + s] = (Tout)v + (Tout)(weight_of(i) * (double)rho0);
   }
 }
@@ -72,7 +72,7 @@ __global__ void k_get_sites(Geometry g, float rho0, StoreScale ss,
   const Neighbours nb = neighbours(site_of(sites[j]), g);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    f[i * n + j] = (double)S::load(src[i * g.ps + pull_site(nb, i)], class_of(i), ss) +
+    f[i * n + j] = (double)S::load(src[plane_of(i) * g.ps + pull_site(nb, i)], class_of(i), ss) +
                    weight_of(i) * (double)rho0;
   }
 }
@@ -92,7 +92,7 @@ __device__ __forceinline__ SiteMoments site_moments(const Neighbours& nb,
   Acc drho = 0, j0 = 0, j1 = 0, j2 = 0, s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const Acc v = (Acc)S::load(src[i * ps + pull_site(nb, i)], class_of(i), ss);
+    const Acc v = (Acc)S::load(src[plane_of(i) * ps + pull_site(nb, i)], class_of(i), ss);
     const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     drho += v;
     if (cx) j0 += cx * v;

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kTile) k_batch_run(const ReplicaDev* __restric
 #pragma unroll
       for (int i = 0; i < kQ; ++i)
         G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] =
-            S::load(__ldcg(src + s + pull_delta(d, i) + i * rep.geo.ps), class_of(i), rep.ss);
+            S::load(__ldcg(src + s + pull_delta(d, i) + plane_of(i) * rep.geo.ps), class_of(i), rep.ss);
       SiteNoise noise;
       const uint32_t step = step0 + (uint32_t)t;
       if (rep.noise) {
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kTile) k_batch_run(const ReplicaDev* __restric
       }
 #pragma unroll
       for (int i = 0; i < kQ; ++i)
-        dst[s + i * rep.geo.ps] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), rep.ss);
+        dst[s + plane_of(i) * rep.geo.ps] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), rep.ss);
     }
     __threadfence();  // this thread's stores before the completion count
     __syncthreads();  // also: nobody reads `rep` or `item_sh` of this item any more

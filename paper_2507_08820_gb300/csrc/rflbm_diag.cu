@@ -51,7 +51,7 @@ __device__ __forceinline__ void gather_tile(const typename Storage<kStore>::T* _
 #pragma unroll
   for (int i = 0; i < kQ; ++i)
     G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] =
-        Storage<kStore>::load(src[i * g.ps + pull_site(nb, i)], class_of(i), ss);
+        Storage<kStore>::load(src[plane_of(i) * g.ps + pull_site(nb, i)], class_of(i), ss);
 }
 
 // Each thread accumulates up to kDiagSitesPerThread sites in float32, then the block sums
@@ -120,7 +120,7 @@ __global__ void k_field(Geometry g, StoreScale ss, const typename Storage<kStore
   float v = 0.0f, drho = 0.0f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const float x = Storage<kStore>::load(src[i * g.ps + pull_site(nb, i)], class_of(i), ss);
+    const float x = Storage<kStore>::load(src[plane_of(i) * g.ps + pull_site(nb, i)], class_of(i), ss);
     const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     float w;
     switch (field) {

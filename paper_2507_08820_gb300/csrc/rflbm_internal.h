@@ -105,13 +105,12 @@ struct StepParams {
   uint32_t key0, key1, step, replica;
 };
 
-// TMA descriptors of a source buffer (row segments with a 4-element halo on each side)
-// and of a destination buffer (row segments), for segment width `width`.
+// TMA descriptors of a source buffer (the three planes of a source row, row segment plus
+// a 16-byte halo on each side) and of a destination buffer (all planes of a row segment).
 struct TmaMaps {
-  const CUtensorMap* load;
-  const CUtensorMap* store;
+  const CUtensorMap* load;   // box: (width + 2 halo) x 1 x 1 x 3 planes
+  const CUtensorMap* store;  // box: width x 1 x 1 x 27 planes
   int width;
-  int persistent_sms;  // > 0: persistent double-buffered kernel over this many SMs
 };
 
 constexpr int kStepBlock = 256;

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kStepBlock) step_pull(const StepParams p) {
   for (int i = 0; i < kQ; ++i) {
     // per-thread neighbour pointer plus the plane offset i * ps (uniform across the grid)
     G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] =
-        S::load(__ldg((src + pull_delta(d, i)) + i * p.geo.ps), class_of(i), p.ss);
+        S::load(__ldg((src + pull_delta(d, i)) + plane_of(i) * p.geo.ps), class_of(i), p.ss);
   }
 
   SiteNoise noise;
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kStepBlock) step_pull(const StepParams p) {
   T* __restrict__ dst = static_cast<T*>(p.dst) + s;
 #pragma unroll
   for (int i = 0; i < kQ; ++i)
-    dst[i * p.geo.ps] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
+    dst[plane_of(i) * p.geo.ps] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
 }
 
 template <int kStore, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>

@@ -3,16 +3,17 @@
 //
 // One CTA of kW threads updates one row segment [x0, x0 + kW) of one lattice row (y, z).
 // The 27 populations of a site are pulled from 9 source rows (y - c_y, z - c_z), shifted
-// by -c_x along x. One thread per population (spread over the warps) issues one tiled TMA
-// load of the source row segment [x0 - H, x0 + kW + H) of plane i into shared memory
-// (H = 4 float32 or 8 16-bit elements: 16-byte aligned coordinates; 27 loads complete on
-// one mbarrier); where the segment touches the periodic x edge the wrapped neighbour is
-// fetched with a plain load. The first half of the 24 normals is drawn before the kernel
-// waits for the previous step (programmatic dependent launch lets this grid start while
-// the previous one drains), the second half while the copies are in flight. Each thread
-// then reads its 27 values from shared memory at fixed offsets (x - c_x within the row),
-// collides in registers in float32, writes its 27 results back to shared memory, and the
-// same threads issue 27 tiled TMA stores of the row segment into the destination planes.
+// by -c_x along x. The three populations of a source row (c_x = -1, 0, +1) occupy three
+// adjacent planes of the buffer, so lane g of warp 0 (g = 0..8) fetches group g with one
+// tiled TMA load of three planes x [x0 - H, x0 + kW + H) (H = 4 float32 or 8 16-bit
+// elements: 16-byte aligned coordinates); the 9 loads complete on one mbarrier. Where the
+// segment touches the periodic x edge the wrapped neighbour is fetched with a plain load.
+// The first half of the 24 normals is drawn before the kernel waits for the previous step
+// (programmatic dependent launch lets this grid start while the previous one drains), the
+// second half while the copies are in flight. Each thread then reads its 27 values from
+// shared memory at fixed offsets (x - c_x within its group row), collides in registers in
+// float32 and writes its 27 results into a dense [plane][kW] tile, which lane 0 stores
+// with one TMA copy of all 27 planes.
 //
 // Every wait on the mbarrier is bounded; a CTA that gives up sets the handle's error flag,
 // waits (again bounded) for its copies in flight and exits without storing.
@@ -23,33 +24,33 @@
 
 namespace rflbm_dev {
 
-// Velocity component of population i for a run-time i (2 bits per population).
-__host__ __device__ constexpr uint64_t pack_component(int axis) {
-  uint64_t v = 0;
-  for (int i = 0; i < kQ; ++i) {
-    const int c = axis == 0 ? cx_of(i) : (axis == 1 ? cy_of(i) : cz_of(i));
-    v |= (uint64_t)(c + 1) << (2 * i);
-  }
-  return v;
-}
-constexpr uint64_t kPackCx = pack_component(0), kPackCy = pack_component(1),
-                   kPackCz = pack_component(2);
-__device__ __forceinline__ int comp(uint64_t pack, int i) { return (int)((pack >> (2 * i)) & 3u) - 1; }
-
 constexpr uint32_t kMaxPolls = 1u << 22;  // bounded mbarrier waits
+constexpr int kGroups = 9;                 // source rows (c_y, c_z)
+
+// Shared-memory geometry of one CTA.
+template <int kStore, int kW>
+struct TmaLayout {
+  using T = typename Storage<kStore>::T;
+  static constexpr int kH = Storage<kStore>::kHalo;
+  static constexpr int kSeg = kW + 2 * kH;  // elements per plane row of a group
+  static constexpr int kGroupBytes = (3 * kSeg * (int)sizeof(T) + 127) / 128 * 128;
+  static constexpr int kGroup = kGroupBytes / (int)sizeof(T);  // group stride in elements
+  static constexpr size_t kBytes = (size_t)kGroups * kGroupBytes + 128;  // + alignment slack
+  static_assert((size_t)kQ * kW * sizeof(T) <= (size_t)kGroups * kGroupBytes,
+                "the output tile must fit in the input tile");
+};
 
 template <int kStore, int kW, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
 __global__ void __launch_bounds__(kW) step_tma(const __grid_constant__ CUtensorMap load_map,
                                                const __grid_constant__ CUtensorMap store_map,
                                                const StepParams p) {
   using S = Storage<kStore>;
-  using T = typename S::T;
-  constexpr int kH = S::kHalo;
-  constexpr int kSeg = kW + 2 * kH;                                       // loaded elements
-  constexpr int kRow = ((kSeg * (int)sizeof(T) + 127) / 128 * 128) / (int)sizeof(T);  // row stride
+  using L = TmaLayout<kStore, kW>;
+  using T = typename L::T;
+  constexpr int kH = L::kH;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
-  // rows start on 128-byte boundaries of the shared window (the launch adds 128 bytes)
+  // groups start on 128-byte boundaries of the shared window (the launch adds 128 bytes)
   T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
 
   const int t = threadIdx.x;
@@ -72,30 +73,29 @@ __global__ void __launch_bounds__(kW) step_tma(const __grid_constant__ CUtensorM
   __syncthreads();
   grid_dependency_wait();  // the previous step's writes (our source) are complete
 
-  // population i is fetched by lane i / nw of warp i % nw (spread over the nw warps)
-  constexpr int kWarps = kW / 32;
-  const int my_pop = (t & 31) * kWarps + (t >> 5);
-  T patch = T();
-  int patch_at = -1;
-  if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kQ * kSeg * sizeof(T)));
-  if (my_pop < kQ) {
-    const int i = my_pop;
-    const int cx = comp(kPackCx, i), cy = comp(kPackCy, i), cz = comp(kPackCz, i);
+  // lane g of warp 0 loads the source row of group g = 3 (c_y + 1) + (c_z + 1)
+  T patch_l = T(), patch_r = T();
+  int at_l = -1, at_r = -1;
+  if (t < kGroups) {
+    if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)));
+    const int cy = t / 3 - 1, cz = t % 3 - 1;
     int ys = (int)y - cy, zs = (int)z - cz;
     ys += ys < 0 ? (int)p.geo.ny : 0;
     ys -= ys >= (int)p.geo.ny ? (int)p.geo.ny : 0;
     zs += zs < 0 ? (int)p.geo.nz : 0;
     zs -= zs >= (int)p.geo.nz ? (int)p.geo.nz : 0;
-    tma_load_4d(sm + i * kRow, &load_map, (int)x0 - kH, ys, zs, i, &bar);
-    // periodic x edge: the element left of x = 0 is x = nx - 1, right of nx - 1 is 0
+    tma_load_4d(sm + t * L::kGroup, &load_map, (int)x0 - kH, ys, zs, 3 * t, &bar);
+    // periodic x edge: plane c_x = +1 needs x = nx - 1 left of x = 0, plane c_x = -1
+    // needs x = 0 right of x = nx - 1
     const T* src = static_cast<const T*>(p.src);
-    const int64_t rowoff = (int64_t)i * p.geo.ps + (int64_t)p.geo.nx * ((int64_t)ys + (int64_t)p.geo.ny * zs);
-    if (cx == 1 && x0 == 0) {
-      patch = src[rowoff + (p.geo.nx - 1)];
-      patch_at = i * kRow + kH - 1;
-    } else if (cx == -1 && x0 + kW == p.geo.nx) {
-      patch = src[rowoff];
-      patch_at = i * kRow + kH + kW;
+    const int64_t rowoff = (int64_t)p.geo.nx * ((int64_t)ys + (int64_t)p.geo.ny * zs);
+    if (x0 == 0) {
+      patch_l = src[(int64_t)(3 * t + 2) * p.geo.ps + rowoff + (p.geo.nx - 1)];
+      at_l = t * L::kGroup + 2 * L::kSeg + kH - 1;
+    }
+    if (x0 + kW == p.geo.nx) {
+      patch_r = src[(int64_t)(3 * t) * p.geo.ps + rowoff];
+      at_r = t * L::kGroup + kH + kW;
     }
   }
 
@@ -107,36 +107,33 @@ __global__ void __launch_bounds__(kW) step_tma(const __grid_constant__ CUtensorM
     mbar_wait_bounded(&bar, 0, kMaxPolls);  // let copies in flight land before exiting
     return;
   }
-  if (patch_at >= 0) sm[patch_at] = patch;
+  if (at_l >= 0) sm[at_l] = patch_l;
+  if (at_r >= 0) sm[at_r] = patch_r;
   __syncthreads();
 
   float G[3][3][3];
   const T* mine = sm + kH + t;
 #pragma unroll
-  for (int i = 0; i < kQ; ++i)
-    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = S::load(mine[i * kRow - cx_of(i)], class_of(i), p.ss);
+  for (int i = 0; i < kQ; ++i) {
+    const int gi = 3 * (cy_of(i) + 1) + (cz_of(i) + 1);
+    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] =
+        S::load(mine[gi * L::kGroup + (cx_of(i) + 1) * L::kSeg - cx_of(i)], class_of(i), p.ss);
+  }
 
   collide_site<kModel, kNoise, kGhostNeq, kPhiRho0>(G, p.cp, noise);
 
-  __syncthreads();  // every thread has read its inputs: the rows can hold the outputs
-  T* out = sm + t;  // output row i at the (128-byte aligned) start of shared row i
+  __syncthreads();  // every thread has read its inputs: the tile can hold the outputs
+  T* out = sm + t;  // dense [plane][kW] output tile at the (128-byte aligned) start
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) out[i * kRow] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
+  for (int i = 0; i < kQ; ++i)
+    out[plane_of(i) * kW] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
   fence_proxy_async_smem();
   __syncthreads();
-  if (my_pop < kQ) {
-    tma_store_4d(&store_map, sm + my_pop * kRow, (int)x0, (int)y, (int)z, my_pop);
+  if (t == 0) {
+    tma_store_4d(&store_map, sm, (int)x0, (int)y, (int)z, 0);
     bulk_commit();
     bulk_wait_read();
   }
-}
-
-// Dynamic shared memory of one CTA (27 rows + 128 bytes of alignment slack).
-template <int kStore, int kW>
-constexpr size_t tma_smem_bytes() {
-  using T = typename Storage<kStore>::T;
-  constexpr int kSeg = kW + 2 * Storage<kStore>::kHalo;
-  return (size_t)kQ * ((kSeg * sizeof(T) + 127) / 128 * 128) + 128;
 }
 
 template <int kStore, int kW, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
@@ -147,7 +144,7 @@ cudaError_t launch_tma_segment(const TmaMaps& m, const StepParams& p, cudaStream
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kW);
-  cfg.dynamicSmemBytes = tma_smem_bytes<kStore, kW>();
+  cfg.dynamicSmemBytes = TmaLayout<kStore, kW>::kBytes;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -32,7 +32,6 @@ RFLBM_PHI_RHO0 = 1
 RFLBM_KERNEL_AUTO = 0
 RFLBM_KERNEL_GATHER = 1
 RFLBM_KERNEL_TMA = 2
-RFLBM_KERNEL_TMA_PERSISTENT = 3
 FIELDS = ("rho", "jx", "jy", "jz", "pxx", "pyy", "pzz", "pxy", "pxz", "pyz")
 
 

@@ -103,8 +103,8 @@ def test_16bit_scope_and_paths(R):
     cfg.omega_g, cfg.phi_rho = 1.0, R.RFLBM_PHI_RHO0
     with pytest.raises(R.RflbmError):
         R.rflbm_create_ex(cfg)
-    box = R.Box(128, 2, 2, tau=0.8, storage=R.RFLBM_STORE_BF16, kernel=R.RFLBM_KERNEL_TMA_PERSISTENT)
-    assert R.rflbm_step_path(box.h) == (R.RFLBM_KERNEL_TMA, 128)  # no persistent 16-bit kernel
+    box = R.Box(128, 2, 2, tau=0.8, storage=R.RFLBM_STORE_BF16)
+    assert R.rflbm_step_path(box.h) == (R.RFLBM_KERNEL_TMA, 128)
     box.close()
 
 
