@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--kernel", choices=["auto", "gather", "tma"], default="auto")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--pattern", choices=["pingpong", "aa"], default="pingpong",
+                    help="two population buffers (pull, ping-pong) or one updated in place (AA)")
     ap.add_argument("--init", choices=["rest", "taylor-green"], default="rest",
                     help="rest start, or the Taylor-Green vortex (u0 = 0.01, k = 2 pi / edge)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -61,14 +63,17 @@ STORAGE_NAME = {"f32": "float32", "f16": "float16", "bf16": "bfloat16"}
 
 def workload(args):
     e = args.edge
-    nbytes = 2 * 27 * BYTES_PER_SITE[args.storage] // 54 * e ** 3
+    nbuf = 1 if args.pattern == "aa" else 2
+    nbytes = nbuf * 27 * BYTES_PER_SITE[args.storage] // 54 * e ** 3
     return {"workload": f"periodic {e}^3 Reg-FLBM D3Q27 thermal equilibrium, "
                         f"{STORAGE_NAME[args.storage]} populations, tau {args.tau}, rho0 1, "
                         f"kT {args.kT:g}, seed 1, "
                         + ("rest start" if args.init == "rest" else "Taylor-Green u0 0.01 start"),
             "init": args.init, "box": [e, e, e], "sites": e ** 3, "tau": args.tau, "kT": args.kT,
-            "storage": f"{args.storage} shifted by w_i rho0", "streaming": "pull, ping-pong",
-            "l2": f"inputs {nbytes / 1e6:.0f} MB (two population buffers) > 129 MB L2, no flush",
+            "storage": f"{args.storage} shifted by w_i rho0",
+            "streaming": "pull, ping-pong" if nbuf == 2 else "AA, one buffer in place",
+            "l2": f"inputs {nbytes / 1e6:.0f} MB ({nbuf} population buffer{'s' if nbuf == 2 else ''})"
+                  " > 129 MB L2, no flush",
             "parallelism": "replicas"}
 
 
@@ -93,9 +98,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_name(kind, path, kT, model, storage="f32"):
+def kernel_name(kind, path, kT, model, storage="f32", pattern="pingpong"):
     noise = "noise" if kT > 0 else "no noise"
     m = "BGK" if model else "Reg"
+    if pattern == "aa":
+        if kind == 2:
+            return (f"step_aa_even+step_aa_odd<{storage}, {path}, {m}, {noise}>",
+                    f"step_aa_{storage}_{path}")
+        return f"step_aa_gather<{storage}, {m}, {noise}>", f"step_aa_gather_{storage}"
     if kind == 2:
         return f"step_tma<{storage}, {path}, {m}, {noise}>", f"step_tma_{storage}_{path}"
     return f"step_pull<{storage}, {m}, {noise}>", f"step_pull_{storage}"
@@ -272,9 +282,10 @@ def gb300_arm(args):
     kernel = {"auto": R.RFLBM_KERNEL_AUTO, "gather": R.RFLBM_KERNEL_GATHER,
               "tma": R.RFLBM_KERNEL_TMA}[args.kernel]
     storage = {"f32": R.RFLBM_STORE_F32, "f16": R.RFLBM_STORE_F16, "bf16": R.RFLBM_STORE_BF16}
+    pattern = {"pingpong": R.RFLBM_PATTERN_PINGPONG, "aa": R.RFLBM_PATTERN_AA}[args.pattern]
     box = R.Box(e, e, e, tau=args.tau, kT=args.kT, seed=1, replica=info.rank,
                 stream=stream.cuda_stream, torch_buffers=True, device=info.local_rank,
-                kernel=kernel, storage=storage[args.storage])
+                kernel=kernel, storage=storage[args.storage], pattern=pattern)
     if args.init == "rest":
         R.rflbm_init_rest(box.h)
     else:
@@ -337,7 +348,13 @@ def gb300_arm(args):
                  BYTES_PER_SITE[args.storage]),
                 ("f16_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_F16), 108),
                 ("f16_reg_lbm_kT0", dict(kT=0.0, storage=R.RFLBM_STORE_F16), 108),
-                ("bf16_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_BF16), 108)):
+                ("bf16_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_BF16), 108),
+                ("aa_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_F32,
+                                     pattern=R.RFLBM_PATTERN_AA), 216),
+                ("aa_reg_lbm_kT0", dict(kT=0.0, storage=R.RFLBM_STORE_F32,
+                                        pattern=R.RFLBM_PATTERN_AA), 216),
+                ("aa_f16_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_F16,
+                                         pattern=R.RFLBM_PATTERN_AA), 108)):
             vb = R.Box(e, e, e, tau=args.tau, seed=1, stream=stream.cuda_stream, kernel=kernel, **kw)
             R.rflbm_init_rest(vb.h)
             R.rflbm_step(vb.h, 50)
@@ -379,7 +396,7 @@ def gb300_arm(args):
     per_launch_s = ms * 1e-3 / args.steps
     achieved = BYTES_PER_SITE[args.storage] * n / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
-    kname, kstem = kernel_name(kind, path, args.kT, 0, args.storage)
+    kname, kstem = kernel_name(kind, path, args.kT, 0, args.storage, args.pattern)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(kstem, e),
                 "peak_source": f"hbm_gbs of {peak_kind}", "kernel": kname,

@@ -84,6 +84,21 @@ typedef enum {
   RFLBM_KERNEL_TMA = 2      /* one CTA per row segment, TMA tensor loads and stores */
 } rflbm_kernel;
 
+/* Streaming pattern (Eq. 8 carried out in memory).
+ * PINGPONG: two buffers; a step reads one and writes the other (pull form).
+ * AA: one buffer updated in place, half the memory of PINGPONG. Steps alternate between an
+ * even form, in which a site reads its own 27 slots and writes its post-collision values
+ * back into the slots of the opposite directions, and an odd form, in which it reads the
+ * 27 values its neighbours x - c_i left for it and writes its results into the slots of
+ * the neighbours x + c_i. Every site reads and writes the same set of locations, so the
+ * update is race-free in place. Both patterns compute identical values (same arithmetic,
+ * same Philox counters): only the memory layout between steps differs. AA supports the
+ * paper's configuration (omega_g = 1, local rho in Eq. 10) in every storage format. */
+typedef enum {
+  RFLBM_PATTERN_PINGPONG = 0,
+  RFLBM_PATTERN_AA = 1
+} rflbm_pattern;
+
 typedef struct {
   int nx, ny, nz;        /* box edges, each >= 1; N = nx*ny*nz < 2^31 */
   double tau;            /* hydrodynamic relaxation time tau_h = 1/omega_h > 1/2 */
@@ -97,10 +112,12 @@ typedef struct {
   uint32_t replica;      /* fourth Philox counter word (independent replicas) */
   void* stream;          /* cudaStream_t for all work, NULL = legacy default stream */
   void* buffers[2];      /* optional caller-owned device buffers of
-                            rflbm_buffer_bytes(cfg) bytes each, 256-byte aligned;
+                            rflbm_buffer_bytes(cfg) bytes each, 256-byte aligned
+                            (PINGPONG: both; AA: buffers[0] only, buffers[1] NULL);
                             NULL: the library allocates and frees them */
   int device;            /* CUDA device ordinal, -1 = the current device */
   int kernel;            /* rflbm_kernel */
+  int pattern;           /* rflbm_pattern */
 } rflbm_config_t;
 
 typedef struct {
@@ -113,11 +130,15 @@ typedef struct {
 
 /* Fills cfg with the defaults: 32^3, tau 0.8, kT 0, rho0 1, seed 1, omega_g 1, Reg model,
  * float32 storage, local rho in Eq. 10, replica 0, default stream, library buffers,
- * current device, automatic kernel choice. */
+ * current device, automatic kernel choice, ping-pong streaming. */
 void rflbm_config_default(rflbm_config_t* cfg);
 
-/* Bytes of one population buffer for cfg (two are used, ping-pong), or a negative
- * rflbm_status if cfg is invalid. */
+/* sizeof(rflbm_config_t) as compiled into the library (for bindings to check their
+ * mirror of the struct). */
+int64_t rflbm_config_size(void);
+
+/* Bytes of one population buffer for cfg (two are used with PINGPONG, one with AA), or a
+ * negative rflbm_status if cfg is invalid. */
 int64_t rflbm_buffer_bytes(const rflbm_config_t* cfg);
 
 /* Creates a handle for a periodic box with the paper's defaults (Reg-FLBM, omega_g = 1,
@@ -171,10 +192,13 @@ int rflbm_set_populations_f32(rflbm_t* h, const float* f, int on_device);
 int rflbm_get_sites(rflbm_t* h, const int64_t* sites, int64_t n, double* f);
 
 /* Checkpoint / resume. rflbm_state_bytes: size of the raw storage image of the state
- * (the float32 shifted populations in the library's internal layout). rflbm_save_state
- * copies that image out, rflbm_load_state replaces the state by an image saved from a
- * handle of the same box; with rflbm_set_step and the same seed the run continues
- * bit-identically to an uninterrupted one (the noise is keyed by the step). */
+ * (the shifted populations in the handle's storage format and the library's internal
+ * ping-pong layout, 27 planes of rflbm_buffer_bytes / 27 bytes). rflbm_save_state copies
+ * that image out, rflbm_load_state replaces the state by an image saved from a handle of
+ * the same box and storage format, of either streaming pattern; with rflbm_set_step and
+ * the same seed the run continues bit-identically to an uninterrupted one (the noise is
+ * keyed by the step). An AA handle after an even number of steps since its state was set
+ * writes the image through a one-plane device scratch buffer. */
 int64_t rflbm_state_bytes(const rflbm_t* h);
 int rflbm_save_state(rflbm_t* h, void* image, int on_device);
 int rflbm_load_state(rflbm_t* h, const void* image, int on_device);

@@ -39,6 +39,13 @@ __host__ __device__ constexpr int plane_of(int i) {
   return 3 * (3 * (cy_of(i) + 1) + (cz_of(i) + 1)) + (cx_of(i) + 1);
 }
 
+// Population with the opposite velocity -c_i. Its plane is 26 - plane_of(i).
+__host__ __device__ constexpr int opp_of(int i) {
+  for (int j = 0; j < kQ; ++j)
+    if (cx_of(j) == -cx_of(i) && cy_of(j) == -cy_of(i) && cz_of(j) == -cz_of(i)) return j;
+  return -1;
+}
+
 // 1-D weight W(c) for a tile index a = c + 1.
 __host__ __device__ constexpr double w1d(int a) { return a == 1 ? 2.0 / 3.0 : 1.0 / 6.0; }
 // Lattice weight of population i.
@@ -78,8 +85,8 @@ __host__ __device__ constexpr int mode_of(int p, int q, int r) {
   return t[9 * p + 3 * q + r];
 }
 
-// The two mode tables are inverse to each other, the weights sum to one and the plane map
-// is a permutation.
+// The two mode tables are inverse to each other, the weights sum to one, the plane map is
+// a permutation and opposite populations occupy mirrored planes.
 __host__ __device__ constexpr bool tables_consistent() {
   double wsum = 0.0;
   int seen = 0;
@@ -87,6 +94,7 @@ __host__ __device__ constexpr bool tables_consistent() {
     if (mode_of(p_of(k), q_of(k), r_of(k)) != k) return false;
     wsum += weight_of(k);
     seen |= 1 << plane_of(k);
+    if (opp_of(opp_of(k)) != k || plane_of(opp_of(k)) != kQ - 1 - plane_of(k)) return false;
   }
   return wsum > 1.0 - 1e-12 && wsum < 1.0 + 1e-12 && seen == (1 << kQ) - 1;
 }

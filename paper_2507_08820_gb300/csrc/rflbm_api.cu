@@ -28,7 +28,9 @@ struct rflbm {
   size_t elem = 4;             // bytes per stored population value
   StoreScale ss{};             // 16-bit storage scales (ones for float32)
   bool own_buf = false;
-  int cur = 0;            // buffer holding the current state
+  int cur = 0;            // buffer holding the current state (ping-pong)
+  bool aa = false;        // AA pattern: one buffer (buf[0]) updated in place
+  int phase = 0;          // AA: parity of the steps taken since the state was set
   int64_t step = 0;
   bool initialised = false;
   StepVariant variant{};
@@ -113,6 +115,11 @@ int validate(const rflbm_config_t* c) {
     return fail(RFLBM_EINVAL, "unknown phi_rho option %d", c->phi_rho);
   if (c->kernel < RFLBM_KERNEL_AUTO || c->kernel > RFLBM_KERNEL_TMA)
     return fail(RFLBM_EINVAL, "unknown kernel choice %d", c->kernel);
+  if (c->pattern != RFLBM_PATTERN_PINGPONG && c->pattern != RFLBM_PATTERN_AA)
+    return fail(RFLBM_EINVAL, "unknown streaming pattern %d", c->pattern);
+  if (c->pattern == RFLBM_PATTERN_AA &&
+      ((c->model == RFLBM_MODEL_REG && c->omega_g != 1.0) || c->phi_rho != RFLBM_PHI_LOCAL_RHO))
+    return fail(RFLBM_EINVAL, "the AA pattern supports omega_g = 1 and the local density in Eq. 10 only");
   return RFLBM_OK;
 }
 
@@ -239,7 +246,7 @@ void setup_tma(rflbm* h) {
   if (w == 0 || h->cfg.kernel == RFLBM_KERNEL_GATHER) return;
   const int st = h->variant.storage;
   const uint32_t halo = st == kStoreF32 ? 4 : 8;  // 16 bytes each side
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < (h->aa ? 1 : 2); ++b) {
     // loads: the three planes of one source row; stores: all 27 planes of the segment
     if (!encode_map(&h->load_map[b], h->buf[b], h->geo, (uint32_t)w + 2 * halo, 3, st) ||
         !encode_map(&h->store_map[b], h->buf[b], h->geo, (uint32_t)w, kQ, st))
@@ -250,6 +257,13 @@ void setup_tma(rflbm* h) {
 }
 
 int64_t n_sites(const rflbm* h) { return (int64_t)h->geo.n; }
+
+// The geometry with the view of the current state (where g_i(x) lives in buf[cur]).
+Geometry vgeo(const rflbm* h) {
+  Geometry g = h->geo;
+  g.view = !h->aa ? kViewPull : (h->phase ? kViewFlipped : kViewNatural);
+  return g;
+}
 
 }  // namespace
 
@@ -276,7 +290,10 @@ void rflbm_config_default(rflbm_config_t* cfg) {
   cfg->buffers[0] = cfg->buffers[1] = nullptr;
   cfg->device = -1;
   cfg->kernel = RFLBM_KERNEL_AUTO;
+  cfg->pattern = RFLBM_PATTERN_PINGPONG;
 }
+
+int64_t rflbm_config_size(void) { return (int64_t)sizeof(rflbm_config_t); }
 
 int64_t rflbm_buffer_bytes(const rflbm_config_t* cfg) {
   if (int e = validate(cfg)) return e;
@@ -311,6 +328,8 @@ rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
   }
   h->cfg = *cfg;
   h->device = dev;
+  h->aa = cfg->pattern == RFLBM_PATTERN_AA;
+  const int nbuf = h->aa ? 1 : 2;
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
   h->stream = (cudaStream_t)cfg->stream;
   const int64_t n = (int64_t)cfg->nx * cfg->ny * cfg->nz;
@@ -318,6 +337,7 @@ rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
   g.nx = cfg->nx; g.ny = cfg->ny; g.nz = cfg->nz;
   g.nxy = (uint32_t)cfg->nx * (uint32_t)cfg->ny;
   g.n = (uint32_t)n;
+  g.view = kViewPull;
   g.ps = plane_stride(n);
   g.div_nx = make_fastdiv(g.nx);
   g.div_nxy = make_fastdiv(g.nxy);
@@ -325,18 +345,21 @@ rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
 
   const size_t bytes = (size_t)g.ps * kQ * h->elem;
   if (cfg->buffers[0] || cfg->buffers[1]) {
-    if (!cfg->buffers[0] || !cfg->buffers[1] ||
-        ((uintptr_t)cfg->buffers[0] % 256) || ((uintptr_t)cfg->buffers[1] % 256)) {
-      fail(RFLBM_EINVAL, "caller buffers must both be given and 256-byte aligned");
+    const bool bad = h->aa ? (!cfg->buffers[0] || cfg->buffers[1] || ((uintptr_t)cfg->buffers[0] % 256))
+                           : (!cfg->buffers[0] || !cfg->buffers[1] || ((uintptr_t)cfg->buffers[0] % 256) ||
+                              ((uintptr_t)cfg->buffers[1] % 256));
+    if (bad) {
+      fail(RFLBM_EINVAL, h->aa ? "the AA pattern takes one caller buffer (buffers[0], 256-byte aligned; buffers[1] NULL)"
+                               : "caller buffers must both be given and 256-byte aligned");
       delete h;
       return nullptr;
     }
     h->buf[0] = cfg->buffers[0];
-    h->buf[1] = cfg->buffers[1];
+    h->buf[1] = h->aa ? nullptr : cfg->buffers[1];
     h->own_buf = false;
   } else {
     h->own_buf = true;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < nbuf; ++b) {
       e = cudaMalloc(&h->buf[b], bytes);
       if (e != cudaSuccess) {
         cuda_fail(e, "allocating a population buffer");
@@ -345,8 +368,8 @@ rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
       }
     }
   }
-  // zero both buffers: the plane padding is then deterministic in state images
-  for (int b = 0; b < 2; ++b) {
+  // zero the buffers: the plane padding is then deterministic in state images
+  for (int b = 0; b < nbuf; ++b) {
     e = cudaMemset(h->buf[b], 0, bytes);
     if (e != cudaSuccess) {
       cuda_fail(e, "clearing a population buffer");
@@ -401,6 +424,7 @@ int rflbm_init_rest(rflbm_t* h) {
   RFLBM_CUDA(cudaMemsetAsync(h->buf[0], 0, (size_t)h->geo.ps * kQ * h->elem, h->stream),
              "clearing the populations");
   h->cur = 0;
+  h->phase = 0;
   h->step = 0;
   h->initialised = true;
   return RFLBM_OK;
@@ -424,9 +448,10 @@ int rflbm_init_field(rflbm_t* h, const double* rho, const double* u, int on_devi
       du = st + n;
     }
   }
-  RFLBM_CUDA(launch_init_field(h->geo, h->cp.rho0, h->ss, h->variant.storage, drho, du, h->buf[0], h->stream),
-             "launching init_field");
   h->cur = 0;
+  h->phase = 0;
+  RFLBM_CUDA(launch_init_field(vgeo(h), h->cp.rho0, h->ss, h->variant.storage, drho, du, h->buf[0], h->stream),
+             "launching init_field");
   h->step = 0;
   h->initialised = true;
   if (!on_device) return sync(h, "rflbm_init_field");
@@ -446,10 +471,24 @@ int rflbm_step(rflbm_t* h, int64_t n) {
   p.replica = h->cfg.replica;
   p.err = h->err;
   for (int64_t t = 0; t < n; ++t) {
-    p.src = h->buf[h->cur];
-    p.dst = h->buf[1 - h->cur];
     p.step = (uint32_t)h->step;
     cudaError_t e;
+    if (h->aa) {
+      p.src = p.dst = h->buf[0];
+      const bool odd = h->phase != 0;
+      if (h->tma_width) {
+        const TmaMaps m{&h->load_map[0], &h->store_map[0], h->tma_width};
+        e = launch_step_aa_tma(m, p, h->variant, odd, h->stream);
+      } else {
+        e = launch_step_aa_gather(p, h->variant, odd, h->stream);
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "launching the AA step kernel");
+      h->phase ^= 1;
+      ++h->step;
+      continue;
+    }
+    p.src = h->buf[h->cur];
+    p.dst = h->buf[1 - h->cur];
     if (h->tma_width) {
       const TmaMaps m{&h->load_map[h->cur], &h->store_map[1 - h->cur], h->tma_width};
       e = launch_step_tma(m, p, h->variant, h->stream);
@@ -475,7 +514,7 @@ int rflbm_moments(rflbm_t* h, double* rho, double* u, double* pi, int on_device)
     du = u ? st + n : nullptr;
     dpi = pi ? st + 4 * n : nullptr;
   }
-  RFLBM_CUDA(launch_moments(h->geo, h->cp.rho0, h->ss, h->variant.storage, h->buf[h->cur], drho, du, dpi, h->stream),
+  RFLBM_CUDA(launch_moments(vgeo(h), h->cp.rho0, h->ss, h->variant.storage, h->buf[h->cur], drho, du, dpi, h->stream),
              "launching moments");
   if (!on_device) {
     if (rho) RFLBM_CUDA(cudaMemcpyAsync(rho, drho, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream), "copying rho");
@@ -490,7 +529,7 @@ int rflbm_stats(rflbm_t* h, rflbm_stats_t* out) {
   if (!out) return fail(RFLBM_EINVAL, "stats output is NULL");
   DeviceGuard guard(h->device);
   double* res = h->partials + (size_t)h->stat_blocks * kStatOutFields;
-  RFLBM_CUDA(launch_stats(h->geo, h->cp.rho0, h->ss, h->variant.storage, h->buf[h->cur], h->partials,
+  RFLBM_CUDA(launch_stats(vgeo(h), h->cp.rho0, h->ss, h->variant.storage, h->buf[h->cur], h->partials,
                           h->stat_blocks, res, h->stream),
              "launching stats");
   double host[kStatOutFields];
@@ -521,8 +560,9 @@ static int get_pops(rflbm_t* h, void* f, int on_device, bool f64) {
     dst = h->staging;
   }
   const int st = h->variant.storage;
-  cudaError_t e = f64 ? launch_get_populations_f64(h->geo, h->cp.rho0, h->ss, st, h->buf[h->cur], (double*)dst, h->stream)
-                      : launch_get_populations_f32(h->geo, h->cp.rho0, h->ss, st, h->buf[h->cur], (float*)dst, h->stream);
+  const Geometry g = vgeo(h);
+  cudaError_t e = f64 ? launch_get_populations_f64(g, h->cp.rho0, h->ss, st, h->buf[h->cur], (double*)dst, h->stream)
+                      : launch_get_populations_f32(g, h->cp.rho0, h->ss, st, h->buf[h->cur], (float*)dst, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "launching get_populations");
   if (!on_device) RFLBM_CUDA(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, h->stream), "copying populations");
   return sync(h, "rflbm_get_populations");
@@ -540,12 +580,14 @@ static int set_pops(rflbm_t* h, const void* f, int on_device, bool f64) {
     RFLBM_CUDA(cudaMemcpyAsync(h->staging, f, bytes, cudaMemcpyHostToDevice, h->stream), "copying populations");
     src = h->staging;
   }
-  // the state after this call is step h->step, held in buffer 0
-  const int st = h->variant.storage;
-  cudaError_t e = f64 ? launch_set_populations_f64(h->geo, h->cp.rho0, h->ss, st, (const double*)src, h->buf[0], h->stream)
-                      : launch_set_populations_f32(h->geo, h->cp.rho0, h->ss, st, (const float*)src, h->buf[0], h->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "launching set_populations");
+  // the state after this call is step h->step, held in buffer 0 (AA: natural view)
   h->cur = 0;
+  h->phase = 0;
+  const int st = h->variant.storage;
+  const Geometry g = vgeo(h);
+  cudaError_t e = f64 ? launch_set_populations_f64(g, h->cp.rho0, h->ss, st, (const double*)src, h->buf[0], h->stream)
+                      : launch_set_populations_f32(g, h->cp.rho0, h->ss, st, (const float*)src, h->buf[0], h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "launching set_populations");
   h->initialised = true;
   if (!on_device) return sync(h, "rflbm_set_populations");
   return RFLBM_OK;
@@ -569,7 +611,7 @@ int rflbm_get_sites(rflbm_t* h, const int64_t* sites, int64_t n, double* f) {
   int64_t* dsites = (int64_t*)h->staging;
   double* dout = (double*)((char*)h->staging + bytes_sites);
   RFLBM_CUDA(cudaMemcpyAsync(dsites, sites, bytes_sites, cudaMemcpyHostToDevice, h->stream), "copying sites");
-  RFLBM_CUDA(launch_get_sites(h->geo, h->cp.rho0, h->ss, h->variant.storage, h->buf[h->cur], dsites, n, dout, h->stream),
+  RFLBM_CUDA(launch_get_sites(vgeo(h), h->cp.rho0, h->ss, h->variant.storage, h->buf[h->cur], dsites, n, dout, h->stream),
              "launching get_sites");
   RFLBM_CUDA(cudaMemcpyAsync(f, dout, bytes_out, cudaMemcpyDeviceToHost, h->stream), "copying site populations");
   return sync(h, "rflbm_get_sites");
@@ -593,7 +635,7 @@ int rflbm_mode_sums(rflbm_t* h, double* sum, double* sumsq) {
   const int64_t rows = mode_sum_blocks(h->geo);
   if (int e = ensure_diag_partials(h, sizeof(double) * (size_t)(rows + 1) * 2 * kQ)) return e;
   double* out = h->diag_partials + rows * 2 * kQ;
-  RFLBM_CUDA(launch_mode_sums(h->geo, h->ss, h->variant.storage, h->buf[h->cur], h->diag_partials, out, h->stream),
+  RFLBM_CUDA(launch_mode_sums(vgeo(h), h->ss, h->variant.storage, h->buf[h->cur], h->diag_partials, out, h->stream),
              "launching mode sums");
   double host[2 * kQ];
   RFLBM_CUDA(cudaMemcpyAsync(host, out, sizeof(host), cudaMemcpyDeviceToHost, h->stream), "copying mode sums");
@@ -630,7 +672,7 @@ int rflbm_structure_factor(rflbm_t* h, int field, int nshell, double* s_sum, dou
   const int blocks = std::max(1, std::min(4 * std::max(h->num_sms, 1), (int)((nspec + 255) / 256)));
   if (int e = ensure_diag_partials(h, sizeof(double) * (size_t)(blocks + 1) * 2 * nshell)) return e;
   double* out = h->diag_partials + (size_t)blocks * 2 * nshell;
-  RFLBM_CUDA(launch_field(g, h->ss, h->variant.storage, h->buf[h->cur], field, h->diag_field, h->stream),
+  RFLBM_CUDA(launch_field(vgeo(h), h->ss, h->variant.storage, h->buf[h->cur], field, h->diag_field, h->stream),
              "launching the field kernel");
   if (cufftExecD2Z(h->fft_plan, h->diag_field, (cufftDoubleComplex*)h->diag_spec) != CUFFT_SUCCESS)
     return fail(RFLBM_ECUDA, "cufftExecD2Z failed");
@@ -656,9 +698,35 @@ int rflbm_save_state(rflbm_t* h, void* image, int on_device) {
   if (int e = check_ready(h)) return e;
   if (!image) return fail(RFLBM_EINVAL, "image is NULL");
   DeviceGuard guard(h->device);
-  RFLBM_CUDA(cudaMemcpyAsync(image, h->buf[h->cur], (size_t)rflbm_state_bytes(h),
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream),
-             "copying the state image");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (!h->aa) {
+    RFLBM_CUDA(cudaMemcpyAsync(image, h->buf[h->cur], (size_t)rflbm_state_bytes(h), kind, h->stream),
+               "copying the state image");
+    return sync(h, "rflbm_save_state");
+  }
+  // AA: the image is the pull layout. Flipped view: image plane q = buffer plane 26 - q.
+  // Natural view: image plane P(i) at y = buffer plane P(i) at y + c_i (one shifted copy
+  // per plane through a one-plane scratch buffer).
+  const size_t plane_bytes = (size_t)h->geo.ps * h->elem;
+  char* const img = static_cast<char*>(image);
+  const char* const buf = static_cast<const char*>(h->buf[0]);
+  if (!h->phase) {
+    if (int e = ensure_staging(h, plane_bytes)) return e;
+  }
+  for (int i = 0; i < kQ; ++i) {
+    const int q = plane_of(i);
+    if (h->phase) {
+      RFLBM_CUDA(cudaMemcpyAsync(img + q * plane_bytes, buf + (kQ - 1 - q) * plane_bytes, plane_bytes, kind, h->stream),
+                 "copying a state image plane");
+      continue;
+    }
+    void* out = on_device ? (void*)(img + q * plane_bytes) : h->staging;
+    RFLBM_CUDA(launch_image_plane(h->geo, h->elem, buf + q * plane_bytes, cx_of(i), cy_of(i), cz_of(i), out, h->stream),
+               "launching the image plane kernel");
+    if (!on_device)
+      RFLBM_CUDA(cudaMemcpyAsync(img + q * plane_bytes, h->staging, plane_bytes, cudaMemcpyDeviceToHost, h->stream),
+                 "copying a state image plane");
+  }
   return sync(h, "rflbm_save_state");
 }
 
@@ -666,9 +734,20 @@ int rflbm_load_state(rflbm_t* h, const void* image, int on_device) {
   if (int e = check_handle(h)) return e;
   if (!image) return fail(RFLBM_EINVAL, "image is NULL");
   DeviceGuard guard(h->device);
-  RFLBM_CUDA(cudaMemcpyAsync(h->buf[0], image, (size_t)rflbm_state_bytes(h),
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream),
-             "copying the state image");
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!h->aa) {
+    RFLBM_CUDA(cudaMemcpyAsync(h->buf[0], image, (size_t)rflbm_state_bytes(h), kind, h->stream),
+               "copying the state image");
+  } else {
+    // AA: the pull-layout image becomes the flipped view (buffer plane 26 - q = image plane q)
+    const size_t plane_bytes = (size_t)h->geo.ps * h->elem;
+    const char* const img = static_cast<const char*>(image);
+    char* const buf = static_cast<char*>(h->buf[0]);
+    for (int q = 0; q < kQ; ++q)
+      RFLBM_CUDA(cudaMemcpyAsync(buf + (kQ - 1 - q) * plane_bytes, img + q * plane_bytes, plane_bytes, kind, h->stream),
+                 "copying a state image plane");
+    h->phase = 1;
+  }
   h->cur = 0;
   h->initialised = true;
   return sync(h, "rflbm_load_state");

@@ -29,7 +29,7 @@ __global__ void k_init_field(Geometry g, float rho0, StoreScale ss, const double
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const double f = r * psi(cx_of(i), ux) * psi(cy_of(i), uy) * psi(cz_of(i), uz);
-    dst[plane_of(i) * g.ps + pull_site(nb, i)] = S::store((float)(f - weight_of(i) * (double)rho0), class_of(i), ss);
+    dst[pop_slot(g, nb, site_of(s), i)] = S::store((float)(f - weight_of(i) * (double)rho0), class_of(i), ss);
   }
 }
 
@@ -44,7 +44,7 @@ __global__ void k_set_populations(Geometry g, float rho0, StoreScale ss, const T
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const Tin v = f[i * (int64_t)g.n + s] - (Tin)(weight_of(i) * (double)rho0);
-    dst[plane_of(i) * g.ps + pull_site(nb, i)] = S::store((float)v, class_of(i), ss);
+    dst[pop_slot(g, nb, site_of(s), i)] = S::store((float)v, class_of(i), ss);
   }
 }
 
@@ -57,7 +57,7 @@ __global__ void k_get_populations(Geometry g, float rho0, StoreScale ss,
   const Neighbours nb = neighbours(site_of(s), g);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const float v = S::load(src[plane_of(i) * g.ps + pull_site(nb, i)], class_of(i), ss);
+    const float v = S::load(src[pop_slot(g, nb, site_of(s), i)], class_of(i), ss);
     f[i * (int64_t)g.n + s] = (Tout)v + (Tout)(weight_of(i) * (double)rho0);
   }
 }
@@ -69,10 +69,11 @@ __global__ void k_get_sites(Geometry g, float rho0, StoreScale ss,
   using S = Storage<kStore>;
   const int64_t j = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
   if (j >= n) return;
-  const Neighbours nb = neighbours(site_of(sites[j]), g);
+  const uint32_t s = site_of(sites[j]);
+  const Neighbours nb = neighbours(s, g);
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    f[i * n + j] = (double)S::load(src[plane_of(i) * g.ps + pull_site(nb, i)], class_of(i), ss) +
+    f[i * n + j] = (double)S::load(src[pop_slot(g, nb, s, i)], class_of(i), ss) +
                    weight_of(i) * (double)rho0;
   }
 }
@@ -85,14 +86,15 @@ struct SiteMoments {
 };
 
 template <int kStore, class Acc>
-__device__ __forceinline__ SiteMoments site_moments(const Neighbours& nb,
+__device__ __forceinline__ SiteMoments site_moments(const Geometry& g, uint32_t s,
                                                     const typename Storage<kStore>::T* src,
-                                                    int64_t ps, const StoreScale& ss) {
+                                                    const StoreScale& ss) {
+  const Neighbours nb = neighbours(s, g);
   using S = Storage<kStore>;
   Acc drho = 0, j0 = 0, j1 = 0, j2 = 0, s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const Acc v = (Acc)S::load(src[plane_of(i) * ps + pull_site(nb, i)], class_of(i), ss);
+    const Acc v = (Acc)S::load(src[pop_slot(g, nb, s, i)], class_of(i), ss);
     const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     drho += v;
     if (cx) j0 += cx * v;
@@ -118,7 +120,7 @@ __global__ void k_moments(Geometry g, float rho0, StoreScale ss,
                           double* __restrict__ rho, double* __restrict__ u, double* __restrict__ pi) {
   const int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
   if (s >= g.n) return;
-  const SiteMoments m = site_moments<kStore, double>(neighbours(site_of(s), g), src, g.ps, ss);
+  const SiteMoments m = site_moments<kStore, double>(g, site_of(s), src, ss);
   const double r = (double)rho0 + m.drho;
   if (rho) rho[s] = r;
   if (u) {
@@ -154,7 +156,7 @@ __global__ void k_stats_partial(Geometry g, float rho0, StoreScale ss,
   double acc[kStatFields] = {0, 0, 0, 0, 0, 0};
   for (int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x; s < g.n;
        s += (int64_t)gridDim.x * kAuxBlock) {
-    const SiteMoments m = site_moments<kStore, float>(neighbours(site_of(s), g), src, g.ps, ss);
+    const SiteMoments m = site_moments<kStore, float>(g, site_of(s), src, ss);
     const double r = (double)rho0 + m.drho;
     const bool finite = isfinite(m.drho) && isfinite(m.j[0]) && isfinite(m.j[1]) &&
                         isfinite(m.j[2]);
@@ -214,6 +216,22 @@ __global__ void k_site_normals(uint32_t k0, uint32_t k1, uint32_t step, uint32_t
   site_noise(sites[j], step, replica, k0, k1, nz);
 #pragma unroll
   for (int m = 0; m < 24; ++m) out[24 * j + m] = normal_at(nz, m);
+}
+
+// ---------------------------------------------------------------- state images
+// One plane of a state image (pull layout) from the plane of population i of a buffer in
+// the natural view: out[y] = plane[y + c_i] under periodic wrap, zeros in the padding.
+template <class E>
+__global__ void k_image_plane(Geometry g, const E* __restrict__ plane, int cx, int cy, int cz,
+                              E* __restrict__ out) {
+  const int64_t y = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+  if (y >= g.ps) return;
+  if (y >= g.n) {
+    out[y] = E(0);
+    return;
+  }
+  const Neighbours nb = neighbours((uint32_t)y, g);  // X[a], Y[b], Z[c]: coordinate - (a - 1)
+  out[y] = plane[nb.X[1 - cx] + nb.Y[1 - cy] + nb.Z[1 - cz]];
 }
 
 // ---------------------------------------------------------------- launchers
@@ -276,6 +294,16 @@ cudaError_t launch_stats(const Geometry& g, float rho0, const StoreScale& ss, in
                          cudaStream_t st) {
   RFLBM_STORE_DISPATCH(kind, (k_stats_partial<K><<<nblocks, kAuxBlock, 0, st>>>(g, rho0, ss, (const ST<K>*)src, partials)));
   k_stats_final<<<kStatFields, 32, 0, st>>>(partials, nblocks, out6);
+  return cudaGetLastError();
+}
+cudaError_t launch_image_plane(const Geometry& g, size_t elem, const void* plane, int cx, int cy, int cz,
+                               void* out, cudaStream_t st) {
+  if (elem == 4)
+    k_image_plane<uint32_t><<<blocks_for(g.ps), kAuxBlock, 0, st>>>(g, (const uint32_t*)plane, cx, cy, cz, (uint32_t*)out);
+  else if (elem == 2)
+    k_image_plane<uint16_t><<<blocks_for(g.ps), kAuxBlock, 0, st>>>(g, (const uint16_t*)plane, cx, cy, cz, (uint16_t*)out);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,

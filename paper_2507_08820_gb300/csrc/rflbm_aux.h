@@ -29,6 +29,10 @@ int stats_partial_blocks(const Geometry& g, int num_sms);
 cudaError_t launch_stats(const Geometry& g, float rho0, const StoreScale& ss, int kind,
                          const void* src, double* partials, int nblocks, double* out6,
                          cudaStream_t st);
+// One plane of a state image (pull layout) from the plane of a population with velocity
+// (cx, cy, cz) held in the natural view; elem = 4 or 2 bytes per value.
+cudaError_t launch_image_plane(const Geometry& g, size_t elem, const void* plane, int cx, int cy, int cz,
+                               void* out, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                           int64_t n, cudaStream_t st);
 cudaError_t launch_site_normals(uint32_t k0, uint32_t k1, uint32_t step, uint32_t replica,

@@ -364,6 +364,7 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
     const rflbm_replica_t& c = reps[r];
     Geometry& g = d.geo;
     g.nx = c.nx; g.ny = c.ny; g.nz = c.nz;
+    g.view = kViewPull;
     g.nxy = (uint32_t)c.nx * (uint32_t)c.ny;
     g.n = (uint32_t)((int64_t)c.nx * c.ny * c.nz);
     g.ps = pstride(g.n);

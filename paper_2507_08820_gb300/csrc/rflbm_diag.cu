@@ -51,7 +51,7 @@ __device__ __forceinline__ void gather_tile(const typename Storage<kStore>::T* _
 #pragma unroll
   for (int i = 0; i < kQ; ++i)
     G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] =
-        Storage<kStore>::load(src[plane_of(i) * g.ps + pull_site(nb, i)], class_of(i), ss);
+        Storage<kStore>::load(src[pop_slot(g, nb, s, i)], class_of(i), ss);
 }
 
 // Each thread accumulates up to kDiagSitesPerThread sites in float32, then the block sums
@@ -120,7 +120,7 @@ __global__ void k_field(Geometry g, StoreScale ss, const typename Storage<kStore
   float v = 0.0f, drho = 0.0f;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
-    const float x = Storage<kStore>::load(src[plane_of(i) * g.ps + pull_site(nb, i)], class_of(i), ss);
+    const float x = Storage<kStore>::load(src[pop_slot(g, nb, (uint32_t)s, i)], class_of(i), ss);
     const int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
     float w;
     switch (field) {
@@ -145,35 +145,54 @@ __global__ void k_field(Geometry g, StoreScale ss, const typename Storage<kStore
 
 // Shell sums of |F(k)|^2 / N over the half spectrum of a D2Z transform (kx = 0 .. nx/2),
 // each non-redundant vector counted twice. Shell n = round(|k| L / 2 pi) with
-// L = max(nx, ny, nz). Per-block partial bins in shared memory, then one partial row.
+// L = max(nx, ny, nz). The sums are reproducible bit for bit: each warp owns a row of
+// shell bins in shared memory and its lanes add to it one after another in lane order,
+// over a fixed assignment of spectrum entries to warps; the rows are then summed in warp
+// order into the block's partial row. (Counts are small integers, exact in any order.)
 __global__ void k_shell_bins(Geometry g, const cufftDoubleComplex* __restrict__ spec, int nshell,
                              double* __restrict__ partials) {
-  extern __shared__ double bins[];  // [2 * nshell]: sums, counts
-  for (int j = threadIdx.x; j < 2 * nshell; j += blockDim.x) bins[j] = 0.0;
+  extern __shared__ double bins[];  // [nwarps][nshell] sums, then [nshell] counts
+  const int nw = blockDim.x / 32, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = threadIdx.x; j < (nw + 1) * nshell; j += blockDim.x) bins[j] = 0.0;
   __syncthreads();
+  double* const mine = bins + (size_t)wid * nshell;
+  double* const counts = bins + (size_t)nw * nshell;
   const int nxh = g.nx / 2 + 1;
   const int64_t total = (int64_t)g.nz * g.ny * nxh;
   const double L = (double)max(g.nx, max(g.ny, g.nz));
   const double inv_n = 1.0 / (double)g.n;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int kx = (int)(idx % nxh);
-    const int ky = (int)((idx / nxh) % g.ny);
-    const int kz = (int)(idx / ((int64_t)nxh * g.ny));
-    const double fx = (double)kx / g.nx;
-    const double fy = (double)(ky <= (int)g.ny / 2 ? ky : ky - (int)g.ny) / g.ny;
-    const double fz = (double)(kz <= (int)g.nz / 2 ? kz : kz - (int)g.nz) / g.nz;
-    const int shell = (int)llrint(L * sqrt(fx * fx + fy * fy + fz * fz));
-    if (shell >= nshell) continue;
-    const bool self = (kx == 0) || ((g.nx % 2 == 0) && kx == (int)g.nx / 2);
-    const double w = self ? 1.0 : 2.0;
-    const cufftDoubleComplex c = spec[idx];
-    atomicAdd(&bins[shell], w * (c.x * c.x + c.y * c.y) * inv_n);
-    atomicAdd(&bins[nshell + shell], w);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t wbase = (int64_t)blockIdx.x * blockDim.x + 32 * wid; wbase < total; wbase += stride) {
+    const int64_t idx = wbase + lane;  // warp-uniform trip count
+    int shell = nshell;
+    double v = 0.0, w = 0.0;
+    if (idx < total) {
+      const int kx = (int)(idx % nxh);
+      const int ky = (int)((idx / nxh) % g.ny);
+      const int kz = (int)(idx / ((int64_t)nxh * g.ny));
+      const double fx = (double)kx / g.nx;
+      const double fy = (double)(ky <= (int)g.ny / 2 ? ky : ky - (int)g.ny) / g.ny;
+      const double fz = (double)(kz <= (int)g.nz / 2 ? kz : kz - (int)g.nz) / g.nz;
+      shell = (int)llrint(L * sqrt(fx * fx + fy * fy + fz * fz));
+      const bool self = (kx == 0) || ((g.nx % 2 == 0) && kx == (int)g.nx / 2);
+      w = self ? 1.0 : 2.0;
+      const cufftDoubleComplex c = spec[idx];
+      v = w * (c.x * c.x + c.y * c.y) * inv_n;
+    }
+    const bool ok = shell < nshell;
+    if (ok) atomicAdd(&counts[shell], w);
+    for (int src = 0; src < 32; ++src) {
+      if (lane == src && ok) mine[shell] += v;
+      __syncwarp();
+    }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < 2 * nshell; j += blockDim.x)
-    partials[(int64_t)blockIdx.x * 2 * nshell + j] = bins[j];
+  for (int j = threadIdx.x; j < nshell; j += blockDim.x) {
+    double sum = 0.0;
+    for (int k = 0; k < nw; ++k) sum += bins[(size_t)k * nshell + j];
+    partials[(int64_t)blockIdx.x * 2 * nshell + j] = sum;
+    partials[(int64_t)blockIdx.x * 2 * nshell + nshell + j] = counts[j];
+  }
 }
 
 int64_t mode_sum_blocks(const Geometry& g) {
@@ -211,7 +230,12 @@ cudaError_t launch_field(const Geometry& g, const StoreScale& ss, int kind, cons
 
 cudaError_t launch_shell_bins(const Geometry& g, const void* spec, int nshell, int blocks,
                               double* partials, double* out, cudaStream_t st) {
-  const size_t smem = sizeof(double) * 2 * (size_t)nshell;
+  // kDiagBlock / 32 rows of sums + one row of counts: up to 221 KB at nshell = 3072
+  const size_t smem = sizeof(double) * (size_t)(kDiagBlock / 32 + 1) * (size_t)nshell;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_shell_bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   k_shell_bins<<<blocks, kDiagBlock, smem, st>>>(g, (const cufftDoubleComplex*)spec, nshell, partials);
   k_reduce_columns<<<2 * nshell, 32, 0, st>>>(partials, blocks, 2 * nshell, out);
   return cudaGetLastError();

@@ -30,12 +30,22 @@ __device__ __forceinline__ uint32_t fastdiv(uint32_t n, const FastDiv& f) {
   return (uint32_t)(((unsigned long long)n * f.m) >> f.shift);
 }
 
-// Geometry of a box in the pull layout: plane i of a population buffer holds, at site y,
-// the shifted value f_i(y + c_i, t) - w_i rho0 (the post-collision value of step t - 1
-// at y), so that the pre-collision tile of site x is gathered from x - c_i.
+// Where the pre-collision value g_i(x, t) = f_i(x, t) - w_i rho0 of site x lives in a
+// population buffer between steps (P = plane_of):
+//  - kViewPull: plane P(i) at x - c_i (the post-collision value of step t - 1 at x - c_i).
+//    The ping-pong pattern, and the layout of state images.
+//  - kViewNatural: plane P(i) at x. The AA pattern after an even number of steps.
+//  - kViewFlipped: plane P(opp(i)) = 26 - P(i) at x - c_i. The AA pattern after an odd
+//    number of steps (the even form wrote each value into the opposite slot).
+constexpr uint32_t kViewPull = 0;
+constexpr uint32_t kViewNatural = 1;
+constexpr uint32_t kViewFlipped = 2;
+
+// Geometry of a box and the view of its buffer.
 struct Geometry {
   uint32_t nx, ny, nz, nxy, n;
-  int64_t ps;  // plane stride in elements (n rounded up to 64)
+  uint32_t view;  // kViewPull / kViewNatural / kViewFlipped (read by the non-step kernels)
+  int64_t ps;     // plane stride in elements (n rounded up to 64)
   FastDiv div_nx, div_nxy;
 };
 
@@ -65,6 +75,13 @@ __device__ __forceinline__ uint32_t pull_site(const Neighbours& nb, int i) {
   return nb.X[cx_of(i) + 1] + nb.Y[cy_of(i) + 1] + nb.Z[cz_of(i) + 1];
 }
 
+// Element offset of g_i(s, t) in a buffer of view g.view (nb = neighbours(s, g)).
+__device__ __forceinline__ int64_t pop_slot(const Geometry& g, const Neighbours& nb, uint32_t s, int i) {
+  if (g.view == kViewNatural) return plane_of(i) * g.ps + s;
+  const int plane = g.view == kViewFlipped ? kQ - 1 - plane_of(i) : plane_of(i);
+  return plane * g.ps + pull_site(nb, i);
+}
+
 // Signed offsets from site s to its periodic neighbours, per axis and per direction of
 // the pulled population: D?[a] is the offset of the coordinate minus (a - 1), so the
 // pull source x - c_i of population i is s + DX[cx+1] + DY[cy+1] + DZ[cz+1].
@@ -72,11 +89,7 @@ struct PullDeltas {
   int32_t DX[3], DY[3], DZ[3];
 };
 
-__device__ __forceinline__ PullDeltas pull_deltas(uint32_t s, const Geometry& g) {
-  const uint32_t z = fastdiv(s, g.div_nxy);
-  const uint32_t rem = s - z * g.nxy;
-  const uint32_t y = fastdiv(rem, g.div_nx);
-  const uint32_t x = rem - y * g.nx;
+__device__ __forceinline__ PullDeltas deltas_at(uint32_t x, uint32_t y, uint32_t z, const Geometry& g) {
   const int32_t nx = (int32_t)g.nx, nxy = (int32_t)g.nxy, nyz = nxy * ((int32_t)g.nz - 1);
   PullDeltas d;
   d.DX[1] = 0;
@@ -91,8 +104,20 @@ __device__ __forceinline__ PullDeltas pull_deltas(uint32_t s, const Geometry& g)
   return d;
 }
 
+__device__ __forceinline__ PullDeltas pull_deltas(uint32_t s, const Geometry& g) {
+  const uint32_t z = fastdiv(s, g.div_nxy);
+  const uint32_t rem = s - z * g.nxy;
+  const uint32_t y = fastdiv(rem, g.div_nx);
+  return deltas_at(rem - y * g.nx, y, z, g);
+}
+
 __device__ __forceinline__ int32_t pull_delta(const PullDeltas& d, int i) {
   return d.DX[cx_of(i) + 1] + d.DY[cy_of(i) + 1] + d.DZ[cz_of(i) + 1];
+}
+
+// Offset to x + c_i, the site that receives population i of x (push).
+__device__ __forceinline__ int32_t push_delta(const PullDeltas& d, int i) {
+  return d.DX[1 - cx_of(i)] + d.DY[1 - cy_of(i)] + d.DZ[1 - cz_of(i)];
 }
 
 struct StepParams {
@@ -130,6 +155,13 @@ int record_error(int code, const char* msg, const char* detail);
 
 // Launches one step of the general gather kernel (any box) on `stream`.
 cudaError_t launch_step_gather(const StepParams& p, const StepVariant& v, cudaStream_t stream);
+// One in-place AA step of the general kernel on the buffer p.dst (== p.src): the even form
+// (odd = false) or the odd form. Paper configuration only (no ghost_neq, no phi_rho0).
+cudaError_t launch_step_aa_gather(const StepParams& p, const StepVariant& v, bool odd, cudaStream_t stream);
+// One in-place AA step of the TMA kernels: the even form uses m.store (27-plane box) for
+// its load and its store; the odd form uses m.load (three-plane boxes with halo).
+cudaError_t launch_step_aa_tma(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
+                               cudaStream_t stream);
 
 // Row-segment width of the TMA step kernels for a box of x edge nx (0: not supported).
 int tma_segment_width(uint32_t nx);

@@ -41,6 +41,73 @@ __global__ void __launch_bounds__(kStepBlock) step_pull(const StepParams p) {
     dst[plane_of(i) * p.geo.ps] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
 }
 
+// One in-place step of the AA pattern (even or odd form, see step_aa.cuh) for any box.
+// Plain loads: the buffer is written during the kernel (each slot by the one thread that
+// read it), so the read-only path does not apply.
+template <int kStore, bool kOdd, int kModel, bool kNoise>
+__global__ void __launch_bounds__(kStepBlock) step_aa_gather(const StepParams p) {
+  using S = Storage<kStore>;
+  using T = typename S::T;
+  const uint32_t s = blockIdx.x * kStepBlock + threadIdx.x;
+  if (s >= p.geo.n) return;
+  T* const buf = static_cast<T*>(p.dst) + s;
+  PullDeltas d{};
+  if (kOdd) d = pull_deltas(s, p.geo);
+
+  float G[3][3][3];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    // even: own slot of plane P(i); odd: plane 26 - P(i) at x - c_i
+    const int64_t at = kOdd ? (int64_t)(kQ - 1 - plane_of(i)) * p.geo.ps + pull_delta(d, i)
+                            : (int64_t)plane_of(i) * p.geo.ps;
+    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = S::load(buf[at], class_of(i), p.ss);
+  }
+
+  SiteNoise noise;
+  if (kNoise) site_noise(s, p.step, p.replica, p.key0, p.key1, noise);
+
+  collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
+
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    // even: own slot of plane 26 - P(i); odd: plane P(i) at x + c_i
+    const int64_t at = kOdd ? (int64_t)plane_of(i) * p.geo.ps + push_delta(d, i)
+                            : (int64_t)(kQ - 1 - plane_of(i)) * p.geo.ps;
+    buf[at] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
+  }
+}
+
+template <int kStore, bool kOdd, int kModel, bool kNoise>
+static cudaError_t launch_aa(const StepParams& p, cudaStream_t stream) {
+  const uint32_t blocks = (p.geo.n + kStepBlock - 1) / kStepBlock;
+  step_aa_gather<kStore, kOdd, kModel, kNoise><<<blocks, kStepBlock, 0, stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <int kStore, bool kOdd>
+static cudaError_t launch_aa_model(const StepParams& p, const StepVariant& v, cudaStream_t stream) {
+  if (v.model == kModelBgk)
+    return v.noise ? launch_aa<kStore, kOdd, kModelBgk, true>(p, stream)
+                   : launch_aa<kStore, kOdd, kModelBgk, false>(p, stream);
+  return v.noise ? launch_aa<kStore, kOdd, kModelReg, true>(p, stream)
+                 : launch_aa<kStore, kOdd, kModelReg, false>(p, stream);
+}
+
+template <int kStore>
+static cudaError_t launch_aa_gather_storage(const StepParams& p, const StepVariant& v, bool odd, cudaStream_t stream) {
+  return odd ? launch_aa_model<kStore, true>(p, v, stream) : launch_aa_model<kStore, false>(p, v, stream);
+}
+
+cudaError_t launch_step_aa_gather(const StepParams& p, const StepVariant& v, bool odd, cudaStream_t stream) {
+  if (v.ghost_neq || v.phi_rho0) return cudaErrorInvalidValue;
+  switch (v.storage) {
+    case kStoreF32: return launch_aa_gather_storage<kStoreF32>(p, v, odd, stream);
+    case kStoreF16: return launch_aa_gather_storage<kStoreF16>(p, v, odd, stream);
+    case kStoreBF16: return launch_aa_gather_storage<kStoreBF16>(p, v, odd, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int kStore, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
 static cudaError_t launch(const StepParams& p, cudaStream_t stream) {
   const uint32_t blocks = (p.geo.n + kStepBlock - 1) / kStepBlock;

@@ -1,0 +1,245 @@
+// The fused stream-and-collide step in the AA pattern: one population buffer updated in
+// place, with TMA staging; for boxes whose x edge is a multiple of the row-segment width
+// kW in {32, 64, 128}; templated on the storage format.
+//
+// Between steps the buffer alternates between two views of the same populations
+// (P = plane_of, opp(i) the population with velocity -c_i, P(opp(i)) = 26 - P(i)):
+//   after an even number of steps g_i(x) sits in plane P(i) at x        (natural view),
+//   after an odd number              g_i(x) sits in plane 26 - P(i) at x - c_i (flipped).
+// Even form: a site reads its 27 values from its own slots and writes its post-collision
+// value of population i into its own slot of plane 26 - P(i). Streaming is deferred: that
+// is where the next (odd) step of site x + c_i looks for it.
+// Odd form: a site reads g_i from plane 26 - P(i) at x - c_i and writes its post-collision
+// value of population i into plane P(i) at x + c_i, where the next (even) step of that
+// site reads it as its own. The 27 locations a site reads are the 27 it writes (with
+// j = opp(i): plane P(j) at x - c_j), so each step is race-free in place.
+//
+// Each step computes exactly what the ping-pong kernel computes (same tile order, same
+// arithmetic, same Philox counters (site, step)): the two patterns give bit-identical
+// populations. One CTA of kW threads updates one row segment [x0, x0 + kW) of row (y, z).
+//  - Even: one TMA load and one TMA store of the 27-plane box (x0, y, z, 0..26).
+//  - Odd: 9 three-plane TMA loads with a 16-byte halo, one per source row
+//    (y - c_y, z - c_z), as in the ping-pong kernel but of the mirrored plane group; the
+//    results go straight to the neighbours x + c_i with coalesced stores (the x shift of
+//    one element rules out aligned tensor stores, and the halo of a box would overwrite
+//    slots of the neighbouring segments).
+// Both forms use programmatic dependent launch and bounded mbarrier waits like the
+// ping-pong kernel: global memory is touched only after griddepcontrol.wait, so an in-place
+// step never overlaps the previous one.
+#pragma once
+
+#include "step_tma.cuh"
+
+namespace rflbm_dev {
+
+template <int kStore, int kW>
+struct AaEvenLayout {
+  using T = typename Storage<kStore>::T;
+  static constexpr size_t kTileBytes = (size_t)kQ * kW * sizeof(T);
+  static constexpr size_t kBytes = kTileBytes + 128;  // + alignment slack
+};
+
+template <int kStore, int kW, int kModel, bool kNoise>
+__global__ void __launch_bounds__(kW) step_aa_even(const __grid_constant__ CUtensorMap map,
+                                                   const StepParams p) {
+  using S = Storage<kStore>;
+  using T = typename S::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+
+  const int t = threadIdx.x;
+  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t row = blockIdx.x / nseg;
+  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
+
+  grid_launch_dependents();
+  const uint32_t s = x0 + t + p.geo.nx * row;
+  SiteNoise noise;
+  if (kNoise) site_noise_part<0, 3>(s, p.step, p.replica, p.key0, p.key1, noise);
+
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  grid_dependency_wait();
+
+  if (t == 0) {
+    mbar_arrive_expect_tx(&bar, (uint32_t)AaEvenLayout<kStore, kW>::kTileBytes);
+    tma_load_4d(sm, &map, (int)x0, (int)y, (int)z, 0, &bar);
+  }
+
+  if (kNoise) site_noise_part<3, 6>(s, p.step, p.replica, p.key0, p.key1, noise);
+
+  const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
+  if (__syncthreads_or(!ok)) {
+    if (t == 0) atomicOr(p.err, 1);
+    mbar_wait_bounded(&bar, 0, kMaxPolls);
+    return;
+  }
+
+  float G[3][3][3];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i)
+    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = S::load(sm[plane_of(i) * kW + t], class_of(i), p.ss);
+
+  collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
+
+  __syncthreads();  // all inputs are in registers: the tile can take the outputs
+#pragma unroll
+  for (int i = 0; i < kQ; ++i)
+    sm[(kQ - 1 - plane_of(i)) * kW + t] =
+        S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (t == 0) {
+    tma_store_4d(&map, sm, (int)x0, (int)y, (int)z, 0);
+    bulk_commit();
+    bulk_wait_read();
+  }
+}
+
+template <int kStore, int kW, int kModel, bool kNoise>
+__global__ void __launch_bounds__(kW) step_aa_odd(const __grid_constant__ CUtensorMap load_map,
+                                                  const StepParams p) {
+  using S = Storage<kStore>;
+  using L = TmaLayout<kStore, kW>;
+  using T = typename L::T;
+  constexpr int kH = L::kH;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+
+  const int t = threadIdx.x;
+  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t row = blockIdx.x / nseg;
+  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
+
+  grid_launch_dependents();
+  const uint32_t x = x0 + t;
+  const uint32_t s = x + p.geo.nx * row;
+  SiteNoise noise;
+  if (kNoise) site_noise_part<0, 3>(s, p.step, p.replica, p.key0, p.key1, noise);
+
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  grid_dependency_wait();
+
+  // lane g of warp 0 loads source row (y - c_y, z - c_z) of group g = 3 (c_y + 1) + (c_z + 1):
+  // the populations with velocity -c live in the mirrored group 8 - g, in-group order
+  // -c_x = -1, 0, +1, i.e. position 1 - c_x for the population with x velocity c_x
+  T* const buf = static_cast<T*>(p.dst);
+  T patch_l = T(), patch_r = T();
+  int at_l = -1, at_r = -1;
+  if (t < kGroups) {
+    if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)));
+    const int cy = t / 3 - 1, cz = t % 3 - 1;
+    int ys = (int)y - cy, zs = (int)z - cz;
+    ys += ys < 0 ? (int)p.geo.ny : 0;
+    ys -= ys >= (int)p.geo.ny ? (int)p.geo.ny : 0;
+    zs += zs < 0 ? (int)p.geo.nz : 0;
+    zs -= zs >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+    const int mirror = kGroups - 1 - t;
+    tma_load_4d(sm + t * L::kGroup, &load_map, (int)x0 - kH, ys, zs, 3 * mirror, &bar);
+    // periodic x edge: c_x = +1 (position 0) needs x = nx - 1 left of x = 0; c_x = -1
+    // (position 2) needs x = 0 right of x = nx - 1. These slots belong to this segment.
+    const int64_t rowoff = (int64_t)p.geo.nx * ((int64_t)ys + (int64_t)p.geo.ny * zs);
+    if (x0 == 0) {
+      patch_l = buf[(int64_t)(3 * mirror) * p.geo.ps + rowoff + (p.geo.nx - 1)];
+      at_l = t * L::kGroup + kH - 1;
+    }
+    if (x0 + kW == p.geo.nx) {
+      patch_r = buf[(int64_t)(3 * mirror + 2) * p.geo.ps + rowoff];
+      at_r = t * L::kGroup + 2 * L::kSeg + kH + kW;
+    }
+  }
+
+  if (kNoise) site_noise_part<3, 6>(s, p.step, p.replica, p.key0, p.key1, noise);
+  const PullDeltas d = deltas_at(x, y, z, p.geo);
+
+  const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
+  if (__syncthreads_or(!ok)) {
+    if (t == 0) atomicOr(p.err, 1);
+    mbar_wait_bounded(&bar, 0, kMaxPolls);
+    return;
+  }
+  if (at_l >= 0) sm[at_l] = patch_l;
+  if (at_r >= 0) sm[at_r] = patch_r;
+  __syncthreads();
+
+  float G[3][3][3];
+  const T* mine = sm + kH + t;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const int gi = 3 * (cy_of(i) + 1) + (cz_of(i) + 1);
+    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] =
+        S::load(mine[gi * L::kGroup + (1 - cx_of(i)) * L::kSeg - cx_of(i)], class_of(i), p.ss);
+  }
+
+  collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
+
+  // population i of x goes to plane P(i) at x + c_i
+  T* const dst = buf + s;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i)
+    dst[plane_of(i) * p.geo.ps + push_delta(d, i)] =
+        S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
+}
+
+template <int kStore, int kW, int kModel, bool kNoise>
+cudaError_t launch_aa_segment(const TmaMaps& m, const StepParams& p, bool odd, cudaStream_t st) {
+  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.geo.ny * p.geo.nz;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kW);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (odd) {
+    cfg.dynamicSmemBytes = TmaLayout<kStore, kW>::kBytes;
+    return cudaLaunchKernelEx(&cfg, step_aa_odd<kStore, kW, kModel, kNoise>, *m.load, p);
+  }
+  cfg.dynamicSmemBytes = AaEvenLayout<kStore, kW>::kBytes;
+  return cudaLaunchKernelEx(&cfg, step_aa_even<kStore, kW, kModel, kNoise>, *m.store, p);
+}
+
+template <int kStore, int kW>
+cudaError_t launch_aa_variant(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
+                              cudaStream_t st) {
+  if (v.ghost_neq || v.phi_rho0) return cudaErrorInvalidValue;
+  if (v.model == kModelBgk)
+    return v.noise ? launch_aa_segment<kStore, kW, kModelBgk, true>(m, p, odd, st)
+                   : launch_aa_segment<kStore, kW, kModelBgk, false>(m, p, odd, st);
+  return v.noise ? launch_aa_segment<kStore, kW, kModelReg, true>(m, p, odd, st)
+                 : launch_aa_segment<kStore, kW, kModelReg, false>(m, p, odd, st);
+}
+
+template <int kStore>
+cudaError_t launch_aa_storage(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
+                              cudaStream_t st) {
+  switch (m.width) {
+    case 128: return launch_aa_variant<kStore, 128>(m, p, v, odd, st);
+    case 64: return launch_aa_variant<kStore, 64>(m, p, v, odd, st);
+    case 32: return launch_aa_variant<kStore, 32>(m, p, v, odd, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Per-storage entry points (one translation unit each).
+cudaError_t launch_step_aa_tma_f32(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
+                                   cudaStream_t st);
+cudaError_t launch_step_aa_tma_f16(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
+                                   cudaStream_t st);
+cudaError_t launch_step_aa_tma_bf16(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
+                                    cudaStream_t st);
+
+}  // namespace rflbm_dev

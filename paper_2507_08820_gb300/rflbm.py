@@ -32,6 +32,8 @@ RFLBM_PHI_RHO0 = 1
 RFLBM_KERNEL_AUTO = 0
 RFLBM_KERNEL_GATHER = 1
 RFLBM_KERNEL_TMA = 2
+RFLBM_PATTERN_PINGPONG = 0
+RFLBM_PATTERN_AA = 1
 FIELDS = ("rho", "jx", "jy", "jz", "pxx", "pyy", "pzz", "pxy", "pxz", "pyz")
 
 
@@ -49,6 +51,7 @@ class rflbm_config_t(C.Structure):
         ("model", C.c_int), ("storage", C.c_int), ("phi_rho", C.c_int),
         ("replica", C.c_uint32), ("stream", C.c_void_p),
         ("buffers", C.c_void_p * 2), ("device", C.c_int), ("kernel", C.c_int),
+        ("pattern", C.c_int),
     ]
 
 
@@ -76,6 +79,7 @@ _H = C.c_void_p
 _P = C.c_void_p
 _sig = {
     "rflbm_config_default": (None, [C.POINTER(rflbm_config_t)]),
+    "rflbm_config_size": (C.c_int64, []),
     "rflbm_buffer_bytes": (C.c_int64, [C.POINTER(rflbm_config_t)]),
     "rflbm_create": (_H, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_uint64]),
     "rflbm_create_ex": (_H, [C.POINTER(rflbm_config_t)]),
@@ -155,6 +159,10 @@ def rflbm_config_default():
     cfg = rflbm_config_t()
     lib.rflbm_config_default(C.byref(cfg))
     return cfg
+
+
+def rflbm_config_size():
+    return lib.rflbm_config_size()
 
 
 def rflbm_buffer_bytes(cfg):
@@ -390,7 +398,7 @@ class Box:
     def __init__(self, nx, ny, nz, tau, kT=0.0, rho0=1.0, seed=1, omega_g=1.0,
                  model=RFLBM_MODEL_REG, phi_rho=RFLBM_PHI_LOCAL_RHO, replica=0,
                  stream=None, torch_buffers=False, device=-1, kernel=RFLBM_KERNEL_AUTO,
-                 storage=RFLBM_STORE_F32):
+                 storage=RFLBM_STORE_F32, pattern=RFLBM_PATTERN_PINGPONG):
         cfg = rflbm_config_default()
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
         cfg.tau, cfg.kT, cfg.rho0, cfg.seed = tau, kT, rho0, seed
@@ -398,6 +406,7 @@ class Box:
         cfg.device = device
         cfg.kernel = kernel
         cfg.storage = storage
+        cfg.pattern = pattern
         if stream is not None:
             cfg.stream = stream
         self._buffers = None
@@ -405,10 +414,11 @@ class Box:
             import torch
             nbytes = rflbm_buffer_bytes(cfg)
             dev = torch.device("cuda", device if device >= 0 else torch.cuda.current_device())
+            nbuf = 1 if pattern == RFLBM_PATTERN_AA else 2
             self._buffers = [torch.empty(nbytes, dtype=torch.uint8, device=dev)
-                             for _ in range(2)]
-            cfg.buffers[0] = self._buffers[0].data_ptr()
-            cfg.buffers[1] = self._buffers[1].data_ptr()
+                             for _ in range(nbuf)]
+            for b, t in enumerate(self._buffers):
+                cfg.buffers[b] = t.data_ptr()
         self.cfg = cfg
         self.shape = (nx, ny, nz)
         self.n = nx * ny * nz

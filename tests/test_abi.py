@@ -34,6 +34,34 @@ def test_binding_wraps_every_declared_symbol(lib):
         assert callable(getattr(R, name)), name
 
 
+def test_config_struct_mirror_matches_the_library(lib):
+    from paper_2507_08820_gb300 import rflbm as R
+    assert R.rflbm_config_size() == ctypes.sizeof(R.rflbm_config_t)
+    cfg = R.rflbm_config_default()
+    assert (cfg.pattern, cfg.kernel, cfg.device) == (R.RFLBM_PATTERN_PINGPONG, R.RFLBM_KERNEL_AUTO, -1)
+
+
+def test_aa_pattern_validation_without_gpu(lib):
+    from paper_2507_08820_gb300 import rflbm as R
+    cfg = R.rflbm_config_default()
+    cfg.pattern = R.RFLBM_PATTERN_AA
+    for storage in (R.RFLBM_STORE_F32, R.RFLBM_STORE_F16, R.RFLBM_STORE_BF16):
+        cfg.storage = storage
+        assert R.rflbm_buffer_bytes(cfg) == 27 * 32768 * (4 if storage == 0 else 2)
+    cfg.storage = R.RFLBM_STORE_F32
+    for field, bad in (("pattern", 2), ("omega_g", 0.8), ("phi_rho", R.RFLBM_PHI_RHO0)):
+        c = R.rflbm_config_default()
+        c.pattern = R.RFLBM_PATTERN_AA
+        setattr(c, field, bad)
+        with pytest.raises(R.RflbmError) as e:
+            R.rflbm_buffer_bytes(c)
+        assert e.value.status == R.RFLBM_EINVAL
+    # BGK relaxes every mode at omega_h: omega_g does not enter, and AA accepts it
+    c = R.rflbm_config_default()
+    c.pattern, c.model, c.omega_g = R.RFLBM_PATTERN_AA, R.RFLBM_MODEL_BGK, 0.8
+    assert R.rflbm_buffer_bytes(c) > 0
+
+
 def test_config_validation_without_gpu(lib):
     from paper_2507_08820_gb300 import rflbm as R
     cfg = R.rflbm_config_default()

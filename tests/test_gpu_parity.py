@@ -134,7 +134,7 @@ def test_auto_kernel_choice(R):
 
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_kernels_agree_bitwise(R, kernel):
-    """The three step kernels run the same per-site arithmetic on the same inputs."""
+    """The two step kernels run the same per-site arithmetic on the same inputs."""
     shape = (64, 10, 6)
     f0 = _state(shape, seed=31)
     out = {}
