@@ -88,13 +88,18 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# the sources the ping-pong TMA step kernel is compiled from (its translation unit and
+# every header it includes)
+STEP_KERNEL_SOURCES = ("collide.cuh", "d3q27.cuh", "philox.cuh", "rflbm_internal.h",
+                       "rflbm_step_tma.cu", "step_tma.cuh", "storage.cuh", "tma.cuh")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_08820_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode() + fh.read())
+    for name in STEP_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
 
 

@@ -42,6 +42,8 @@ struct rflbm {
   int kernel = RFLBM_KERNEL_GATHER;  // the step kernel in use
   CUtensorMap load_map[2];     // per buffer: source-row loads with halo
   CUtensorMap store_map[2];    // per buffer: row-segment stores
+  CUtensorMap row_map;         // AA with one segment per row: three-plane row stores
+  bool has_row_map = false;
   // diagnostics (allocated on first use)
   double* diag_partials = nullptr;
   size_t diag_partials_bytes = 0;
@@ -252,6 +254,9 @@ void setup_tma(rflbm* h) {
         !encode_map(&h->store_map[b], h->buf[b], h->geo, (uint32_t)w, kQ, st))
       return;
   }
+  // AA odd form with one segment per row: three-plane stores of whole rows
+  h->has_row_map = h->aa && (uint32_t)w == h->geo.nx &&
+                   encode_map(&h->row_map, h->buf[0], h->geo, (uint32_t)w, 3, st);
   h->tma_width = w;
   h->kernel = RFLBM_KERNEL_TMA;
 }
@@ -477,7 +482,8 @@ int rflbm_step(rflbm_t* h, int64_t n) {
       p.src = p.dst = h->buf[0];
       const bool odd = h->phase != 0;
       if (h->tma_width) {
-        const TmaMaps m{&h->load_map[0], &h->store_map[0], h->tma_width};
+        const TmaMaps m{&h->load_map[0], &h->store_map[0], h->tma_width,
+                        h->has_row_map ? &h->row_map : nullptr};
         e = launch_step_aa_tma(m, p, h->variant, odd, h->stream);
       } else {
         e = launch_step_aa_gather(p, h->variant, odd, h->stream);

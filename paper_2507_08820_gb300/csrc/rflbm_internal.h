@@ -136,6 +136,7 @@ struct TmaMaps {
   const CUtensorMap* load;   // box: (width + 2 halo) x 1 x 1 x 3 planes
   const CUtensorMap* store;  // box: width x 1 x 1 x 27 planes
   int width;
+  const CUtensorMap* row3 = nullptr;  // AA, width == nx: box width x 1 x 1 x 3 planes
 };
 
 constexpr int kStepBlock = 256;

@@ -1,4 +1,4 @@
-// In-place AA step kernels (step_aa.cuh) for bf16 storage.
+// In-place AA step kernels (step_aa.cuh) for bfloat16 storage.
 #include "step_aa.cuh"
 
 namespace rflbm_dev {

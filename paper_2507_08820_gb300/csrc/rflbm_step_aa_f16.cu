@@ -1,4 +1,4 @@
-// In-place AA step kernels (step_aa.cuh) for f16 storage.
+// In-place AA step kernels (step_aa.cuh) for float16 storage.
 #include "step_aa.cuh"
 
 namespace rflbm_dev {

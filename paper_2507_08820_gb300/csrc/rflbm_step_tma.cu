@@ -1,6 +1,5 @@
 // Step kernels with TMA staging for float32 storage (step_tma.cuh), and the dispatch for
-// all storage formats and both streaming patterns.
-#include "step_aa.cuh"
+// all storage formats.
 #include "step_tma.cuh"
 
 namespace rflbm_dev {
@@ -40,16 +39,6 @@ cudaError_t launch_step_tma(const TmaMaps& m, const StepParams& p, const StepVar
     case 128: return launch_variant<128>(m, p, v, stream);
     case 64: return launch_variant<64>(m, p, v, stream);
     case 32: return launch_variant<32>(m, p, v, stream);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_step_aa_tma(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
-                               cudaStream_t stream) {
-  switch (v.storage) {
-    case kStoreF32: return launch_step_aa_tma_f32(m, p, v, odd, stream);
-    case kStoreF16: return launch_step_aa_tma_f16(m, p, v, odd, stream);
-    case kStoreBF16: return launch_step_aa_tma_bf16(m, p, v, odd, stream);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -19,10 +19,15 @@
 // populations. One CTA of kW threads updates one row segment [x0, x0 + kW) of row (y, z).
 //  - Even: one TMA load and one TMA store of the 27-plane box (x0, y, z, 0..26).
 //  - Odd: 9 three-plane TMA loads with a 16-byte halo, one per source row
-//    (y - c_y, z - c_z), as in the ping-pong kernel but of the mirrored plane group; the
-//    results go straight to the neighbours x + c_i with coalesced stores (the x shift of
-//    one element rules out aligned tensor stores, and the halo of a box would overwrite
-//    slots of the neighbouring segments).
+//    (y - c_y, z - c_z), as in the ping-pong kernel but of the mirrored plane group. When
+//    the segment is a whole row (nx == kW) the results are rotated by c_x in shared memory
+//    and leave as 9 three-plane row stores, one per destination row (y + c_y, z + c_z).
+//    Otherwise they go straight to the neighbours x + c_i with coalesced stores: the x
+//    shift of one element rules out aligned tensor stores of a segment, and a wider box
+//    would overwrite slots of the neighbouring segments. (Two staged alternatives measured
+//    slower: tensor stores of each segment's aligned interior with plain stores at its
+//    edges, and the segments of a row as one thread-block cluster handing the edge values
+//    to their neighbours through distributed shared memory.)
 // Both forms use programmatic dependent launch and bounded mbarrier waits like the
 // ping-pong kernel: global memory is touched only after griddepcontrol.wait, so an in-place
 // step never overlaps the previous one.
@@ -101,8 +106,20 @@ __global__ void __launch_bounds__(kW) step_aa_even(const __grid_constant__ CUten
   }
 }
 
-template <int kStore, int kW, int kModel, bool kNoise>
+// Output tile of the odd form when one CTA covers a whole row (nx == kW): per destination
+// row (group) the three planes, each rotated by its c_x, at 128-byte aligned group starts.
+template <int kStore, int kW>
+struct AaRowOut {
+  using T = typename Storage<kStore>::T;
+  static constexpr int kGroupBytes = (3 * kW * (int)sizeof(T) + 127) / 128 * 128;
+  static constexpr int kGroup = kGroupBytes / (int)sizeof(T);
+  static_assert((size_t)kGroups * kGroupBytes <= (size_t)kGroups * TmaLayout<kStore, kW>::kGroupBytes,
+                "the rotated output tile must fit in the input tile");
+};
+
+template <int kStore, int kW, int kModel, bool kNoise, bool kFullRow>
 __global__ void __launch_bounds__(kW) step_aa_odd(const __grid_constant__ CUtensorMap load_map,
+                                                  const __grid_constant__ CUtensorMap row_map,
                                                   const StepParams p) {
   using S = Storage<kStore>;
   using L = TmaLayout<kStore, kW>;
@@ -184,7 +201,36 @@ __global__ void __launch_bounds__(kW) step_aa_odd(const __grid_constant__ CUtens
 
   collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
 
-  // population i of x goes to plane P(i) at x + c_i
+  if (kFullRow) {
+    // the segment is the whole row: population i of x goes to position (x + c_x) mod nx of
+    // plane P(i) in row (y + c_y, z + c_z). Rotate each plane row in shared memory, then
+    // lane g of warp 0 stores destination group g (three planes, one row) with one copy.
+    using O = AaRowOut<kStore, kW>;
+    __syncthreads();  // all inputs are in registers: the tile can take the outputs
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int g = 3 * (cy_of(i) + 1) + (cz_of(i) + 1);
+      sm[g * O::kGroup + (cx_of(i) + 1) * kW + ((t + cx_of(i)) & (kW - 1))] =
+          S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t < kGroups) {
+      const int cy = t / 3 - 1, cz = t % 3 - 1;
+      int yd = (int)y + cy, zd = (int)z + cz;
+      yd += yd < 0 ? (int)p.geo.ny : 0;
+      yd -= yd >= (int)p.geo.ny ? (int)p.geo.ny : 0;
+      zd += zd < 0 ? (int)p.geo.nz : 0;
+      zd -= zd >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+      tma_store_4d(&row_map, sm + t * O::kGroup, 0, yd, zd, 3 * t);
+      bulk_commit();
+      bulk_wait_read();
+    }
+    return;
+  }
+
+  // population i of x goes to plane P(i) at x + c_i (coalesced: a warp writes 32
+  // consecutive positions of each plane)
   T* const dst = buf + s;
 #pragma unroll
   for (int i = 0; i < kQ; ++i)
@@ -206,7 +252,9 @@ cudaError_t launch_aa_segment(const TmaMaps& m, const StepParams& p, bool odd, c
   cfg.numAttrs = 1;
   if (odd) {
     cfg.dynamicSmemBytes = TmaLayout<kStore, kW>::kBytes;
-    return cudaLaunchKernelEx(&cfg, step_aa_odd<kStore, kW, kModel, kNoise>, *m.load, p);
+    if (m.row3 && p.geo.nx == (uint32_t)kW)
+      return cudaLaunchKernelEx(&cfg, step_aa_odd<kStore, kW, kModel, kNoise, true>, *m.load, *m.row3, p);
+    return cudaLaunchKernelEx(&cfg, step_aa_odd<kStore, kW, kModel, kNoise, false>, *m.load, *m.load, p);
   }
   cfg.dynamicSmemBytes = AaEvenLayout<kStore, kW>::kBytes;
   return cudaLaunchKernelEx(&cfg, step_aa_even<kStore, kW, kModel, kNoise>, *m.store, p);
