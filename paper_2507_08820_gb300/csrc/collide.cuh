@@ -47,9 +47,17 @@ __device__ __forceinline__ void line_inverse(float L0, float L1, float L2, float
   op = a + L1;
 }
 
-template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
+// Supplies the pre-collision value of tile entry (a, b, c) to the BGK update at the end of
+// the collision. By default the tile itself, which keeps its 27 values live in registers
+// through the whole collision; kernels that still hold the inputs in shared memory pass a
+// reader instead, and the registers are free in between.
+struct KeepTile {
+  __device__ __forceinline__ float operator()(int, int, int, float g) const { return g; }
+};
+
+template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0, class Reload = KeepTile>
 __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideParams& cp,
-                                             const SiteNoise& noise) {
+                                             const SiteNoise& noise, const Reload& reload = Reload()) {
   // ---- 1. moments of order <= 2 (sweep x, then y, then z)
   float X0[3][3], X1[3][3], X2[3][3];
 #pragma unroll
@@ -93,7 +101,10 @@ __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideP
   // U[p] = u^p / beta_p: 1, 3u, 9u^2/2 ; RX[p] = rho U_x[p]
   const float Uy[3] = {1.0f, 3.0f * uy, 4.5f * uy * uy};
   const float Uz[3] = {1.0f, 3.0f * uz, 4.5f * uz * uz};
-  const float RX[3] = {rho, 3.0f * jx, 4.5f * jx * ux};
+  // BGK scales every equilibrium moment by omega: fold it into the x factor
+  const float om = cp.omega;
+  const float rs = kModel == kModelBgk ? om * rho : rho;
+  const float RX[3] = {rs, (3.0f * (kModel == kModelBgk ? om : 1.0f)) * jx, 4.5f * (kModel == kModelBgk ? om * jx : jx) * ux};
   float M[3][3][3];
 #pragma unroll
   for (int p = 0; p < 3; ++p)
@@ -102,7 +113,6 @@ __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideP
 #pragma unroll
       for (int r = 0; r < 3; ++r) M[p][q][r] = RX[p] * (Uy[q] * Uz[r]);
 
-  const float om = cp.omega;
   if (kModel == kModelReg) {
     // conserved modes are kept exactly
     M[0][0][0] = drho;
@@ -140,18 +150,11 @@ __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideP
           }
     }
   } else {
-    // BGK: omega f^(0) here, (1 - omega) f added after the back transform
+    // BGK: omega f^(0) here (omega is in RX), (1 - omega) f added after the back
+    // transform; the shifted density mode is omega drho
     M[0][0][0] = om * drho;
-    M[1][0][0] = om * M[1][0][0];
     M[0][1][0] = om * (3.0f * jy);
     M[0][0][1] = om * (3.0f * jz);
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-          if (p + q + r >= 2) M[p][q][r] *= om;
   }
   if (kNoise) {
     // Box-Muller pair m gives the normals r_k of modes k = 2m + 4 (cosine) and 2m + 5 (sine)
@@ -199,7 +202,7 @@ __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideP
       for (int a = 0; a < 3; ++a) {
         const float wt = float(w1d(a) * w1d(b) * w1d(c));
         if (kModel == kModelBgk) {
-          G[a][b][c] = fmaf(1.0f - om, G[a][b][c], wt * o[a]);
+          G[a][b][c] = fmaf(1.0f - om, reload(a, b, c, G[a][b][c]), wt * o[a]);
         } else {
           G[a][b][c] = wt * o[a];
         }

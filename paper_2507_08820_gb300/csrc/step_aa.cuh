@@ -45,7 +45,7 @@ struct AaEvenLayout {
 };
 
 template <int kStore, int kW, int kModel, bool kNoise>
-__global__ void __launch_bounds__(kW) step_aa_even(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_aa_even(const __grid_constant__ CUtensorMap map,
                                                    const StepParams p) {
   using S = Storage<kStore>;
   using T = typename S::T;
@@ -90,9 +90,13 @@ __global__ void __launch_bounds__(kW) step_aa_even(const __grid_constant__ CUten
   for (int i = 0; i < kQ; ++i)
     G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = S::load(sm[plane_of(i) * kW + t], class_of(i), p.ss);
 
-  collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
+  // BGK re-reads its inputs from the tile at the end instead of keeping them in registers
+  const auto reload = [&](int a, int b, int c, float) {
+    return S::load(sm[(9 * b + 3 * c + a) * kW + t], class_at(a, b, c), p.ss);
+  };
+  collide_site<kModel, kNoise, false, false>(G, p.cp, noise, reload);
 
-  __syncthreads();  // all inputs are in registers: the tile can take the outputs
+  __syncthreads();  // all inputs are read: the tile can take the outputs
 #pragma unroll
   for (int i = 0; i < kQ; ++i)
     sm[(kQ - 1 - plane_of(i)) * kW + t] =
@@ -118,7 +122,7 @@ struct AaRowOut {
 };
 
 template <int kStore, int kW, int kModel, bool kNoise, bool kFullRow>
-__global__ void __launch_bounds__(kW) step_aa_odd(const __grid_constant__ CUtensorMap load_map,
+__global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_aa_odd(const __grid_constant__ CUtensorMap load_map,
                                                   const __grid_constant__ CUtensorMap row_map,
                                                   const StepParams p) {
   using S = Storage<kStore>;
@@ -199,14 +203,18 @@ __global__ void __launch_bounds__(kW) step_aa_odd(const __grid_constant__ CUtens
         S::load(mine[gi * L::kGroup + (1 - cx_of(i)) * L::kSeg - cx_of(i)], class_of(i), p.ss);
   }
 
-  collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
+  // BGK re-reads its inputs from the tile at the end instead of keeping them in registers
+  const auto reload = [&](int a, int b, int c, float) {
+    return S::load(mine[(3 * b + c) * L::kGroup + (2 - a) * L::kSeg + (1 - a)], class_at(a, b, c), p.ss);
+  };
+  collide_site<kModel, kNoise, false, false>(G, p.cp, noise, reload);
 
   if (kFullRow) {
     // the segment is the whole row: population i of x goes to position (x + c_x) mod nx of
     // plane P(i) in row (y + c_y, z + c_z). Rotate each plane row in shared memory, then
     // lane g of warp 0 stores destination group g (three planes, one row) with one copy.
     using O = AaRowOut<kStore, kW>;
-    __syncthreads();  // all inputs are in registers: the tile can take the outputs
+    __syncthreads();  // all inputs are read: the tile can take the outputs
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
       const int g = 3 * (cy_of(i) + 1) + (cz_of(i) + 1);

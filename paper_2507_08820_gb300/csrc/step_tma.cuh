@@ -41,7 +41,7 @@ struct TmaLayout {
 };
 
 template <int kStore, int kW, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
-__global__ void __launch_bounds__(kW) step_tma(const __grid_constant__ CUtensorMap load_map,
+__global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_tma(const __grid_constant__ CUtensorMap load_map,
                                                const __grid_constant__ CUtensorMap store_map,
                                                const StepParams p) {
   using S = Storage<kStore>;
@@ -120,7 +120,11 @@ __global__ void __launch_bounds__(kW) step_tma(const __grid_constant__ CUtensorM
         S::load(mine[gi * L::kGroup + (cx_of(i) + 1) * L::kSeg - cx_of(i)], class_of(i), p.ss);
   }
 
-  collide_site<kModel, kNoise, kGhostNeq, kPhiRho0>(G, p.cp, noise);
+  // BGK re-reads its inputs from the tile at the end instead of keeping them in registers
+  const auto reload = [&](int a, int b, int c, float) {
+    return S::load(mine[(3 * b + c) * L::kGroup + a * L::kSeg - (a - 1)], class_at(a, b, c), p.ss);
+  };
+  collide_site<kModel, kNoise, kGhostNeq, kPhiRho0>(G, p.cp, noise, reload);
 
   __syncthreads();  // every thread has read its inputs: the tile can hold the outputs
   T* out = sm + t;  // dense [plane][kW] output tile at the (128-byte aligned) start

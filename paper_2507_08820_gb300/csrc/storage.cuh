@@ -22,6 +22,11 @@ __host__ __device__ constexpr int class_of(int i) {
   return (i == 0) ? 0 : (i <= 6 ? 1 : (i <= 18 ? 2 : 3));
 }
 
+// Velocity class of the tile entry (a, b, c) = (c_x + 1, c_y + 1, c_z + 1).
+__host__ __device__ constexpr int class_at(int a, int b, int c) {
+  return (a != 1) + (b != 1) + (c != 1);
+}
+
 // Per-class scale factors of 16-bit storage: stored = g * scale, g = stored * inv_scale.
 struct StoreScale {
   float scale[4];
