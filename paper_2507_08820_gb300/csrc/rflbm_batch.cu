@@ -57,26 +57,21 @@ __global__ void __launch_bounds__(kTile) k_batch_run(const ReplicaDev* __restric
                                                      unsigned long long* done, int* err) {
   using S = Storage<kStore>;
   using T = typename S::T;
-  __shared__ unsigned long long item_sh;
+  __shared__ unsigned long long next_sh;
   __shared__ int fail_sh;
-  __shared__ __align__(16) ReplicaDev rep;  // the current item's replica
   const int64_t total = tiles_per_step * nsteps;
   const uint32_t step0 = (uint32_t)*step0_ptr;
-  for (;;) {
-    if (threadIdx.x == 0) item_sh = atomicAdd(queue, 1ull);
-    __syncthreads();
-    const unsigned long long item = item_sh;
-    if ((int64_t)item >= total) break;
+  if (threadIdx.x == 0) next_sh = atomicAdd(queue, 1ull);
+  __syncthreads();
+  unsigned long long item = next_sh;
+  while ((int64_t)item < total) {
     const int64_t t = (int64_t)item / tiles_per_step;
     const int64_t j = (int64_t)item - t * tiles_per_step;
-    const int r = tile_rep[j];
-    {
-      const int* from = reinterpret_cast<const int*>(reps + r);
-      int* to = reinterpret_cast<int*>(&rep);
-      for (int w = threadIdx.x; w < (int)(sizeof(ReplicaDev) / sizeof(int)); w += kTile) to[w] = __ldg(from + w);
-    }
-    __syncthreads();  // the descriptor is complete before anyone reads it
+    const int r = __ldg(tile_rep + j);
+    const ReplicaDev& rep = reps[r];  // uniform over the CTA: read through the read-only cache
     if (threadIdx.x == 0) {
+      // the next item is taken now and published by the barrier below
+      next_sh = atomicAdd(queue, 1ull);
       int failed = 0;
       if (t > 0) {
         const unsigned long long need = (unsigned long long)(t * rep.ntiles);
@@ -91,7 +86,8 @@ __global__ void __launch_bounds__(kTile) k_batch_run(const ReplicaDev* __restric
       }
       fail_sh = failed;
     }
-    __syncthreads();
+    __syncthreads();  // the dependency holds for the whole CTA; next_sh and fail_sh are set
+    const unsigned long long next = next_sh;
     if (fail_sh) {
       if (threadIdx.x == 0) atomicOr(err, 1);
       return;
@@ -120,9 +116,12 @@ __global__ void __launch_bounds__(kTile) k_batch_run(const ReplicaDev* __restric
       for (int i = 0; i < kQ; ++i)
         dst[s + plane_of(i) * rep.geo.ps] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), rep.ss);
     }
-    __threadfence();  // this thread's stores before the completion count
-    __syncthreads();  // also: nobody reads `rep` or `item_sh` of this item any more
-    if (threadIdx.x == 0) atomicAdd(&done[r], 1ull);
+    __syncthreads();  // every thread's stores of this item precede the release below
+    if (threadIdx.x == 0) {
+      __threadfence();  // cumulative over the CTA's stores ordered by the barrier
+      atomicAdd(&done[r], 1ull);
+    }
+    item = next;
   }
 }
 
