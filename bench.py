@@ -370,7 +370,7 @@ def gb300_arm(args):
                               "roofline_frac": bps * sites_s / 1e9 / peak_v,
                               "bytes_per_site": bps}
             vb.close()
-        # batched ensemble: 64 replicas of uneven sizes, one persistent launch per call
+        # batched ensemble: 64 replicas of uneven sizes, one CUDA graph of per-step launches per call
         from paper_2507_08820_gb300 import workloads as W
         reps = W.replica_ensemble(64, seed=0)
         sites = sum(r["nx"] * r["ny"] * r["nz"] for r in reps)

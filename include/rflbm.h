@@ -179,11 +179,15 @@ int rflbm_moments(rflbm_t* h, double* rho, double* u, double* pi, int on_device)
  * Returns RFLBM_EUNSTABLE (with *out filled) when non-finite values are present. */
 int rflbm_stats(rflbm_t* h, rflbm_stats_t* out);
 
-/* Current populations f_i(x, t) as 27*N doubles / floats (layout above). Synchronous. */
+/* Current populations f_i(x, t) as 27*N doubles / floats (layout above). Synchronous.
+ * Host memory that is page-locked (cudaHostAlloc, cudaHostRegister) is written by the
+ * conversion kernel in place; other host memory goes through a device staging buffer. */
 int rflbm_get_populations(rflbm_t* h, double* f, int on_device);
 int rflbm_get_populations_f32(rflbm_t* h, float* f, int on_device);
 
-/* Replaces the state by f (27*N doubles / floats) without changing t. */
+/* Replaces the state by f (27*N doubles / floats) without changing t. Host input is
+ * read in place when page-locked, else through the staging buffer; either way the call
+ * returns after f has been read. */
 int rflbm_set_populations(rflbm_t* h, const double* f, int on_device);
 int rflbm_set_populations_f32(rflbm_t* h, const float* f, int on_device);
 
@@ -281,14 +285,17 @@ int rflbm_site_normals(uint64_t seed, int64_t step, uint32_t replica,
  * must be serialised by the caller. Returns RFLBM_OK, RFLBM_EUNSTABLE (non-finite values;
  * *out filled), RFLBM_EINVAL or RFLBM_ECUDA (message in rflbm_last_error). */
 /* Batched ensembles: many independent periodic boxes ("replicas") of uneven sizes, seeds,
- * tau and kT, advanced together by one persistent kernel launch per call (replayed from a
- * CUDA graph). Each replica runs the Reg-FLBM step of a single box (Eq. 25, omega_g = 1,
- * local rho in Eq. 10) with Philox key = its seed and replica word 0, so it reproduces the
- * run of rflbm_create(nx, ny, nz, tau, kT, rho0, seed) in the same storage format.
- * The work is split into tiles of `tile` sites (128, 256 or 512; 0 = chosen by timing a
- * few steps of each on the ensemble at creation) handed out by a global queue; a tile of
- * step t waits (bounded) for its replica's step t - 1, and a wait that expires makes the
- * call report RFLBM_ETIMEOUT. The library allocates and owns all device memory. */
+ * tau and kT, advanced together: each step is one launch over the tiles of every replica,
+ * and the n steps of a call replay as one CUDA graph (captured once per n). Each replica
+ * runs the Reg-FLBM step of a single box (Eq. 25, omega_g = 1, local rho in Eq. 10) with
+ * Philox key = its seed and replica word 0, so it reproduces the run of
+ * rflbm_create(nx, ny, nz, tau, kT, rho0, seed) in the same storage format bit for bit.
+ * `tile` is the CTA size (128, 192, 256 or 512; 0 = chosen by timing a few steps of each
+ * on the ensemble at creation). A replica whose row length nx divides the tile and is a
+ * whole number of 16-byte units takes tiles of tile / nx whole rows moved by TMA copies;
+ * any other replica takes tiles of `tile` consecutive sites. A bounded wait for a copy
+ * that expires makes the call report RFLBM_ETIMEOUT. The library allocates and owns all
+ * device memory. */
 typedef struct rflbm_batch rflbm_batch_t;
 typedef struct {
   int nx, ny, nz;   /* box edges (N = nx*ny*nz < 2^31) */
@@ -298,7 +305,7 @@ typedef struct {
 rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho0, int storage,
                                   int tile);
 void rflbm_batch_destroy(rflbm_batch_t* b);
-/* Tile size in use, resident CTAs per SM of the persistent kernel, tiles per step. */
+/* Tile size in use, resident CTAs per SM of the row-tile kernel, tiles per step. */
 int rflbm_batch_tuning(const rflbm_batch_t* b, int* tile, int* ctas_per_sm, int64_t* tiles_per_step);
 /* Every replica at rest, step 0. */
 int rflbm_batch_init_rest(rflbm_batch_t* b);

@@ -179,6 +179,18 @@ int ensure_staging(rflbm* h, size_t bytes) {
   return RFLBM_OK;
 }
 
+// The device-side address of a page-locked host pointer (cudaHostAlloc / cudaHostRegister
+// memory, e.g. a pinned PyTorch tensor), or NULL for any other pointer. Kernels read and
+// write such memory directly (over NVLink-C2C on Grace), with no staging copy.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int check_handle(const rflbm* h) {
   if (!h) return fail(RFLBM_EINVAL, "handle is NULL");
   return RFLBM_OK;
@@ -201,43 +213,10 @@ int sync(rflbm* h, const char* what) {
   return RFLBM_OK;
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_tiled_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
-  return fn;
-}
-
 // The population buffer as a 4-D tensor (x, y, z, plane); box = (box_x, 1, 1, box_planes).
 bool encode_map(CUtensorMap* map, void* base, const Geometry& g, uint32_t box_x, uint32_t box_planes,
                 int storage) {
-  EncodeTiledFn fn = encode_tiled_fn();
-  if (!fn) return false;
-  const cuuint64_t e = storage_bytes(storage);
-  const cuuint64_t dims[4] = {g.nx, g.ny, g.nz, (cuuint64_t)kQ};
-  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * e, (cuuint64_t)g.nxy * e, (cuuint64_t)g.ps * e};
-  const cuuint32_t box[4] = {box_x, 1, 1, box_planes};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUtensorMapDataType dt = storage == kStoreF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                 : storage == kStoreBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  return fn(map, dt, 4, base, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return encode_population_map(map, base, g, box_x, 1, box_planes, storage);
 }
 
 // Selects the TMA step path when the box allows it and the descriptors encode.
@@ -274,6 +253,48 @@ Geometry vgeo(const rflbm* h) {
 
 int rflbm_dev::record_error(int code, const char* msg, const char* detail) {
   return detail ? fail(code, "%s: %s", msg, detail) : fail(code, "%s", msg);
+}
+
+namespace {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool rflbm_dev::encode_population_map(CUtensorMap* map, void* base, const Geometry& g, uint32_t box_x,
+                                      uint32_t box_y, uint32_t box_planes, int storage) {
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return false;
+  const cuuint64_t e = storage_bytes(storage);
+  const cuuint64_t dims[4] = {g.nx, g.ny, g.nz, (cuuint64_t)kQ};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * e, (cuuint64_t)g.nxy * e, (cuuint64_t)g.ps * e};
+  const cuuint32_t box[4] = {box_x, box_y, 1, box_planes};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUtensorMapDataType dt = storage == kStoreF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : storage == kStoreBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return fn(map, dt, 4, base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 extern "C" {
@@ -561,16 +582,21 @@ static int get_pops(rflbm_t* h, void* f, int on_device, bool f64) {
   const int64_t n = n_sites(h);
   const size_t bytes = (size_t)kQ * n * (f64 ? sizeof(double) : sizeof(float));
   void* dst = f;
+  bool copy_back = false;
   if (!on_device) {
-    if (int e = ensure_staging(h, bytes)) return e;
-    dst = h->staging;
+    dst = const_cast<void*>(mapped_host(f));
+    if (!dst) {
+      if (int e = ensure_staging(h, bytes)) return e;
+      dst = h->staging;
+      copy_back = true;
+    }
   }
   const int st = h->variant.storage;
   const Geometry g = vgeo(h);
   cudaError_t e = f64 ? launch_get_populations_f64(g, h->cp.rho0, h->ss, st, h->buf[h->cur], (double*)dst, h->stream)
                       : launch_get_populations_f32(g, h->cp.rho0, h->ss, st, h->buf[h->cur], (float*)dst, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "launching get_populations");
-  if (!on_device) RFLBM_CUDA(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, h->stream), "copying populations");
+  if (copy_back) RFLBM_CUDA(cudaMemcpyAsync(f, dst, bytes, cudaMemcpyDeviceToHost, h->stream), "copying populations");
   return sync(h, "rflbm_get_populations");
 }
 
@@ -582,9 +608,12 @@ static int set_pops(rflbm_t* h, const void* f, int on_device, bool f64) {
   const size_t bytes = (size_t)kQ * n * (f64 ? sizeof(double) : sizeof(float));
   const void* src = f;
   if (!on_device) {
-    if (int e = ensure_staging(h, bytes)) return e;
-    RFLBM_CUDA(cudaMemcpyAsync(h->staging, f, bytes, cudaMemcpyHostToDevice, h->stream), "copying populations");
-    src = h->staging;
+    src = mapped_host(f);
+    if (!src) {
+      if (int e = ensure_staging(h, bytes)) return e;
+      RFLBM_CUDA(cudaMemcpyAsync(h->staging, f, bytes, cudaMemcpyHostToDevice, h->stream), "copying populations");
+      src = h->staging;
+    }
   }
   // the state after this call is step h->step, held in buffer 0 (AA: natural view)
   h->cur = 0;

@@ -1,18 +1,21 @@
 // Batched ensembles: many independent periodic boxes (replicas) of uneven sizes, seeds,
-// relaxation times and thermal energies, all advanced by one persistent kernel launch.
+// relaxation times and thermal energies, advanced together.
 //
-// Work items are (step, tile) pairs handed out in step-major order by a global counter;
-// a tile is kTile consecutive sites of one replica. Before a CTA updates replica r at
-// step t it waits until all tiles of replica r at step t - 1 are complete (a per-replica
-// completion counter; this also protects the buffer the step writes, which step t - 1
-// read). The earliest unfinished item never waits: its dependencies have smaller queue
-// indices and were taken earlier, so the kernel always progresses. Every wait is bounded;
-// a CTA that gives up sets the error flag and leaves, which makes the CTAs that wait on
-// it give up as well, so the launch ends with an error status instead of hanging.
-//
-// Population loads bypass L1 (__ldcg): the data were written by other CTAs during the
-// same launch. Each replica's arithmetic is the single-box general kernel's, with Philox
-// key = the replica's seed and replica word 0, so a replica reproduces its single-box run.
+// One launch per step covers the tiles of every replica (a tile table maps CTA j to its
+// replica); a run of n steps is one CUDA graph of n launches, chained by programmatic
+// dependent launch like the single-box step: a CTA draws its noise while the previous
+// step drains and touches the populations only after griddepcontrol.wait. Two kinds of
+// tile, per replica:
+//  - rows: when a row of the replica is a whole number of 16-byte units and divides the
+//    CTA size (kTile = R nx), a tile is R consecutive rows (y0 .. y0 + R - 1) of one slab
+//    z. Lanes 0..8 load, for group g = 3 (c_y + 1) + (c_z + 1), the three planes of the R
+//    source rows (y0 - c_y .., z - c_z) with one TMA copy each; the rows that wrap around
+//    the y edge are copied in afterwards and x wraps by index. The 27 outputs go through
+//    shared memory and leave as one TMA store of the (nx, R, 27) box.
+//  - sites: otherwise, kTile consecutive sites, each gathering its 27 populations.
+// Each replica's arithmetic is the single-box kernels' (same tile order, same Philox key =
+// the replica's seed, replica word 0), so a replica reproduces its single-box run bit for
+// bit.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +28,7 @@
 
 #include "../../include/rflbm.h"
 #include "rflbm_aux.h"
+#include "tma.cuh"
 
 namespace rflbm_dev {
 
@@ -37,141 +41,258 @@ struct ReplicaDev {
   int noise;          // kT > 0
   int cur;            // buffer holding the state at the start of the launch
   int64_t tile_begin;  // first global tile index of this replica
-  int64_t ntiles;
+  int64_t ntiles;      // tiles per step
+  uint32_t rows;       // rows per tile (rows tiles), 0: sites tiles
+  uint32_t yblocks;    // row blocks per slab: ceil(ny / rows)
+  const CUtensorMap* maps;  // rows tiles, per buffer b: [2 b] loads (nx, rows, 1, 3), [2 b + 1] stores (nx, rows, 1, 27)
 };
 
-constexpr uint32_t kBatchMaxPolls = 1u << 24;
-
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
+// Dynamic shared memory of a rows tile: 9 groups of 3 planes x kTile sites (each group
+// rounded to 128 bytes), which then holds the 27-plane output tile.
+__host__ __device__ constexpr size_t batch_group_bytes(int tile, size_t elem) {
+  return (3 * (size_t)tile * elem + 127) / 128 * 128;
+}
+__host__ __device__ constexpr size_t batch_smem_bytes(int tile, size_t elem) {
+  return 9 * batch_group_bytes(tile, elem) + 128;
 }
 
-template <int kStore, int kTile>
-__global__ void __launch_bounds__(kTile) k_batch_run(const ReplicaDev* __restrict__ reps,
-                                                     const int* __restrict__ tile_rep,
-                                                     int64_t tiles_per_step, int64_t nsteps,
-                                                     const unsigned long long* step0_ptr,
-                                                     unsigned long long* queue,
-                                                     unsigned long long* done, int* err) {
+constexpr uint32_t kBatchTmaPolls = 1u << 22;
+constexpr int kBatchGroups = 9;  // source rows (c_y, c_z) of a site
+
+// One step of the tiles [tile0, tile0 + gridDim.x) of the tile table, all of one kind
+// (rows tiles when kRows, else sites tiles).
+// Rows tiles are held to 56 registers (65536 / (kTile 56) resident CTAs per SM): the
+// replica's collision parameters come from shared memory, not from the constant bank.
+template <int kStore, int kTile, bool kRows>
+__global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 1) k_batch_step(const ReplicaDev* __restrict__ reps,
+                                                      const int* __restrict__ tile_rep, int64_t tile0,
+                                                      const unsigned long long* step0_ptr, uint32_t k,
+                                                      int* err) {
   using S = Storage<kStore>;
   using T = typename S::T;
-  __shared__ unsigned long long next_sh;
-  __shared__ int fail_sh;
-  const int64_t total = tiles_per_step * nsteps;
-  const uint32_t step0 = (uint32_t)*step0_ptr;
-  if (threadIdx.x == 0) next_sh = atomicAdd(queue, 1ull);
+  constexpr int kGroup = (int)(batch_group_bytes(kTile, sizeof(T)) / sizeof(T));  // elements
+  constexpr int rn = kTile;  // sites of a rows tile (R nx)
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(16) ReplicaDev rep;  // this tile's replica
+  T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+  const int tid = threadIdx.x;
+  const int64_t j = tile0 + blockIdx.x;
+  const int r = __ldg(tile_rep + j);
+  {
+    const int* from = reinterpret_cast<const int*>(reps + r);
+    int* to = reinterpret_cast<int*>(&rep);
+    for (int w = tid; w < (int)(sizeof(ReplicaDev) / sizeof(int)); w += kTile) to[w] = __ldg(from + w);
+  }
+  if (kRows && tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
   __syncthreads();
-  unsigned long long item = next_sh;
-  while ((int64_t)item < total) {
-    const int64_t t = (int64_t)item / tiles_per_step;
-    const int64_t j = (int64_t)item - t * tiles_per_step;
-    const int r = __ldg(tile_rep + j);
-    const ReplicaDev& rep = reps[r];  // uniform over the CTA: read through the read-only cache
-    if (threadIdx.x == 0) {
-      // the next item is taken now and published by the barrier below
-      next_sh = atomicAdd(queue, 1ull);
-      int failed = 0;
-      if (t > 0) {
-        const unsigned long long need = (unsigned long long)(t * rep.ntiles);
-        uint32_t it = 0;
-        while (ld_acquire(&done[r]) < need) {
-          if (++it >= kBatchMaxPolls) {
-            failed = 1;
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-      fail_sh = failed;
-    }
-    __syncthreads();  // the dependency holds for the whole CTA; next_sh and fail_sh are set
-    const unsigned long long next = next_sh;
-    if (fail_sh) {
-      if (threadIdx.x == 0) atomicOr(err, 1);
-      return;
-    }
-    const int parity = (rep.cur + (int)(t & 1)) & 1;
-    const T* src = static_cast<const T*>(rep.buf[parity]);
-    T* dst = static_cast<T*>(rep.buf[parity ^ 1]);
-    const int64_t s64 = (j - rep.tile_begin) * kTile + threadIdx.x;
-    if (s64 < (int64_t)rep.geo.n) {
-      const uint32_t s = (uint32_t)s64;
-      const PullDeltas d = pull_deltas(s, rep.geo);
-      float G[3][3][3];
+  grid_launch_dependents();
+  const uint32_t step = (uint32_t)*step0_ptr + k;
+  const int parity = (rep.cur + (int)(k & 1u)) & 1;
+  const T* src = static_cast<const T*>(rep.buf[parity]);
+  T* dst = static_cast<T*>(rep.buf[parity ^ 1]);
+  const uint32_t li = (uint32_t)(j - rep.tile_begin);  // tile index within the replica
+
+  if (!kRows) {
+    // ---- sites tile: kTile consecutive sites, gathered
+    const int64_t s64 = (int64_t)li * kTile + tid;
+    if (s64 >= (int64_t)rep.geo.n) return;
+    const uint32_t s = (uint32_t)s64;
+    SiteNoise noise;
+    if (rep.noise) site_noise(s, step, 0u, rep.key0, rep.key1, noise);
+    const PullDeltas d = pull_deltas(s, rep.geo);
+    grid_dependency_wait();
+    float G[3][3][3];
 #pragma unroll
-      for (int i = 0; i < kQ; ++i)
-        G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] =
-            S::load(__ldcg(src + s + pull_delta(d, i) + plane_of(i) * rep.geo.ps), class_of(i), rep.ss);
-      SiteNoise noise;
-      const uint32_t step = step0 + (uint32_t)t;
-      if (rep.noise) {
-        site_noise(s, step, 0u, rep.key0, rep.key1, noise);
-        collide_site<kModelReg, true, false, false>(G, rep.cp, noise);
-      } else {
-        collide_site<kModelReg, false, false, false>(G, rep.cp, noise);
-      }
+    for (int i = 0; i < kQ; ++i)
+      G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] =
+          S::load(__ldg(src + s + pull_delta(d, i) + plane_of(i) * rep.geo.ps), class_of(i), rep.ss);
+    if (rep.noise)
+      collide_site<kModelReg, true, false, false>(G, rep.cp, noise);
+    else
+      collide_site<kModelReg, false, false, false>(G, rep.cp, noise);
 #pragma unroll
-      for (int i = 0; i < kQ; ++i)
-        dst[s + plane_of(i) * rep.geo.ps] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), rep.ss);
+    for (int i = 0; i < kQ; ++i)
+      dst[s + plane_of(i) * rep.geo.ps] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), rep.ss);
+    return;
+  }
+
+  // ---- rows tile: R rows of slab z from y0
+  const uint32_t R = rep.rows;
+  const uint32_t nx = rep.geo.nx, ny = rep.geo.ny, nz = rep.geo.nz;
+  const uint32_t z = li / rep.yblocks;
+  const uint32_t y0 = (li - z * rep.yblocks) * R;
+  const uint32_t nrows = min(R, ny - y0);
+  const uint32_t row = fastdiv((uint32_t)tid, rep.geo.div_nx);
+  const uint32_t x = (uint32_t)tid - row * nx;
+  const bool active = row < nrows;
+  // the noise is drawn while the previous step drains and the copies are in flight
+  SiteNoise noise;
+  if (rep.noise && active) site_noise(x + nx * ((y0 + row) + ny * z), step, 0u, rep.key0, rep.key1, noise);
+
+  grid_dependency_wait();  // the previous step's writes (our source) are complete
+  if (tid < kBatchGroups) {
+    if (tid == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kBatchGroups * 3 * rn * sizeof(T)));
+    const int cy = tid / 3 - 1, cz = tid % 3 - 1;
+    int zs = (int)z - cz;
+    zs += zs < 0 ? (int)nz : 0;
+    zs -= zs >= (int)nz ? (int)nz : 0;
+    tma_load_4d(sm + tid * kGroup, rep.maps + 2 * parity, 0, (int)y0 - cy, zs, 3 * tid, &bar);
+  }
+  const bool ok = mbar_wait_bounded(&bar, 0, kBatchTmaPolls);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicOr(err, 1);
+    mbar_wait_bounded(&bar, 0, kBatchTmaPolls);  // copies in flight land first
+    return;
+  }
+  // Rows that wrap around the y edge. The box of c_y = +1 (groups 6..8) starts at row
+  // y0 - 1: for y0 = 0 its first row must be row ny - 1. The box of c_y = -1 (groups 0..2)
+  // reads row y + 1 for row y: for the tile holding row ny - 1 that is row 0 (a slab of
+  // one row block takes both).
+  if (tid < (int)nx && (y0 == 0 || y0 + nrows == ny)) {
+    // one x of each patched row: 3 groups x 3 planes per patched row position
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      if (side == 0 ? y0 != 0 : y0 + nrows != ny) continue;
+      const int64_t ys = side == 0 ? (int64_t)ny - 1 : 0;
+      const int brow = side == 0 ? 0 : (int)nrows - 1;
+#pragma unroll
+      for (int gi = 0; gi < 3; ++gi) {
+        const int g = side == 0 ? 6 + gi : gi;  // c_y = +1: groups 6..8, c_y = -1: groups 0..2
+        int zs = (int)z - (gi - 1);              // c_z = gi - 1
+        zs += zs < 0 ? (int)nz : 0;
+        zs -= zs >= (int)nz ? (int)nz : 0;
+        const T* from = src + (int64_t)3 * g * rep.geo.ps + (int64_t)nx * (ys + (int64_t)ny * zs) + tid;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sm[g * kGroup + a * rn + brow * (int)nx + tid] = from[(int64_t)a * rep.geo.ps];
+      }
     }
-    __syncthreads();  // every thread's stores of this item precede the release below
-    if (threadIdx.x == 0) {
-      __threadfence();  // cumulative over the CTA's stores ordered by the barrier
-      atomicAdd(&done[r], 1ull);
-    }
-    item = next;
+  }
+  __syncthreads();
+  float G[3][3][3];
+  if (active) {
+    const int xm = x == 0 ? (int)nx - 1 : (int)x - 1, xp = x + 1 == nx ? 0 : (int)x + 1;
+    // plane a of every group: the value at x - c_x = x + 1, x, x - 1 (periodic in x)
+    const T* const pa[3] = {sm + row * nx + xp, sm + rn + row * nx + x, sm + 2 * rn + row * nx + xm};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          G[a][b][c] = S::load(pa[a][(3 * b + c) * kGroup], class_at(a, b, c), rep.ss);
+    if (rep.noise)
+      collide_site<kModelReg, true, false, false>(G, rep.cp, noise);
+    else
+      collide_site<kModelReg, false, false, false>(G, rep.cp, noise);
+  }
+  __syncthreads();  // every input is read: the tile takes the outputs
+  if (active) {
+    T* out = sm + row * nx + x;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i)
+      out[plane_of(i) * rn] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), rep.ss);
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    tma_store_4d(rep.maps + 2 * (parity ^ 1) + 1, sm, 0, (int)y0, (int)z, 0);
+    bulk_commit();
+    bulk_wait_read();
   }
 }
 
 template <int kStore, int kTile>
-static cudaError_t launch_batch_t(const ReplicaDev* reps, const int* tile_rep, int64_t tiles,
-                                  int64_t nsteps, const unsigned long long* step0, unsigned long long* queue,
-                                  unsigned long long* done, int* err, int grid, cudaStream_t st) {
-  k_batch_run<kStore, kTile><<<grid, kTile, 0, st>>>(reps, tile_rep, tiles, nsteps, step0, queue, done, err);
-  return cudaGetLastError();
+static cudaError_t set_smem_t() {
+  const size_t smem = batch_smem_bytes(kTile, storage_bytes(kStore));
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_batch_step<kStore, kTile, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// nsteps steps over all tiles: per step one launch of the rows tiles [0, rows_tiles) and
+// one of the sites tiles [rows_tiles, tiles), chained by programmatic dependent launch.
+template <int kStore, int kTile>
+static cudaError_t launch_batch_t(const ReplicaDev* reps, const int* tile_rep, int64_t tiles, int64_t rows_tiles,
+                                  int64_t nsteps, const unsigned long long* step0, int* err, cudaStream_t st) {
+  if (cudaError_t e = set_smem_t<kStore, kTile>()) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kTile);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  for (int64_t k = 0; k < nsteps; ++k) {
+    if (rows_tiles > 0) {
+      cfg.gridDim = dim3((unsigned)rows_tiles);
+      cfg.dynamicSmemBytes = batch_smem_bytes(kTile, storage_bytes(kStore));
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, true>, reps, tile_rep, (int64_t)0,
+                                               step0, (uint32_t)k, err);
+      if (e != cudaSuccess) return e;
+    }
+    if (tiles > rows_tiles) {
+      cfg.gridDim = dim3((unsigned)(tiles - rows_tiles));
+      cfg.dynamicSmemBytes = 0;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, false>, reps, tile_rep, rows_tiles,
+                                               step0, (uint32_t)k, err);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 template <int kStore, int kTile>
 static int occupancy_t() {
+  if (set_smem_t<kStore, kTile>() != cudaSuccess) return 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_run<kStore, kTile>, kTile, 0) != cudaSuccess) return 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<kStore, kTile, true>, kTile,
+                                                    batch_smem_bytes(kTile, storage_bytes(kStore))) != cudaSuccess)
+    return 1;
   return std::max(n, 1);
 }
 
-static int batch_occupancy(int storage, int tile) {
-  switch (storage * 10 + (tile == 128 ? 0 : (tile == 256 ? 1 : 2))) {
-    case 0: return occupancy_t<kStoreF32, 128>();
-    case 1: return occupancy_t<kStoreF32, 256>();
-    case 2: return occupancy_t<kStoreF32, 512>();
-    case 10: return occupancy_t<kStoreF16, 128>();
-    case 11: return occupancy_t<kStoreF16, 256>();
-    case 12: return occupancy_t<kStoreF16, 512>();
-    case 20: return occupancy_t<kStoreBF16, 128>();
-    case 21: return occupancy_t<kStoreBF16, 256>();
-    default: return occupancy_t<kStoreBF16, 512>();
+// Tile sizes: CTA threads, and sites per tile of the sites kind. 192 divides every row
+// length 16, 24, 32, 48, 64, 96 of the ensemble configuration.
+constexpr int kBatchTiles[4] = {128, 192, 256, 512};
+
+static int tile_index(int tile) {
+  for (int k = 0; k < 4; ++k)
+    if (kBatchTiles[k] == tile) return k;
+  return -1;
+}
+
+#define RFLBM_BATCH_DISPATCH(storage, tile, CALL)                    \
+  switch ((storage) * 4 + tile_index(tile)) {                        \
+    case 0: { constexpr int S = kStoreF32, T = 128; CALL; }          \
+    case 1: { constexpr int S = kStoreF32, T = 192; CALL; }          \
+    case 2: { constexpr int S = kStoreF32, T = 256; CALL; }          \
+    case 3: { constexpr int S = kStoreF32, T = 512; CALL; }          \
+    case 4: { constexpr int S = kStoreF16, T = 128; CALL; }          \
+    case 5: { constexpr int S = kStoreF16, T = 192; CALL; }          \
+    case 6: { constexpr int S = kStoreF16, T = 256; CALL; }          \
+    case 7: { constexpr int S = kStoreF16, T = 512; CALL; }          \
+    case 8: { constexpr int S = kStoreBF16, T = 128; CALL; }         \
+    case 9: { constexpr int S = kStoreBF16, T = 192; CALL; }         \
+    case 10: { constexpr int S = kStoreBF16, T = 256; CALL; }        \
+    case 11: { constexpr int S = kStoreBF16, T = 512; CALL; }        \
+    default: break;                                                  \
   }
+
+static int batch_occupancy(int storage, int tile) {
+  RFLBM_BATCH_DISPATCH(storage, tile, return (occupancy_t<S, T>()));
+  return 1;
 }
 
 static cudaError_t launch_batch(int storage, int tile, const ReplicaDev* reps, const int* tile_rep,
-                                int64_t tiles, int64_t nsteps, const unsigned long long* step0,
-                                unsigned long long* queue, unsigned long long* done, int* err,
-                                int grid, cudaStream_t st) {
-#define RFLBM_BATCH_CASE(S, T) \
-  return launch_batch_t<S, T>(reps, tile_rep, tiles, nsteps, step0, queue, done, err, grid, st)
-  switch (storage * 10 + (tile == 128 ? 0 : (tile == 256 ? 1 : 2))) {
-    case 0: RFLBM_BATCH_CASE(kStoreF32, 128);
-    case 1: RFLBM_BATCH_CASE(kStoreF32, 256);
-    case 2: RFLBM_BATCH_CASE(kStoreF32, 512);
-    case 10: RFLBM_BATCH_CASE(kStoreF16, 128);
-    case 11: RFLBM_BATCH_CASE(kStoreF16, 256);
-    case 12: RFLBM_BATCH_CASE(kStoreF16, 512);
-    case 20: RFLBM_BATCH_CASE(kStoreBF16, 128);
-    case 21: RFLBM_BATCH_CASE(kStoreBF16, 256);
-    default: RFLBM_BATCH_CASE(kStoreBF16, 512);
-  }
-#undef RFLBM_BATCH_CASE
+                                int64_t tiles, int64_t rows_tiles, int64_t nsteps,
+                                const unsigned long long* step0, int* err, cudaStream_t st) {
+  RFLBM_BATCH_DISPATCH(storage, tile,
+                       return (launch_batch_t<S, T>(reps, tile_rep, tiles, rows_tiles, nsteps, step0, err, st)));
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace rflbm_dev
@@ -189,10 +310,11 @@ struct rflbm_batch {
   std::vector<ReplicaDev> host;
   ReplicaDev* dev_reps = nullptr;
   int* tile_rep = nullptr;
+  CUtensorMap* maps = nullptr;  // 4 per replica (rows tiles), device memory
   int64_t tiles = 0;
+  int64_t rows_tiles = 0;  // tiles [0, rows_tiles) are rows tiles, the rest sites tiles
   int tile = 256;
   int ctas_per_sm = 1;
-  unsigned long long* counters = nullptr;  // [0] queue, [1 + r] completion per replica
   unsigned long long* step0 = nullptr;     // first step index of the current run (device)
   int* err = nullptr;
   double* partials = nullptr;
@@ -234,14 +356,46 @@ int upload_reps(rflbm_batch* b) {
   return RFLBM_OK;
 }
 
-// Builds the per-replica descriptors and the tile map for tile size `tile`.
+// Builds the per-replica descriptors, their tensor maps and the tile map for tile size
+// `tile` (CTA threads). A replica takes rows tiles when its row is a whole number of
+// 16-byte units, divides the tile, fits the TMA box limit (256), and its maps encode.
 int layout_tiles(rflbm_batch* b, int tile) {
+  const size_t elem = storage_bytes(b->storage);
+  std::vector<CUtensorMap> maps((size_t)b->n * 4);
+  if (!b->maps) BCUDA(cudaMalloc((void**)&b->maps, sizeof(CUtensorMap) * maps.size()), "allocating tensor maps");
   int64_t tiles = 0;
   for (int r = 0; r < b->n; ++r) {
-    b->host[r].tile_begin = tiles;
-    b->host[r].ntiles = ((int64_t)b->host[r].geo.n + tile - 1) / tile;
-    tiles += b->host[r].ntiles;
+    ReplicaDev& d = b->host[r];
+    const Geometry& g = d.geo;
+    d.rows = 0;
+    d.yblocks = 0;
+    d.maps = nullptr;
+    if ((g.nx * elem) % 16 == 0 && tile % g.nx == 0 && g.nx <= 256) {
+      const uint32_t R = (uint32_t)tile / g.nx;
+      bool ok = true;
+      for (int k = 0; k < 2 && ok; ++k)
+        ok = encode_population_map(&maps[4 * r + 2 * k], d.buf[k], g, g.nx, R, 3, b->storage) &&
+             encode_population_map(&maps[4 * r + 2 * k + 1], d.buf[k], g, g.nx, R, kQ, b->storage);
+      if (ok) {
+        d.rows = R;
+        d.yblocks = (g.ny + R - 1) / R;
+        d.maps = b->maps + 4 * r;
+      }
+    }
+    d.ntiles = d.rows ? (int64_t)g.nz * d.yblocks : ((int64_t)g.n + tile - 1) / tile;
   }
+  // rows tiles first, then sites tiles (one launch each per step)
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int r = 0; r < b->n; ++r) {
+      ReplicaDev& d = b->host[r];
+      if ((d.rows != 0) != (pass == 0)) continue;
+      d.tile_begin = tiles;
+      tiles += d.ntiles;
+    }
+    if (pass == 0) b->rows_tiles = tiles;
+  }
+  BCUDA(cudaMemcpy(b->maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice),
+        "uploading tensor maps");
   std::vector<int> map((size_t)tiles);
   for (int r = 0; r < b->n; ++r)
     for (int64_t j = 0; j < b->host[r].ntiles; ++j) map[(size_t)(b->host[r].tile_begin + j)] = r;
@@ -264,16 +418,10 @@ int layout_tiles(rflbm_batch* b, int tile) {
   return upload_reps(b);
 }
 
-// The launch sequence of one run: clear the queue and completion counters, run the
-// persistent kernel.
+// The launch sequence of one run: one step kernel over all tiles per step.
 int enqueue_run(rflbm_batch* b, int64_t nsteps, cudaStream_t st) {
-  BCUDA(cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long) * (size_t)(b->n + 1), st),
-        "clearing the work counters");
-  const int64_t items = b->tiles * nsteps;
-  const int64_t full = (int64_t)b->ctas_per_sm * b->num_sms;
-  const int grid = (int)std::max<int64_t>(1, std::min(full, items));
-  BCUDA(launch_batch(b->storage, b->tile, b->dev_reps, b->tile_rep, b->tiles, nsteps, b->step0,
-                     b->counters, b->counters + 1, b->err, grid, st),
+  BCUDA(launch_batch(b->storage, b->tile, b->dev_reps, b->tile_rep, b->tiles, b->rows_tiles, nsteps, b->step0,
+                     b->err, st),
         "launching the batched step kernel");
   return RFLBM_OK;
 }
@@ -284,7 +432,7 @@ int bsync(rflbm_batch* b, const char* what) {
   BCUDA(cudaMemcpy(&flag, b->err, sizeof(int), cudaMemcpyDeviceToHost), "reading the error flag");
   if (flag) {
     cudaMemset(b->err, 0, sizeof(int));
-    return bfail(RFLBM_ETIMEOUT, "%s: a CTA gave up waiting for a replica's previous step", what);
+    return bfail(RFLBM_ETIMEOUT, "%s: a CTA gave up waiting for its bulk copies (bounded wait expired)", what);
   }
   return RFLBM_OK;
 }
@@ -332,7 +480,7 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
     return nullptr;
   }
   if (!(rho0 > 0.0) || (storage != RFLBM_STORE_F32 && storage != RFLBM_STORE_F16 && storage != RFLBM_STORE_BF16) ||
-      (tile != 0 && tile != 128 && tile != 256 && tile != 512)) {
+      (tile != 0 && tile_index(tile) < 0)) {
     bfail(RFLBM_EINVAL, "rflbm_batch_create: invalid rho0, storage or tile");
     return nullptr;
   }
@@ -407,8 +555,7 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
   }
   if (rc == RFLBM_OK) {
     cudaError_t e = cudaMalloc((void**)&b->dev_reps, sizeof(ReplicaDev) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->counters, sizeof(unsigned long long) * (size_t)(n + 2));
-    if (e == cudaSuccess) b->step0 = b->counters + n + 1;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->step0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(b->step0, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
@@ -430,7 +577,7 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
     cudaEventCreate(&t1);
     float best = 1e30f;
     int best_tile = 256;
-    for (int cand : {128, 256, 512}) {
+    for (int cand : kBatchTiles) {
       if (layout_tiles(b, cand) != RFLBM_OK) continue;
       enqueue_run(b, 1, b->stream);  // warm-up
       cudaEventRecord(t0, b->stream);
@@ -464,7 +611,8 @@ void rflbm_batch_destroy(rflbm_batch_t* b) {
   }
   cudaFree(b->dev_reps);
   cudaFree(b->tile_rep);
-  cudaFree(b->counters);
+  cudaFree(b->maps);
+  cudaFree(b->step0);
   cudaFree(b->err);
   cudaFree(b->partials);
   if (b->exec) cudaGraphExecDestroy(b->exec);

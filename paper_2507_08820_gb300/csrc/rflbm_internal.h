@@ -150,6 +150,11 @@ struct StepVariant {
   int storage;      // kStoreF32 / kStoreF16 / kStoreBF16 (16-bit: no ghost_neq, no phi_rho0)
 };
 
+// Encodes the population buffer at `base` (4-D: x, y, z, plane; planes ps apart) for tiled
+// TMA copies of (box_x, box_y, 1, box_planes) boxes; false if the driver refuses.
+bool encode_population_map(CUtensorMap* map, void* base, const Geometry& g, uint32_t box_x,
+                           uint32_t box_y, uint32_t box_planes, int storage);
+
 // Records `msg` (and `detail`, if not NULL) as the calling thread's last error
 // (rflbm_last_error) and returns `code`.
 int record_error(int code, const char* msg, const char* detail);

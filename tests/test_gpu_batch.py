@@ -1,7 +1,11 @@
-"""Batched ensembles: many replicas of uneven sizes, seeds, tau and kT in one persistent
-launch reproduce their single-box runs; the ensemble of the batched configuration
+"""Batched ensembles: many replicas of uneven sizes, seeds, tau and kT advanced together
+reproduce their single-box runs; the ensemble of the batched configuration
 (64 replicas, edges in {16,24,32,48,64,96}, kT log-uniform in [1e-5, 1e-3], tau uniform in
-[0.55, 1.2], rest start, 1000 steps) runs in float32 and float16 storage."""
+[0.55, 1.2], rest start, 1000 steps) runs in float32 and float16 storage.
+
+The replicas below take both kinds of tile at every tile size: rows tiles where nx divides
+the tile (row blocks that fill a slab exactly, end short of it, or hold more rows than the
+slab has, with one or two slabs), site tiles elsewhere."""
 import numpy as np
 import pytest
 
@@ -14,7 +18,9 @@ SMALL = [dict(nx=16, ny=16, nz=16, tau=0.6, kT=1e-4, seed=3),
          dict(nx=32, ny=32, nz=32, tau=1.1, kT=1e-5, seed=5),
          dict(nx=20, ny=12, nz=9, tau=0.55, kT=2e-4, seed=6),
          dict(nx=64, ny=8, nz=4, tau=0.8, kT=0.0, seed=7),
-         dict(nx=1, ny=1, nz=1, tau=0.7, kT=1e-4, seed=8)]
+         dict(nx=1, ny=1, nz=1, tau=0.7, kT=1e-4, seed=8),
+         dict(nx=32, ny=3, nz=1, tau=0.75, kT=1e-4, seed=9),
+         dict(nx=16, ny=5, nz=2, tau=0.65, kT=3e-4, seed=10)]
 
 
 @pytest.fixture(scope="module")
@@ -45,8 +51,8 @@ def _batch_pops(R, b, reps, r):
     return f
 
 
-@pytest.mark.parametrize("storage", [0, 1])
-@pytest.mark.parametrize("tile", [128, 256, 512])
+@pytest.mark.parametrize("storage", [0, 1, 2])
+@pytest.mark.parametrize("tile", [128, 192, 256, 512])
 def test_replicas_reproduce_their_single_box_runs(R, storage, tile):
     b = R.rflbm_batch_create(SMALL, storage=storage, tile=tile)
     assert R.rflbm_batch_tuning(b)[0] == tile
@@ -64,7 +70,7 @@ def test_replicas_reproduce_their_single_box_runs(R, storage, tile):
 def test_autotuner_and_errors(R):
     b = R.rflbm_batch_create(SMALL[:3], tile=0)
     tile, per_sm, tiles = R.rflbm_batch_tuning(b)
-    assert tile in (128, 256, 512) and per_sm >= 1 and tiles > 0
+    assert tile in (128, 192, 256, 512) and per_sm >= 1 and tiles > 0
     with pytest.raises(R.RflbmError) as e:
         R.rflbm_batch_run(b, 1)  # not initialised
     assert e.value.status == R.RFLBM_ESTATE
