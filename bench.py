@@ -407,7 +407,7 @@ def gb300_arm(args):
                 "peak_source": f"hbm_gbs of {peak_kind}", "kernel": kname,
                 "algorithmic_bytes_per_launch": BYTES_PER_SITE[args.storage] * n}
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and info.world == 1:  # the oracle baseline is an N = 1 figure
         r = oracle_sample_rate(e, args.tau, args.kT, budget_s=15.0, steps=2)
         cpu = {"value": r["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
                "sample": f"FP64 oracle collision + streaming of {r['sites']} sampled sites of "
