@@ -13,6 +13,7 @@
 #include <cufft.h>
 
 #include "../../include/rflbm.h"
+#include "../../include/rflbm_testing.h"
 #include "rflbm_aux.h"
 #include "rflbm_diag.h"
 
@@ -43,6 +44,7 @@ struct rflbm {
   CUtensorMap load_map[2];     // per buffer: source-row loads with halo
   CUtensorMap store_map[2];    // per buffer: row-segment stores
   CUtensorMap row_map;         // AA with one segment per row: three-plane row stores
+  uint32_t test_extra_tx = 0;  // testing hook (rflbm_testing_expect_extra_bytes)
   bool has_row_map = false;
   // diagnostics (allocated on first use)
   double* diag_partials = nullptr;
@@ -496,6 +498,7 @@ int rflbm_step(rflbm_t* h, int64_t n) {
   p.key1 = (uint32_t)(h->cfg.seed >> 32);
   p.replica = h->cfg.replica;
   p.err = h->err;
+  p.test_extra_tx = h->test_extra_tx;
   for (int64_t t = 0; t < n; ++t) {
     p.step = (uint32_t)h->step;
     cudaError_t e;
@@ -830,6 +833,13 @@ int rflbm_step_path(const rflbm_t* h, int* width) {
   if (int e = check_handle(h)) return e;
   if (width) *width = h->tma_width;
   return h->kernel;
+}
+
+int rflbm_testing_expect_extra_bytes(rflbm_t* h, uint32_t bytes) {
+  if (int e = check_handle(h)) return e;
+  if (bytes > (1u << 20)) return fail(RFLBM_EINVAL, "extra byte count %u above 2^20", bytes);
+  h->test_extra_tx = bytes;
+  return RFLBM_OK;
 }
 
 int rflbm_philox4x32_10(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, int64_t n) {

@@ -128,6 +128,7 @@ struct StepParams {
   void* dst;
   int* err;  // device error flag (bit 0: a bounded wait expired)
   uint32_t key0, key1, step, replica;
+  uint32_t test_extra_tx;  // testing hook: bytes a TMA step expects beyond its copies (0)
 };
 
 // TMA descriptors of a source buffer (the three planes of a source row, row segment plus

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   T patch_l = T(), patch_r = T();
   int at_l = -1, at_r = -1;
   if (t < kGroups) {
-    if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)));
+    if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)) + p.test_extra_tx);
     const int cy = t / 3 - 1, cz = t % 3 - 1;
     int ys = (int)y - cy, zs = (int)z - cz;
     ys += ys < 0 ? (int)p.geo.ny : 0;

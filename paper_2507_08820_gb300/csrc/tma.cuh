@@ -40,12 +40,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0u;
 }
 
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Upper bound of one bounded wait in time (besides its poll count).
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
 // Waits for phase `parity` of the barrier for at most `max_polls` polls (each poll may
-// suspend the thread for a hardware-defined time); returns false if it gave up.
+// suspend the thread for a hardware-defined time) and at most kWaitLimitNs; returns false
+// if it gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint32_t max_polls) {
-  for (uint32_t it = 0; it < max_polls; ++it) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1; it < max_polls; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0u && global_ns() - t0 > kWaitLimitNs) return false;
   }
   return false;
 }

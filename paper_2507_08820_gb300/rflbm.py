@@ -119,6 +119,7 @@ _sig = {
     "rflbm_batch_stats": (C.c_int, [_H, C.c_int, C.POINTER(rflbm_stats_t)]),
     "rflbm_structure_factor": (C.c_int, [_H, C.c_int, C.c_int, _P, _P]),
     "rflbm_shell_count": (C.c_int, [_H]),
+    "rflbm_testing_expect_extra_bytes": (C.c_int, [_H, C.c_uint32]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(lib, _name)
@@ -281,6 +282,13 @@ def rflbm_get_dims(h):
 
 def rflbm_launches_per_step(h):
     return _check(lib.rflbm_launches_per_step(h))
+
+
+def rflbm_testing_expect_extra_bytes(h, nbytes):
+    """Testing hook (include/rflbm_testing.h): later TMA steps wait for bytes that never
+    arrive, so their bounded waits run out and the next synchronising call raises
+    RFLBM_ETIMEOUT; 0 restores normal operation."""
+    return _check(lib.rflbm_testing_expect_extra_bytes(h, int(nbytes)))
 
 
 def rflbm_step_path(h):

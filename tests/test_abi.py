@@ -1,6 +1,7 @@
 """The C ABI library builds, loads and exports every function include/rflbm.h declares;
 host-side validation works without a GPU."""
 import ctypes
+import glob
 import os
 import re
 
@@ -10,9 +11,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    text = open(os.path.join(ROOT, "include", "rflbm.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(rflbm_\w+)\s*\(", text)))
+    names = set()
+    for header in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = re.sub(r"/\*.*?\*/", "", open(header).read(), flags=re.S)
+        names.update(re.findall(r"\b(rflbm_\w+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
