@@ -159,3 +159,37 @@ def test_taylor_green_decay_with_float16_storage(R):
     box.close()
     rate = -np.polyfit(ts[2:], np.log(amps[2:]), 1)[0]
     assert abs(rate / (2.0 * o.CS2 * (tau - 0.5) * k * k) - 1.0) < 0.01
+
+
+def _stats_512(R, storage, steps=5000):
+    L, kT = 512, 1e-4
+    n = L ** 3
+    box = R.Box(L, L, L, tau=0.8, kT=kT, seed=1, storage=storage)
+    R.rflbm_init_rest(box.h)
+    R.rflbm_step(box.h, steps)
+    s1, s2 = R.rflbm_mode_sums(box.h)
+    var = s2 / n - (s1 / n) ** 2
+    ns = R.rflbm_shell_count(box.h)
+    s_rho, count = R.rflbm_structure_factor(box.h, 0, ns)
+    box.close()
+    bands = [(8, 16), (16, 32), (32, 64), (64, 256)]
+    sk = np.array([s_rho[a:b].sum() / count[a:b].sum() for a, b in bands])
+    return var, sk
+
+
+@pytest.mark.slow
+def test_512_cubed_mixed_precision_statistics(R):
+    """Config C3 at its size: 512^3, tau 0.8, kT 1e-4, 5000 steps from rest, in float32,
+    float16 and bfloat16 storage (same seed). Every per-site mode variance and the density
+    structure factor on four shell bands agree with the float32 run to the storage's
+    rounding (float16 0.1 %, bfloat16 1 %) and with the FDT values rho0 kT b_k / cs2 and
+    rho0 kT / cs2 to 1 %. The float32 run itself is pinned to the FDT at 128^3."""
+    kT = 1e-4
+    var32, sk32 = _stats_512(R, 0)
+    theory = 3.0 * kT * B
+    assert np.all(np.abs(var32 / theory - 1.0) < 0.01), var32 / theory
+    assert np.all(np.abs(sk32 / (3.0 * kT) - 1.0) < 0.01), sk32 / (3.0 * kT)
+    for storage, tol in ((1, 1e-3), (2, 1e-2)):
+        var, sk = _stats_512(R, storage)
+        assert np.all(np.abs(var / var32 - 1.0) < tol), (storage, var / var32)
+        assert np.all(np.abs(sk / sk32 - 1.0) < tol), (storage, sk / sk32)
