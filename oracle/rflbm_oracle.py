@@ -27,7 +27,9 @@ Readings taken where the paper is silent or ambiguous (each listed in the design
   * Eq. 22's "perm" is the sum over the first n-1 indices paired with the last one;
   * the equilibrium of Eq. 26 uses the coefficients of Eq. 21 (the text points at
     Eq. 22, which is the non-equilibrium recursion);
-  * Pi (Sec. III) is the second Hermite coefficient a^(2) = sum_i f_i H^(2)_i.
+  * Pi (Sec. III) is the second Hermite coefficient a^(2) = sum_i f_i H^(2)_i;
+  * a thermal initial state (`thermal_state`): independent Gaussian modes with the
+    variances Eq. 10 maintains, drawn with Philox calls j = 6..12 of step 0.
 
 Layout: populations are arrays of shape (27, N) for N = nx*ny*nz sites with site index
 s = x + nx*(y + ny*z); the state held between steps is the pre-collision f(x, t).
@@ -409,6 +411,30 @@ def macroscopic(f):
 def _tables_cached():
     E, w = basis(), weights()
     return E, w, norms(E, w)
+
+
+def thermal_state(kT: float, seed: int, sites, rho0: float = 1.0, replica: int = 0) -> np.ndarray:
+    """A draw from the stationary distribution of the linearised fluctuating model: at
+    every site all 27 modes m_k of Table II (density and momentum included) are
+    independent normals of variance rho0 kT b_k / c_s^2, the per-mode variance that the
+    amplitude of Eq. 10 maintains (Sec. II.A, after Eq. 10), around the rest state:
+    f = w rho0 + back_transform(m) (Eq. 11). Shape (27, M).
+
+    Noise words (a reading; the paper starts from rest): Philox4x32-10 calls j = 6..12 at
+    counter (site, 0, j, replica) and key (seed mod 2^32, seed div 2^32), outside the calls
+    j = 0..5 of the steps; Box-Muller pairs in order give n[0..27]; m_k = sqrt(rho0 kT b_k
+    / c_s^2) n[k] for k = 0..26.
+    """
+    sites = np.asarray(sites, dtype=np.uint64)
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    n = np.empty((28, sites.size))
+    for j in range(7):
+        x0, x1, x2, x3 = philox4x32_10(
+            (sites, np.zeros_like(sites), np.full_like(sites, 6 + j), np.full_like(sites, replica)), key)
+        n[4 * j], n[4 * j + 1] = box_muller(x0, x1)
+        n[4 * j + 2], n[4 * j + 3] = box_muller(x2, x3)
+    m = np.sqrt(fdt_mode_variance(rho0, kT))[:, None] * n[:Q]
+    return rest_state(sites.size, rho0) + back_transform(m)
 
 
 def fdt_mode_variance(rho0: float, kT: float) -> np.ndarray:

@@ -39,7 +39,7 @@ struct ReplicaDev {
   void* buf[2];
   uint32_t key0, key1;
   int noise;          // kT > 0
-  int cur;            // buffer holding the state at the start of the launch
+  int cur;            // buffer holding the state at the start of a run
   int64_t tile_begin;  // first global tile index of this replica
   int64_t ntiles;      // tiles per step
   uint32_t rows;       // rows per tile (rows tiles), 0: sites tiles
@@ -64,10 +64,9 @@ constexpr int kBatchGroups = 9;  // source rows (c_y, c_z) of a site
 // Rows tiles are held to 56 registers (65536 / (kTile 56) resident CTAs per SM): the
 // replica's collision parameters come from shared memory, not from the constant bank.
 template <int kStore, int kTile, bool kRows>
-__global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 1) k_batch_step(const ReplicaDev* __restrict__ reps,
-                                                      const int* __restrict__ tile_rep, int64_t tile0,
-                                                      const unsigned long long* step0_ptr, uint32_t k,
-                                                      int* err) {
+__global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
+    k_batch_step(const ReplicaDev* __restrict__ reps, const int* __restrict__ tile_rep, int64_t tile0,
+                 const unsigned long long* step0_ptr, uint32_t k, int* err) {
   using S = Storage<kStore>;
   using T = typename S::T;
   constexpr int kGroup = (int)(batch_group_bytes(kTile, sizeof(T)) / sizeof(T));  // elements
