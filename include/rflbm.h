@@ -160,6 +160,15 @@ const char* rflbm_last_error(void);
 /* Fluid at rest: f_i = w_i rho0 (Table I weights; the u = 0 value of Eq. 26); t = 0. */
 int rflbm_init_rest(rflbm_t* h);
 
+/* Thermal equilibrium: every mode k of Table II at every site (density and momentum
+ * included) an independent normal of variance rho0 kT b_k / cs2 around the rest state,
+ * f = w rho0 + w_i sum_k m_k e_ki / b_k (Eq. 11). This is the stationary distribution of
+ * the linearised fluctuating model, the per-mode variance the amplitude of Eq. 10
+ * maintains (Sec. II.A), so statistics need no burn-in. The draws are Philox4x32-10 calls
+ * j = 6..12 at counter (site, 0, j, replica) with the handle's seed (the steps use
+ * j = 0..5). kT = 0 gives the rest state. t = 0. Asynchronous on the handle's stream. */
+int rflbm_init_thermal(rflbm_t* h);
+
 /* f_i(x, 0) = f_i^(0)(rho(x), u(x)), the equilibrium of Eq. 26; t = 0.
  * rho: N doubles, or NULL for rho0 everywhere; u: 3*N doubles (rows x, y, z), or NULL
  * for rest. Host or device memory per on_device. */

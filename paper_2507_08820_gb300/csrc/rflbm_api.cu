@@ -458,6 +458,20 @@ int rflbm_init_rest(rflbm_t* h) {
   return RFLBM_OK;
 }
 
+int rflbm_init_thermal(rflbm_t* h) {
+  if (int e = check_handle(h)) return e;
+  DeviceGuard guard(h->device);
+  h->cur = 0;
+  h->phase = 0;
+  RFLBM_CUDA(launch_init_thermal(vgeo(h), h->cp.rho0, (float)h->cfg.kT, h->ss, h->variant.storage,
+                                 (uint32_t)(h->cfg.seed & 0xffffffffu), (uint32_t)(h->cfg.seed >> 32),
+                                 h->cfg.replica, h->buf[0], h->stream),
+             "launching init_thermal");
+  h->step = 0;
+  h->initialised = true;
+  return RFLBM_OK;
+}
+
 int rflbm_init_field(rflbm_t* h, const double* rho, const double* u, int on_device) {
   if (int e = check_handle(h)) return e;
   DeviceGuard guard(h->device);

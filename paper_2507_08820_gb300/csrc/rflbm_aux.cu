@@ -33,6 +33,70 @@ __global__ void k_init_field(Geometry g, float rho0, StoreScale ss, const double
   }
 }
 
+// Population with the velocity of tile entry (a, b, c) = (c_x + 1, c_y + 1, c_z + 1).
+__host__ __device__ constexpr int pop_at(int a, int b, int c) {
+  for (int k = 0; k < kQ; ++k)
+    if (cx_of(k) == a - 1 && cy_of(k) == b - 1 && cz_of(k) == c - 1) return k;
+  return 0;
+}
+
+// Thermal initial state: every mode of every site an independent normal of variance
+// rho0 kT b_k / cs2 (the variance the amplitude of Eq. 10 maintains) around the rest
+// state, drawn with Philox calls j = 6..12 of counter (site, 0, j, replica) (the step
+// draws use j = 0..5). The scaled moments M = m_k / b_k = sqrt(3 rho0 kT / b_k) n_k go
+// through the back transform of Eq. 11 (three sweeps of 1-D lines, then the weights).
+template <int kStore>
+__global__ void k_init_thermal(Geometry g, float rho0, float kT, StoreScale ss, uint32_t key0, uint32_t key1,
+                               uint32_t replica, typename Storage<kStore>::T* __restrict__ dst) {
+  using S = Storage<kStore>;
+  const int64_t s = (int64_t)blockIdx.x * kAuxBlock + threadIdx.x;
+  if (s >= g.n) return;
+  float nrm[28];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const uint4 w = philox4x32_10(make_uint4(site_of(s), 0u, 6u + (uint32_t)j, replica), key0, key1);
+    float r, c, sn;
+    box_muller(w.x, w.y, r, c, sn);
+    nrm[4 * j] = r * c;
+    nrm[4 * j + 1] = r * sn;
+    box_muller(w.z, w.w, r, c, sn);
+    nrm[4 * j + 2] = r * c;
+    nrm[4 * j + 3] = r * sn;
+  }
+  float M[3][3][3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        M[p][q][r] = sqrtf((float)(3.0 * (1.0 / bnorm(p, q, r))) * rho0 * kT) * nrm[mode_of(p, q, r)];
+  float Z[3][3][3], Y[3][3][3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      line_inverse(M[p][q][0], M[p][q][1], M[p][q][2], Z[p][q][0], Z[p][q][1], Z[p][q][2]);
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      line_inverse(Z[p][0][c], Z[p][1][c], Z[p][2][c], Y[p][0][c], Y[p][1][c], Y[p][2][c]);
+  const Neighbours nb = neighbours(site_of(s), g);
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float o[3];
+      line_inverse(Y[0][b][c], Y[1][b][c], Y[2][b][c], o[0], o[1], o[2]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        dst[pop_slot(g, nb, site_of(s), pop_at(a, b, c))] =
+            S::store((float)(w1d(a) * w1d(b) * w1d(c)) * o[a], class_at(a, b, c), ss);
+      }
+    }
+}
+
 // Import of public-layout populations (double: exact shift in FP64; float: in FP32).
 template <class Tin, int kStore>
 __global__ void k_set_populations(Geometry g, float rho0, StoreScale ss, const Tin* __restrict__ f,
@@ -304,6 +368,12 @@ cudaError_t launch_image_plane(const Geometry& g, size_t elem, const void* plane
     k_image_plane<uint16_t><<<blocks_for(g.ps), kAuxBlock, 0, st>>>(g, (const uint16_t*)plane, cx, cy, cz, (uint16_t*)out);
   else
     return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+cudaError_t launch_init_thermal(const Geometry& g, float rho0, float kT, const StoreScale& ss, int kind,
+                                uint32_t key0, uint32_t key1, uint32_t replica, void* dst, cudaStream_t st) {
+  RFLBM_STORE_DISPATCH(kind, (k_init_thermal<K><<<blocks_for(g.n), kAuxBlock, 0, st>>>(g, rho0, kT, ss, key0, key1,
+                                                                                        replica, (ST<K>*)dst)));
   return cudaGetLastError();
 }
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,

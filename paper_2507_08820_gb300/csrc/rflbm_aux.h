@@ -10,6 +10,9 @@ constexpr int kStatOutFields = 6;  // drho sum, momentum (3), max |u|, non-finit
 
 cudaError_t launch_init_field(const Geometry& g, float rho0, const StoreScale& ss, int kind,
                               const double* rho, const double* u, void* dst, cudaStream_t st);
+// Thermal initial state (independent Gaussian modes with the FDT variances) in view g.view.
+cudaError_t launch_init_thermal(const Geometry& g, float rho0, float kT, const StoreScale& ss, int kind,
+                                uint32_t key0, uint32_t key1, uint32_t replica, void* dst, cudaStream_t st);
 cudaError_t launch_set_populations_f64(const Geometry& g, float rho0, const StoreScale& ss, int kind,
                                        const double* f, void* dst, cudaStream_t st);
 cudaError_t launch_set_populations_f32(const Geometry& g, float rho0, const StoreScale& ss, int kind,

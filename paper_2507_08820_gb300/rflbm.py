@@ -87,6 +87,7 @@ _sig = {
     "rflbm_last_error": (C.c_char_p, []),
     "rflbm_init_rest": (C.c_int, [_H]),
     "rflbm_init_field": (C.c_int, [_H, _P, _P, C.c_int]),
+    "rflbm_init_thermal": (C.c_int, [_H]),
     "rflbm_step": (C.c_int, [_H, C.c_int64]),
     "rflbm_moments": (C.c_int, [_H, _P, _P, _P, C.c_int]),
     "rflbm_stats": (C.c_int, [_H, C.POINTER(rflbm_stats_t)]),
@@ -194,6 +195,10 @@ def rflbm_last_error():
 
 def rflbm_init_rest(h):
     return _check(lib.rflbm_init_rest(h))
+
+
+def rflbm_init_thermal(h):
+    return _check(lib.rflbm_init_thermal(h))
 
 
 def rflbm_init_field(h, rho=None, u=None):
