@@ -2,6 +2,7 @@
 steps, kT = 1/3000): equilibration ratios of the Reg-FLBM against the paper's values, and
 the stability limits of both models (Sec. III: Reg-FLBM stable down to tau = 0.5001,
 BGK-FLBM only from tau = 0.505)."""
+import numpy as np
 import pytest
 
 from conftest import read_golden
@@ -41,3 +42,13 @@ def test_stability_limits_of_both_models(ex):
     assert ex.equilibration_ratios(0.5005, model="bgk") is None
     bgk = ex.equilibration_ratios(0.505, model="bgk")
     assert bgk is not None and all(1.0 < v < 1.15 for v in bgk)
+
+
+def test_spectra_are_flat_from_the_thermal_state(ex):
+    """The Fig. 1 machinery: at tau = 1 from the thermal state every field's per-shell
+    equilibration ratio is 1 within its statistical error on four shell bands."""
+    er, count = ex.er_spectra(1.0, kT=1e-4, model="reg", edge=64, steps=3000, every=100)
+    for f in range(4):
+        for lo, hi in ((2, 4), (4, 8), (8, 16), (16, 32)):
+            mean = np.nansum(er[f, lo:hi] * count[lo:hi]) / count[lo:hi].sum()
+            assert abs(mean - 1.0) < (0.05 if lo == 2 else 0.02), (f, lo, mean)
