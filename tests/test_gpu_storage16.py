@@ -193,3 +193,23 @@ def test_512_cubed_mixed_precision_statistics(R):
         var, sk = _stats_512(R, storage)
         assert np.all(np.abs(var / var32 - 1.0) < tol), (storage, var / var32)
         assert np.all(np.abs(sk / sk32 - 1.0) < tol), (storage, sk / sk32)
+
+
+@pytest.mark.parametrize("storage,rms_max,abs_max", [(0, 1e-6, 1e-5), (1, 1e-3, 6e-3), (2, 8e-3, 5e-2)])
+def test_macroscopic_fields_against_the_oracle(R, storage, rms_max, abs_max):
+    """rho, u and Pi of every site after 20 steps from the thermal state (32^3, tau 0.8,
+    kT 1e-4) against the FP64 oracle, in units of each field's thermal standard deviation
+    (sqrt(3 kT), sqrt(kT), sqrt(2 kT / 3) for Pi_aa, sqrt(kT / 3) for Pi_ab)."""
+    L, kT, tau, seed, steps = 32, 1e-4, 0.8, 5, 20
+    shape, n = (L, L, L), L ** 3
+    f = o.run(o.thermal_state(kT, seed, np.arange(n)), shape, tau, kT, seed, steps)
+    rho_o, u_o, pi_o = o.macroscopic(f)
+    box = R.Box(*shape, tau=tau, kT=kT, seed=seed, storage=storage)
+    R.rflbm_init_thermal(box.h)
+    R.rflbm_step(box.h, steps)
+    rho, u, pi = box.macroscopic()
+    box.close()
+    for d, sd in ((rho - rho_o, np.sqrt(3 * kT)), (u - u_o, np.sqrt(kT)),
+                  (pi[:3] - pi_o[:3], np.sqrt(2 * kT / 3)), (pi[3:] - pi_o[3:], np.sqrt(kT / 3))):
+        assert np.sqrt(np.mean(d ** 2)) / sd < rms_max
+        assert np.max(np.abs(d)) / sd < abs_max
