@@ -43,12 +43,13 @@ def _rel(got, want, rho0=1.0):
 
 
 def _run_pair(R, shape, steps, tau=0.8, kT=1e-4, seed=3, t0=0, model="reg", omega_g=1.0,
-              phi_rho="local", f0=None, kernel=0):
-    box = R.Box(*shape, tau=tau, kT=kT, seed=seed, omega_g=omega_g,
+              phi_rho="local", f0=None, kernel=0, rho0=1.0):
+    box = R.Box(*shape, tau=tau, kT=kT, seed=seed, omega_g=omega_g, rho0=rho0,
                 model=R.RFLBM_MODEL_BGK if model == "bgk" else R.RFLBM_MODEL_REG,
                 phi_rho=R.RFLBM_PHI_RHO0 if phi_rho == "rho0" else R.RFLBM_PHI_LOCAL_RHO,
                 kernel=kernel)
-    R.rflbm_set_populations(box.h, _state(shape, seed=11) if f0 is None else f0)
+    # the state is scaled to the reference density (f^(0) is linear in rho)
+    R.rflbm_set_populations(box.h, np.ascontiguousarray(rho0 * _state(shape, seed=11)) if f0 is None else f0)
     R.rflbm_set_step(box.h, t0)
     start = box.populations()
     R.rflbm_step(box.h, steps)
@@ -56,7 +57,7 @@ def _run_pair(R, shape, steps, tau=0.8, kT=1e-4, seed=3, t0=0, model="reg", omeg
     assert R.rflbm_get_step(box.h) == t0 + steps
     box.close()
     want = o.run(start, shape, tau, kT, seed, steps, t0=t0, model=model, omega_g=omega_g,
-                 phi_rho=phi_rho)
+                 phi_rho=phi_rho, rho0=rho0)
     return got, want, start
 
 
@@ -151,6 +152,7 @@ VARIANTS = [
     dict(kT=0.0), dict(model="bgk"), dict(model="bgk", kT=0.0), dict(omega_g=0.7),
     dict(omega_g=1.4, kT=0.0), dict(phi_rho="rho0"), dict(tau=0.5001), dict(tau=0.51),
     dict(tau=5.0), dict(tau=100.0), dict(kT=1e-3, tau=0.6), dict(model="bgk", tau=0.505),
+    dict(rho0=1.7), dict(rho0=0.6, kT=1e-3), dict(rho0=2.5, model="bgk"), dict(rho0=1.7, phi_rho="rho0"),
 ]
 
 
@@ -158,7 +160,7 @@ VARIANTS = [
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_one_step_variants(R, variant, shape, kernel):
     got, want, _ = _run_pair(R, shape, steps=2, t0=3, kernel=kernel, **variant)
-    assert _rel(got, want) < POP_RTOL, variant
+    assert _rel(got, want, variant.get("rho0", 1.0)) < POP_RTOL, variant
 
 
 # ------------------------------------------------------------------- the 32^3 x 100 run

@@ -30,8 +30,9 @@ def R():
 
 def _one_step(R, shape, storage, kernel, **kw):
     n = int(np.prod(shape))
+    rho0 = kw.get("rho0", 1.0)
     rho, u = W.random_fields(*shape, seed=11, drho=0.02, du=0.03)
-    f0 = np.ascontiguousarray(o.equilibrium_state(rho, u) + W.population_perturbation(n, 12, 2e-4))
+    f0 = np.ascontiguousarray(rho0 * (o.equilibrium_state(rho, u) + W.population_perturbation(n, 12, 2e-4)))
     args = dict(tau=0.8, kT=1e-4, seed=3)
     args.update(kw)
     box = R.Box(*shape, storage=storage, kernel=kernel, **args)
@@ -41,16 +42,17 @@ def _one_step(R, shape, storage, kernel, **kw):
     got = box.populations()
     box.close()
     model = "bgk" if args.get("model", 0) == R.RFLBM_MODEL_BGK else "reg"
-    want = o.run(start, shape, args["tau"], args["kT"], args["seed"], 1, model=model)
+    want = o.run(start, shape, args["tau"], args["kT"], args["seed"], 1, model=model, rho0=rho0)
     return got, want
 
 
 @pytest.mark.parametrize("storage", [1, 2])
 @pytest.mark.parametrize("shape,kernel", [((13, 6, 5), 0), ((64, 6, 5), 2)])
-@pytest.mark.parametrize("variant", [dict(), dict(kT=0.0), dict(model=1), dict(tau=0.51)])
+@pytest.mark.parametrize("variant", [dict(), dict(kT=0.0), dict(model=1), dict(tau=0.51), dict(rho0=1.7),
+                                     dict(rho0=0.6, kT=1e-3)])
 def test_one_step_within_storage_round_off(R, storage, shape, kernel, variant):
     got, want = _one_step(R, shape, storage, kernel, **variant)
-    w = o.weights()[:, None]
+    w = o.weights()[:, None] * variant.get("rho0", 1.0)
     bound = 1.05 * U[storage] * np.abs(want - w) + 1e-6 * w
     assert np.all(np.abs(got - want) <= bound), np.max(np.abs(got - want) / bound)
 
