@@ -32,6 +32,9 @@
  *     failure (thread-local, valid until the next call on the same thread). Work is
  *     enqueued on the handle's stream; a CUDA error raised by a kernel surfaces at the
  *     next call that synchronises (moments, stats, get_*, synchronize).
+ *   - Threads: different handles may be used from different threads at once; one handle
+ *     must not be used by two threads at the same time (its calls share the handle's
+ *     stream, state counters and scratch buffers).
  */
 #ifndef RFLBM_H
 #define RFLBM_H
