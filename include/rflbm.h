@@ -79,8 +79,9 @@ typedef enum {
 } rflbm_phi_rho;
 
 /* Step kernels. Both compute the same step; they differ in how the 27 neighbours are
- * fetched. The TMA kernel needs nx to be a multiple of 32 (row segments of 128, 64 or 32
- * sites); on other boxes every choice runs the general kernel. */
+ * fetched. The TMA kernel needs nx to be a multiple of 32 (row segments of 128, 192, 96,
+ * 64 or 32 sites, the first that divides nx); on other boxes every choice runs the
+ * general kernel. */
 typedef enum {
   RFLBM_KERNEL_AUTO = 0,    /* TMA when the box allows it, else the general kernel */
   RFLBM_KERNEL_GATHER = 1,  /* one thread per site, 27 addressed loads */

@@ -26,7 +26,11 @@ static cudaError_t launch_variant(const TmaMaps& m, const StepParams& p, const S
 }
 
 int tma_segment_width(uint32_t nx) {
+  // the widest segment that tiles the row: wider CTAs amortise their fixed costs (128 sites
+  // measured 94 %, 64 sites 87 %, 32 sites 85 % of the copy bandwidth at 128^3)
   if (nx % 128 == 0) return 128;
+  if (nx % 192 == 0) return 192;
+  if (nx % 96 == 0) return 96;
   if (nx % 64 == 0) return 64;
   if (nx % 32 == 0) return 32;
   return 0;
@@ -37,6 +41,8 @@ cudaError_t launch_step_tma(const TmaMaps& m, const StepParams& p, const StepVar
   if (v.storage != kStoreF32) return launch_step_tma_16(m, p, v, stream);
   switch (m.width) {
     case 128: return launch_variant<128>(m, p, v, stream);
+    case 192: return launch_variant<192>(m, p, v, stream);
+    case 96: return launch_variant<96>(m, p, v, stream);
     case 64: return launch_variant<64>(m, p, v, stream);
     case 32: return launch_variant<32>(m, p, v, stream);
     default: return cudaErrorInvalidValue;

@@ -20,6 +20,8 @@ static cudaError_t launch_16_store(const TmaMaps& m, const StepParams& p, const 
                                    cudaStream_t st) {
   switch (m.width) {
     case 128: return launch_16_w<kStore, 128>(m, p, v, st);
+    case 192: return launch_16_w<kStore, 192>(m, p, v, st);
+    case 96: return launch_16_w<kStore, 96>(m, p, v, st);
     case 64: return launch_16_w<kStore, 64>(m, p, v, st);
     case 32: return launch_16_w<kStore, 32>(m, p, v, st);
     default: return cudaErrorInvalidValue;

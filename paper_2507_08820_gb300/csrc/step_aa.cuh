@@ -1,6 +1,6 @@
 // The fused stream-and-collide step in the AA pattern: one population buffer updated in
 // place, with TMA staging; for boxes whose x edge is a multiple of the row-segment width
-// kW in {32, 64, 128}; templated on the storage format.
+// kW in {32, 64, 96, 128, 192}; templated on the storage format.
 //
 // Between steps the buffer alternates between two views of the same populations
 // (P = plane_of, opp(i) the population with velocity -c_i, P(opp(i)) = 26 - P(i)):
@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
       const int g = 3 * (cy_of(i) + 1) + (cz_of(i) + 1);
-      sm[g * O::kGroup + (cx_of(i) + 1) * kW + ((t + cx_of(i)) & (kW - 1))] =
+      const int pos = t + cx_of(i);  // x + c_x, wrapped within the row
+      sm[g * O::kGroup + (cx_of(i) + 1) * kW + (pos < 0 ? pos + kW : (pos >= kW ? pos - kW : pos))] =
           S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
     }
     fence_proxy_async_smem();
@@ -284,6 +285,8 @@ cudaError_t launch_aa_storage(const TmaMaps& m, const StepParams& p, const StepV
                               cudaStream_t st) {
   switch (m.width) {
     case 128: return launch_aa_variant<kStore, 128>(m, p, v, odd, st);
+    case 192: return launch_aa_variant<kStore, 192>(m, p, v, odd, st);
+    case 96: return launch_aa_variant<kStore, 96>(m, p, v, odd, st);
     case 64: return launch_aa_variant<kStore, 64>(m, p, v, odd, st);
     case 32: return launch_aa_variant<kStore, 32>(m, p, v, odd, st);
     default: return cudaErrorInvalidValue;

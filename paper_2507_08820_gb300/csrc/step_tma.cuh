@@ -1,5 +1,6 @@
 // The fused stream-and-collide step with TMA staging, for boxes whose x edge is a
-// multiple of the row-segment width kW in {32, 64, 128}; templated on the storage format.
+// multiple of the row-segment width kW in {32, 64, 96, 128, 192}; templated on the
+// storage format.
 //
 // One CTA of kW threads updates one row segment [x0, x0 + kW) of one lattice row (y, z).
 // The 27 populations of a site are pulled from 9 source rows (y - c_y, z - c_z), shifted

@@ -56,7 +56,7 @@ def _pair(R, shape, kernel, storage, f0, **kw):
 
 
 CASES = [((13, 6, 5), 0), ((64, 6, 5), 2), ((128, 4, 3), 2), ((96, 5, 4), 2), ((256, 3, 4), 2),
-         ((224, 3, 2), 2), ((288, 2, 3), 2),
+         ((224, 3, 2), 2), ((288, 2, 3), 2), ((576, 2, 2), 2), ((160, 3, 2), 2),
          ((192, 2, 3), 2), ((32, 3, 3), 1)]
 MODELS = [dict(kT=1e-4), dict(kT=0.0), dict(model=1, kT=1e-4), dict(model=1, kT=0.0)]
 

@@ -103,8 +103,9 @@ def test_normals_accurate_for_extreme_radius_draws(R):
 # (shape, TMA row-segment width): the TMA kernels need x edges that are multiples of 32
 # (single- and multi-segment rows below); other boxes run the general gather kernel
 SHAPES = [((1, 1, 1), 0), ((2, 3, 4), 0), ((5, 1, 7), 0), ((17, 9, 5), 0), ((33, 31, 7), 0),
-          ((32, 3, 2), 32), ((96, 4, 3), 32), ((64, 5, 3), 64), ((128, 2, 2), 128),
-          ((256, 3, 1), 128), ((32, 1, 1), 32), ((128, 9, 7), 128)]
+          ((32, 3, 2), 32), ((96, 4, 3), 96), ((64, 5, 3), 64), ((128, 2, 2), 128),
+          ((256, 3, 1), 128), ((32, 1, 1), 32), ((128, 9, 7), 128), ((192, 3, 2), 192),
+          ((288, 2, 3), 96), ((576, 2, 1), 192), ((160, 3, 2), 32), ((320, 2, 2), 64)]
 KERNELS = ["gather", "tma"]
 
 
