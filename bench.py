@@ -311,6 +311,7 @@ def ensemble_arm(args):
     dist.barrier(info, info.local_rank)
     ms_max = dist.max_over_ranks(info, ms, dev)
     tile, per_sm, tiles = R.rflbm_batch_tuning(bh)
+    launches = R.rflbm_batch_launches_per_step(bh) * args.steps
     R.rflbm_batch_destroy(bh)
     if info.rank != 0:
         dist.finalize(info)
@@ -331,7 +332,7 @@ def ensemble_arm(args):
                      "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs of {peak_kind}",
                      "kernel": f"k_batch_step<{args.storage}, {tile}, rows>",
                      "algorithmic_bytes_per_launch": bps * sites},
-        "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clocks,
+        "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks,
     }
     print(json.dumps(line))
     dist.finalize(info)

@@ -320,6 +320,9 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
 void rflbm_batch_destroy(rflbm_batch_t* b);
 /* Tile size in use, resident CTAs per SM of the row-tile kernel, tiles per step. */
 int rflbm_batch_tuning(const rflbm_batch_t* b, int* tile, int* ctas_per_sm, int64_t* tiles_per_step);
+/* Kernel launches per step: 1 when every replica takes one kind of tile, 2 when both
+ * kinds are present (row tiles and site tiles run as separate launches). */
+int rflbm_batch_launches_per_step(const rflbm_batch_t* b);
 /* Every replica at rest, step 0. */
 int rflbm_batch_init_rest(rflbm_batch_t* b);
 /* n steps of every replica (asynchronous on the default stream). */

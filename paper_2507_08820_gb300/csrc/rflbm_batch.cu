@@ -619,6 +619,11 @@ void rflbm_batch_destroy(rflbm_batch_t* b) {
   delete b;
 }
 
+int rflbm_batch_launches_per_step(const rflbm_batch_t* b) {
+  if (!b) return bfail(RFLBM_EINVAL, "batch handle is NULL");
+  return (b->rows_tiles > 0 ? 1 : 0) + (b->tiles > b->rows_tiles ? 1 : 0);
+}
+
 int rflbm_batch_tuning(const rflbm_batch_t* b, int* tile, int* ctas_per_sm, int64_t* tiles_per_step) {
   if (!b) return bfail(RFLBM_EINVAL, "batch handle is NULL");
   if (tile) *tile = b->tile;

@@ -113,6 +113,7 @@ _sig = {
     "rflbm_batch_create": (_H, [_P, C.c_int, C.c_double, C.c_int, C.c_int]),
     "rflbm_batch_destroy": (None, [_H]),
     "rflbm_batch_tuning": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "rflbm_batch_launches_per_step": (C.c_int, [_H]),
     "rflbm_batch_init_rest": (C.c_int, [_H]),
     "rflbm_batch_run": (C.c_int, [_H, C.c_int64]),
     "rflbm_batch_synchronize": (C.c_int, [_H]),
@@ -370,6 +371,10 @@ def rflbm_batch_create(replicas, rho0=1.0, storage=RFLBM_STORE_F32, tile=0):
 
 def rflbm_batch_destroy(b):
     lib.rflbm_batch_destroy(b)
+
+
+def rflbm_batch_launches_per_step(b):
+    return _check(lib.rflbm_batch_launches_per_step(b))
 
 
 def rflbm_batch_tuning(b):

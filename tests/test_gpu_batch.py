@@ -56,6 +56,7 @@ def _batch_pops(R, b, reps, r):
 def test_replicas_reproduce_their_single_box_runs(R, storage, tile):
     b = R.rflbm_batch_create(SMALL, storage=storage, tile=tile)
     assert R.rflbm_batch_tuning(b)[0] == tile
+    assert R.rflbm_batch_launches_per_step(b) == 2  # nx = 16 takes row tiles, nx = 20 site tiles
     R.rflbm_batch_init_rest(b)
     for n in (3, 4, 3):  # several calls: odd/even buffer parity and the step index
         R.rflbm_batch_run(b, n)
@@ -71,6 +72,7 @@ def test_autotuner_and_errors(R):
     b = R.rflbm_batch_create(SMALL[:3], tile=0)
     tile, per_sm, tiles = R.rflbm_batch_tuning(b)
     assert tile in (128, 192, 256, 512) and per_sm >= 1 and tiles > 0
+    assert R.rflbm_batch_launches_per_step(b) in (1, 2)
     with pytest.raises(R.RflbmError) as e:
         R.rflbm_batch_run(b, 1)  # not initialised
     assert e.value.status == R.RFLBM_ESTATE
