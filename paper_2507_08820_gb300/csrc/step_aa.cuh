@@ -219,7 +219,9 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
     for (int i = 0; i < kQ; ++i) {
       const int g = 3 * (cy_of(i) + 1) + (cz_of(i) + 1);
       const int pos = t + cx_of(i);  // x + c_x, wrapped within the row
-      sm[g * O::kGroup + (cx_of(i) + 1) * kW + (pos < 0 ? pos + kW : (pos >= kW ? pos - kW : pos))] =
+      const int wrapped = (kW & (kW - 1)) == 0 ? (pos & (kW - 1))
+                                                : (pos < 0 ? pos + kW : (pos >= kW ? pos - kW : pos));
+      sm[g * O::kGroup + (cx_of(i) + 1) * kW + wrapped] =
           S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
     }
     fence_proxy_async_smem();
