@@ -96,7 +96,8 @@ def measured_peak():
 # the sources the ping-pong TMA step kernel is compiled from (its translation unit and
 # every header it includes)
 STEP_KERNEL_SOURCES = ("collide.cuh", "d3q27.cuh", "philox.cuh", "rflbm_internal.h",
-                       "rflbm_step_tma.cu", "step_tma.cuh", "storage.cuh", "tma.cuh")
+                       "rflbm_step_tma.cu", "rflbm_step_tma16.cu", "step_tma.cuh", "storage.cuh",
+                       "tma.cuh")
 
 
 def kernel_source_hash():
@@ -108,9 +109,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_name(kind, path, kT, model, storage="f32", pattern="pingpong"):
+def kernel_name(kind, path, kT, model, storage="f32", pattern="pingpong", sites_per_thread=1):
     noise = "noise" if kT > 0 else "no noise"
     m = "BGK" if model else "Reg"
+    if kind == 2 and sites_per_thread == 2:
+        return f"step_tma_pair<{storage}, {path}, {m}, {noise}>", f"step_tma_pair_{storage}_{path}"
     if pattern == "aa":
         if kind == 2:
             return (f"step_aa_even+step_aa_odd<{storage}, {path}, {m}, {noise}>",
@@ -379,6 +382,7 @@ def gb300_arm(args):
         del u, rho
         torch.cuda.empty_cache()
     kind, path = R.rflbm_step_path(box.h)
+    pairs = R.rflbm_step_sites_per_thread(box.h)
     R.rflbm_step(box.h, args.warmup)
     R.rflbm_synchronize(box.h)
 
@@ -471,7 +475,7 @@ def gb300_arm(args):
     per_launch_s = ms * 1e-3 / args.steps
     achieved = BYTES_PER_SITE[args.storage] * n / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
-    kname, kstem = kernel_name(kind, path, args.kT, 0, args.storage, args.pattern)
+    kname, kstem = kernel_name(kind, path, args.kT, 0, args.storage, args.pattern, pairs)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(kstem, e),
                 "peak_source": f"hbm_gbs of {peak_kind}", "kernel": kname,

@@ -1,8 +1,15 @@
 // Per-site collision of the Reg-FLBM (Eq. 25) and BGK-FLBM (Eq. 12) in registers.
 //
-// Input: the 27 pre-collision populations of one site as a 3x3x3 tile G[a][b][c]
+// Input: the 27 pre-collision populations of a site as a 3x3x3 tile G[a][b][c]
 // (a = c_x + 1, ...), shifted by the rest state: g_i = f_i - w_i rho0. Output: the
-// shifted post-collision populations g*_i = f*_i - w_i rho0 in the same tile.
+// shifted post-collision populations g*_i = f*_i - w_i rho0 in the same tile, times an
+// output weight per entry (the lattice weight, optionally with a storage scale folded in).
+//
+// Written once for one site per thread (V = float) and for two sites per thread
+// (V = float2), whose lane-wise arithmetic issues as packed f32x2 instructions (sm_100
+// family: one instruction updates both sites). Every operation is an explicitly rounded
+// add, multiply or fused multiply-add, so that every kernel computes a site bit for bit the
+// same way, whichever form it uses.
 //
 // Work per site (all FP32):
 //  1. the ten moments of order <= 2 by three sum-factorised sweeps (Eqs. 3-5):
@@ -16,6 +23,8 @@
 //  3. the back transform f_i = w_i sum_k b_k^-1 e_ki m_k (Eq. 11) by three
 //     sum-factorised sweeps (4 operations per line of three) and the weights.
 #pragma once
+
+#include <cuda_runtime.h>
 
 #include "d3q27.cuh"
 #include "philox.cuh"
@@ -52,86 +61,192 @@ __device__ __forceinline__ void line_inverse(float L0, float L1, float L2, float
 // through the whole collision; kernels that still hold the inputs in shared memory pass a
 // reader instead, and the registers are free in between.
 struct KeepTile {
-  __device__ __forceinline__ float operator()(int, int, int, float g) const { return g; }
+  template <class V>
+  __device__ __forceinline__ V operator()(int, int, int, V g) const { return g; }
 };
 
-template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0, class Reload = KeepTile>
-__device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideParams& cp,
-                                             const SiteNoise& noise, const Reload& reload = Reload()) {
+// ---- lane-wise arithmetic
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vrcp(float a) { return rcp_approx(a); }
+__device__ __forceinline__ float vsqrt(float a) { return sqrt_approx(a); }
+
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vrcp(float2 a) {
+  return make_float2(rcp_approx(a.x), rcp_approx(a.y));
+}
+__device__ __forceinline__ float2 vsqrt(float2 a) {
+  return make_float2(sqrt_approx(a.x), sqrt_approx(a.y));
+}
+
+template <class V>
+__device__ __forceinline__ V splat(float k);
+template <>
+__device__ __forceinline__ float splat<float>(float k) { return k; }
+template <>
+__device__ __forceinline__ float2 splat<float2>(float k) { return make_float2(k, k); }
+
+// k a, k a + c for a scalar k
+template <class V>
+__device__ __forceinline__ V kmul(float k, V a) { return vmul(splat<V>(k), a); }
+template <class V>
+__device__ __forceinline__ V kfma(float k, V a, V c) { return vfma(splat<V>(k), a, c); }
+
+// One line of the inverse 1-D transform (see line_inverse).
+template <class V>
+__device__ __forceinline__ void line_inverse_v(V L0, V L1, V L2, V& om, V& o0, V& op) {
+  const V a = kfma(2.0f / 3.0f, L2, L0);
+  o0 = kfma(-1.0f / 3.0f, L2, L0);
+  om = vsub(a, L1);
+  op = vadd(a, L1);
+}
+
+// Noise source for one site per thread: the normals drawn beforehand (SiteNoise), call j
+// giving the (radius, cos, sin) triples of Box-Muller pairs 2j and 2j + 1.
+struct DrawnNoise {
+  const SiteNoise& n;
+  __device__ __forceinline__ void operator()(int j, float (&r)[2], float (&c)[2], float (&s)[2]) const {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      r[h] = n.r[2 * j + h];
+      c[h] = n.c[2 * j + h];
+      s[h] = n.s[2 * j + h];
+    }
+  }
+};
+
+// Noise source for two sites per thread (sites site0 and site0 + 1): Philox calls j < kPre
+// drawn beforehand by draw() (raw words, while the tile's copies are in flight), the later
+// calls when the collision needs them.
+template <int kPre>
+struct PairNoise {
+  uint32_t site0, step, replica, k0, k1;
+  uint4 w[kPre > 0 ? kPre : 1][2];
+  __device__ __forceinline__ void draw() {
+#pragma unroll
+    for (int j = 0; j < kPre; ++j) {
+      w[j][0] = philox4x32_10(make_uint4(site0, step, (uint32_t)j, replica), k0, k1);
+      w[j][1] = philox4x32_10(make_uint4(site0 + 1u, step, (uint32_t)j, replica), k0, k1);
+    }
+  }
+  __device__ __forceinline__ void operator()(int j, float2 (&r)[2], float2 (&c)[2], float2 (&s)[2]) const {
+    uint4 a, b;
+    if (j < kPre) {
+      a = w[j < kPre ? j : 0][0];
+      b = w[j < kPre ? j : 0][1];
+    } else {
+      a = philox4x32_10(make_uint4(site0, step, (uint32_t)j, replica), k0, k1);
+      b = philox4x32_10(make_uint4(site0 + 1u, step, (uint32_t)j, replica), k0, k1);
+    }
+    box_muller(a.x, a.y, r[0].x, c[0].x, s[0].x);
+    box_muller(b.x, b.y, r[0].y, c[0].y, s[0].y);
+    box_muller(a.z, a.w, r[1].x, c[1].x, s[1].x);
+    box_muller(b.z, b.w, r[1].y, c[1].y, s[1].y);
+  }
+};
+
+// Weight of the tile entry (a, b, c) applied after the back transform: the lattice weight,
+// optionally times the storage scale of its velocity class.
+struct LatticeWeight {
+  __device__ __forceinline__ float operator()(int a, int b, int c) const {
+    return float(w1d(a) * w1d(b) * w1d(c));
+  }
+};
+
+template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0, class V, class Noise,
+          class Reload, class OutWeight>
+__device__ __forceinline__ void collide_tile(V (&G)[3][3][3], const CollideParams& cp,
+                                          const Noise& noise, const Reload& reload,
+                                          const OutWeight& outw) {
   // ---- 1. moments of order <= 2 (sweep x, then y, then z)
-  float X0[3][3], X1[3][3], X2[3][3];
+  V X0[3][3], X1[3][3], X2[3][3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      X2[b][c] = G[2][b][c] + G[0][b][c];
-      X1[b][c] = G[2][b][c] - G[0][b][c];
-      X0[b][c] = X2[b][c] + G[1][b][c];
+      X2[b][c] = vadd(G[2][b][c], G[0][b][c]);
+      X1[b][c] = vsub(G[2][b][c], G[0][b][c]);
+      X0[b][c] = vadd(X2[b][c], G[1][b][c]);
     }
   }
-  float T00[3], T01[3], T02[3], T10[3], T11[3], T20[3];
+  V T00[3], T01[3], T02[3], T10[3], T11[3], T20[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    T02[c] = X0[2][c] + X0[0][c];
-    T01[c] = X0[2][c] - X0[0][c];
-    T00[c] = T02[c] + X0[1][c];
-    T11[c] = X1[2][c] - X1[0][c];
-    T10[c] = X1[2][c] + X1[0][c] + X1[1][c];
-    T20[c] = X2[2][c] + X2[0][c] + X2[1][c];
+    T02[c] = vadd(X0[2][c], X0[0][c]);
+    T01[c] = vsub(X0[2][c], X0[0][c]);
+    T00[c] = vadd(T02[c], X0[1][c]);
+    T11[c] = vsub(X1[2][c], X1[0][c]);
+    T10[c] = vadd(vadd(X1[2][c], X1[0][c]), X1[1][c]);
+    T20[c] = vadd(vadd(X2[2][c], X2[0][c]), X2[1][c]);
   }
-  const float s002 = T00[2] + T00[0];
-  const float drho = s002 + T00[1];
-  const float jz = T00[2] - T00[0];
-  const float jy = T01[0] + T01[1] + T01[2];
-  const float syz = T01[2] - T01[0];
-  const float syy = T02[0] + T02[1] + T02[2];
-  const float jx = T10[0] + T10[1] + T10[2];
-  const float sxz = T10[2] - T10[0];
-  const float sxy = T11[0] + T11[1] + T11[2];
-  const float sxx = T20[0] + T20[1] + T20[2];
-  const float szz = s002;
+  const V s002 = vadd(T00[2], T00[0]);
+  const V drho = vadd(s002, T00[1]);
+  const V jz = vsub(T00[2], T00[0]);
+  const V jy = vadd(vadd(T01[0], T01[1]), T01[2]);
+  const V syz = vsub(T01[2], T01[0]);
+  const V syy = vadd(vadd(T02[0], T02[1]), T02[2]);
+  const V jx = vadd(vadd(T10[0], T10[1]), T10[2]);
+  const V sxz = vsub(T10[2], T10[0]);
+  const V sxy = vadd(vadd(T11[0], T11[1]), T11[2]);
+  const V sxx = vadd(vadd(T20[0], T20[1]), T20[2]);
+  const V szz = s002;
   // second Hermite moment of f: sum g (c c) - (drho / 3) delta (the rest state drops out)
-  const float third_drho = drho * (1.0f / 3.0f);
-  const float axx = sxx - third_drho, ayy = syy - third_drho, azz = szz - third_drho;
+  const V axx = kfma(-1.0f / 3.0f, drho, sxx);
+  const V ayy = kfma(-1.0f / 3.0f, drho, syy);
+  const V azz = kfma(-1.0f / 3.0f, drho, szz);
 
   // ---- 2. density, velocity and the scaled post-collision moments
-  const float rho = cp.rho0 + drho;
-  const float inv_rho = rcp_approx(rho);
-  const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
-  // U[p] = u^p / beta_p: 1, 3u, 9u^2/2 ; RX[p] = rho U_x[p]
-  const float Uy[3] = {1.0f, 3.0f * uy, 4.5f * uy * uy};
-  const float Uz[3] = {1.0f, 3.0f * uz, 4.5f * uz * uz};
-  // BGK scales every equilibrium moment by omega: fold it into the x factor
+  const V rho = vadd(splat<V>(cp.rho0), drho);
+  const V inv_rho = vrcp(rho);
+  const V ux = vmul(jx, inv_rho), uy = vmul(jy, inv_rho), uz = vmul(jz, inv_rho);
+  // U[p] = u^p / beta_p: 1, 3u, 9u^2/2 (index 0 is the constant 1 and never multiplied)
+  const V Uy[3] = {splat<V>(1.0f), kmul(3.0f, uy), vmul(kmul(4.5f, uy), uy)};
+  const V Uz[3] = {splat<V>(1.0f), kmul(3.0f, uz), vmul(kmul(4.5f, uz), uz)};
   const float om = cp.omega;
-  const float rs = kModel == kModelBgk ? om * rho : rho;
-  const float RX[3] = {rs, (3.0f * (kModel == kModelBgk ? om : 1.0f)) * jx, 4.5f * (kModel == kModelBgk ? om * jx : jx) * ux};
-  float M[3][3][3];
+  const bool bgk = kModel == kModelBgk;
+  // RX[p] = rho U_x[p] (BGK: times omega, which scales every equilibrium moment)
+  const V RX[3] = {bgk ? kmul(om, rho) : rho, kmul(bgk ? 3.0f * om : 3.0f, jx),
+                   vmul(kmul(bgk ? 4.5f * om : 4.5f, jx), ux)};
+  V M[3][3][3];
 #pragma unroll
   for (int p = 0; p < 3; ++p)
 #pragma unroll
     for (int q = 0; q < 3; ++q)
 #pragma unroll
-      for (int r = 0; r < 3; ++r) M[p][q][r] = RX[p] * (Uy[q] * Uz[r]);
+      for (int r = 0; r < 3; ++r) {
+        const V yz = q == 0 ? Uz[r] : (r == 0 ? Uy[q] : vmul(Uy[q], Uz[r]));
+        M[p][q][r] = (q == 0 && r == 0) ? RX[p] : vmul(RX[p], yz);
+      }
 
+  const V vom = splat<V>(om);
   if (kModel == kModelReg) {
     // conserved modes are kept exactly
     M[0][0][0] = drho;
-    M[0][1][0] = 3.0f * jy;
-    M[0][0][1] = 3.0f * jz;
+    M[0][1][0] = kmul(3.0f, jy);
+    M[0][0][1] = kmul(3.0f, jz);
     // stress modes: omega a0/b + (1 - omega) m/b
-    M[2][0][0] = fmaf(om, M[2][0][0], cp.neq_diag * axx);
-    M[0][2][0] = fmaf(om, M[0][2][0], cp.neq_diag * ayy);
-    M[0][0][2] = fmaf(om, M[0][0][2], cp.neq_diag * azz);
-    M[1][1][0] = fmaf(om, M[1][1][0], cp.neq_off * sxy);
-    M[1][0][1] = fmaf(om, M[1][0][1], cp.neq_off * sxz);
-    M[0][1][1] = fmaf(om, M[0][1][1], cp.neq_off * syz);
+    M[2][0][0] = vfma(vom, M[2][0][0], kmul(cp.neq_diag, axx));
+    M[0][2][0] = vfma(vom, M[0][2][0], kmul(cp.neq_diag, ayy));
+    M[0][0][2] = vfma(vom, M[0][0][2], kmul(cp.neq_diag, azz));
+    M[1][1][0] = vfma(vom, M[1][1][0], kmul(cp.neq_off, sxy));
+    M[1][0][1] = vfma(vom, M[1][0][1], kmul(cp.neq_off, sxz));
+    M[0][1][1] = vfma(vom, M[0][1][1], kmul(cp.neq_off, syz));
     if (kGhostNeq) {
       // Eq. 22 closed form: a1 = 1/2 sum_ab a1_ab d^2(u_x^p u_y^q u_z^r)/du_a du_b
-      const float rux = rho * ux, ruy = rho * uy, ruz = rho * uz;
-      const float nxx = axx - rux * ux, nyy = ayy - ruy * uy, nzz = azz - ruz * uz;
-      const float nxy = sxy - rux * uy, nxz = sxz - rux * uz, nyz = syz - ruy * uz;
-      const float PX[3] = {1.0f, ux, ux * ux}, PY[3] = {1.0f, uy, uy * uy},
-                  PZ[3] = {1.0f, uz, uz * uz};
+      const V rux = vmul(rho, ux), ruy = vmul(rho, uy), ruz = vmul(rho, uz);
+      const V nxx = vsub(axx, vmul(rux, ux)), nyy = vsub(ayy, vmul(ruy, uy)),
+              nzz = vsub(azz, vmul(ruz, uz));
+      const V nxy = vsub(sxy, vmul(rux, uy)), nxz = vsub(sxz, vmul(rux, uz)),
+              nyz = vsub(syz, vmul(ruy, uz));
+      const V PX[3] = {splat<V>(1.0f), ux, vmul(ux, ux)}, PY[3] = {splat<V>(1.0f), uy, vmul(uy, uy)},
+              PZ[3] = {splat<V>(1.0f), uz, vmul(uz, uz)};
 #pragma unroll
       for (int p = 0; p < 3; ++p)
 #pragma unroll
@@ -139,75 +254,93 @@ __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideP
 #pragma unroll
           for (int r = 0; r < 3; ++r) {
             if (p + q + r < 3) continue;
-            float t = 0.0f;
-            if (p == 2) t = fmaf(nxx, PY[q] * PZ[r], t);
-            if (q == 2) t = fmaf(nyy, PX[p] * PZ[r], t);
-            if (r == 2) t = fmaf(nzz, PX[p] * PY[q], t);
-            if (p >= 1 && q >= 1) t = fmaf(nxy * float(p * q), PX[lo(p)] * PY[lo(q)] * PZ[r], t);
-            if (p >= 1 && r >= 1) t = fmaf(nxz * float(p * r), PX[lo(p)] * PY[q] * PZ[lo(r)], t);
-            if (q >= 1 && r >= 1) t = fmaf(nyz * float(q * r), PX[p] * PY[lo(q)] * PZ[lo(r)], t);
-            M[p][q][r] = fmaf(cp.ghost_keep * float(1.0 / bnorm(p, q, r)), t, M[p][q][r]);
+            V t = splat<V>(0.0f);
+            if (p == 2) t = vfma(nxx, vmul(PY[q], PZ[r]), t);
+            if (q == 2) t = vfma(nyy, vmul(PX[p], PZ[r]), t);
+            if (r == 2) t = vfma(nzz, vmul(PX[p], PY[q]), t);
+            if (p >= 1 && q >= 1)
+              t = vfma(kmul(float(p * q), nxy), vmul(vmul(PX[lo(p)], PY[lo(q)]), PZ[r]), t);
+            if (p >= 1 && r >= 1)
+              t = vfma(kmul(float(p * r), nxz), vmul(vmul(PX[lo(p)], PY[q]), PZ[lo(r)]), t);
+            if (q >= 1 && r >= 1)
+              t = vfma(kmul(float(q * r), nyz), vmul(vmul(PX[p], PY[lo(q)]), PZ[lo(r)]), t);
+            M[p][q][r] = kfma(cp.ghost_keep * float(1.0 / bnorm(p, q, r)), t, M[p][q][r]);
           }
     }
   } else {
     // BGK: omega f^(0) here (omega is in RX), (1 - omega) f added after the back
     // transform; the shifted density mode is omega drho
-    M[0][0][0] = om * drho;
-    M[0][1][0] = om * (3.0f * jy);
-    M[0][0][1] = om * (3.0f * jz);
+    M[0][0][0] = vmul(vom, drho);
+    M[0][1][0] = vmul(vom, kmul(3.0f, jy));
+    M[0][0][1] = vmul(vom, kmul(3.0f, jz));
   }
   if (kNoise) {
     // Box-Muller pair m gives the normals r_k of modes k = 2m + 4 (cosine) and 2m + 5 (sine)
-    const float srho = kPhiRho0 ? cp.sqrt_rho0 : sqrt_approx(rho);
+    const V srho = kPhiRho0 ? splat<V>(cp.sqrt_rho0) : vsqrt(rho);
 #pragma unroll
-    for (int m = 0; m < 12; ++m) {
-      const int k0 = 2 * m + 4, k1 = 2 * m + 5;
-      float& M0 = M[p_of(k0)][q_of(k0)][r_of(k0)];
-      const float rr = noise.r[m] * srho;
-      if (k1 < kQ && same_amplitude(k0, k1)) {
-        float& M1 = M[p_of(k1)][q_of(k1)][r_of(k1)];
-        const float a = rr * cp.amp[k0 - 4];
-        M0 = fmaf(a, noise.c[m], M0);
-        M1 = fmaf(a, noise.s[m], M1);
-      } else {
-        M0 = fmaf(cp.amp[k0 - 4], rr * noise.c[m], M0);
-        if (k1 < kQ) {
-          float& M1 = M[p_of(k1 < kQ ? k1 : 0)][q_of(k1 < kQ ? k1 : 0)][r_of(k1 < kQ ? k1 : 0)];
-          M1 = fmaf(cp.amp[(k1 < kQ ? k1 : 4) - 4], rr * noise.s[m], M1);
+    for (int j = 0; j < 6; ++j) {
+      V nr[2], nc[2], ns[2];
+      noise(j, nr, nc, ns);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = 2 * j + h;
+        const int k0 = 2 * m + 4, k1 = 2 * m + 5;
+        V& M0 = M[p_of(k0)][q_of(k0)][r_of(k0)];
+        const V rr = vmul(nr[h], srho);
+        if (k1 < kQ && same_amplitude(k0, k1)) {
+          V& M1 = M[p_of(k1)][q_of(k1)][r_of(k1)];
+          const V a = kmul(cp.amp[k0 - 4], rr);
+          M0 = vfma(a, nc[h], M0);
+          M1 = vfma(a, ns[h], M1);
+        } else {
+          M0 = kfma(cp.amp[k0 - 4], vmul(rr, nc[h]), M0);
+          if (k1 < kQ) {
+            const int k1c = k1 < kQ ? k1 : 4;  // (k1 = 27 does not exist: pair 11's sine is unused)
+            V& M1 = M[p_of(k1c)][q_of(k1c)][r_of(k1c)];
+            M1 = kfma(cp.amp[k1c - 4], vmul(rr, ns[h]), M1);
+          }
         }
       }
     }
   }
 
   // ---- 3. back transform (sweep z, then y, then x) and the lattice weights
-  float Z[3][3][3];  // [p][q][c]
+  V Z[3][3][3];  // [p][q][c]
 #pragma unroll
   for (int p = 0; p < 3; ++p)
 #pragma unroll
     for (int q = 0; q < 3; ++q)
-      line_inverse(M[p][q][0], M[p][q][1], M[p][q][2], Z[p][q][0], Z[p][q][1], Z[p][q][2]);
-  float Y[3][3][3];  // [p][b][c]
+      line_inverse_v(M[p][q][0], M[p][q][1], M[p][q][2], Z[p][q][0], Z[p][q][1], Z[p][q][2]);
+  V Y[3][3][3];  // [p][b][c]
 #pragma unroll
   for (int p = 0; p < 3; ++p)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      line_inverse(Z[p][0][c], Z[p][1][c], Z[p][2][c], Y[p][0][c], Y[p][1][c], Y[p][2][c]);
+      line_inverse_v(Z[p][0][c], Z[p][1][c], Z[p][2][c], Y[p][0][c], Y[p][1][c], Y[p][2][c]);
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float o[3];
-      line_inverse(Y[0][b][c], Y[1][b][c], Y[2][b][c], o[0], o[1], o[2]);
+      V o[3];
+      line_inverse_v(Y[0][b][c], Y[1][b][c], Y[2][b][c], o[0], o[1], o[2]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const float wt = float(w1d(a) * w1d(b) * w1d(c));
+        const V wt = splat<V>(outw(a, b, c));
         if (kModel == kModelBgk) {
-          G[a][b][c] = fmaf(1.0f - om, reload(a, b, c, G[a][b][c]), wt * o[a]);
+          G[a][b][c] = vfma(splat<V>(1.0f - om), reload(a, b, c, G[a][b][c]), vmul(wt, o[a]));
         } else {
-          G[a][b][c] = wt * o[a];
+          G[a][b][c] = vmul(wt, o[a]);
         }
       }
     }
+}
+
+// The collision of one site per thread with its normals drawn beforehand and the lattice
+// weights (the storage scale is applied by the caller).
+template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0, class Reload = KeepTile>
+__device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideParams& cp,
+                                             const SiteNoise& noise, const Reload& reload = Reload()) {
+  collide_tile<kModel, kNoise, kGhostNeq, kPhiRho0>(G, cp, DrawnNoise{noise}, reload, LatticeWeight());
 }
 
 }  // namespace rflbm_dev

@@ -848,6 +848,11 @@ int rflbm_step_path(const rflbm_t* h, int* width) {
   return h->kernel;
 }
 
+int rflbm_step_sites_per_thread(const rflbm_t* h) {
+  if (int e = check_handle(h)) return e;
+  return (h->kernel == RFLBM_KERNEL_TMA && !h->aa && tma_uses_pairs(h->variant)) ? 2 : 1;
+}
+
 int rflbm_testing_expect_extra_bytes(rflbm_t* h, uint32_t bytes) {
   if (int e = check_handle(h)) return e;
   if (bytes > (1u << 20)) return fail(RFLBM_EINVAL, "extra byte count %u above 2^20", bytes);

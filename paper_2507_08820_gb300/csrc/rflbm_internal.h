@@ -170,6 +170,9 @@ cudaError_t launch_step_aa_gather(const StepParams& p, const StepVariant& v, boo
 cudaError_t launch_step_aa_tma(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
                                cudaStream_t stream);
 
+// True when the TMA step of variant v updates two sites per thread (step_tma_pair).
+bool tma_uses_pairs(const StepVariant& v);
+
 // Row-segment width of the TMA step kernels for a box of x edge nx (0: not supported).
 int tma_segment_width(uint32_t nx);
 // Launches one step of a TMA-staged kernel on `stream` (any storage format).

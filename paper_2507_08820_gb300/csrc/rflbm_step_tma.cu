@@ -8,6 +8,7 @@ template <int kW>
 static cudaError_t launch_variant(const TmaMaps& m, const StepParams& p, const StepVariant& v,
                                   cudaStream_t st) {
   constexpr int F = kStoreF32;
+  if (tma_uses_pairs(v)) return launch_tma_pair<F, kW, false>(m, p, st);  // kT = 0
   if (v.model == kModelBgk) {
     if (!v.noise) return launch_tma_segment<F, kW, kModelBgk, false, false, false>(m, p, st);
     return v.phi_rho0 ? launch_tma_segment<F, kW, kModelBgk, true, false, true>(m, p, st)
@@ -23,6 +24,15 @@ static cudaError_t launch_variant(const TmaMaps& m, const StepParams& p, const S
   }
   return v.phi_rho0 ? launch_tma_segment<F, kW, kModelReg, true, false, true>(m, p, st)
                     : launch_tma_segment<F, kW, kModelReg, true, false, false>(m, p, st);
+}
+
+bool tma_uses_pairs(const StepVariant& v) {
+  // two sites per thread where it measured faster: every 16-bit Reg step (issue-bound; the
+  // packed arithmetic saves a fifth of the instructions) and the float32 step without noise.
+  // The float32 fluctuating step stays at one site per thread, where the halved occupancy
+  // of the two-site form costs more than the instructions it saves.
+  if (v.model != kModelReg || v.ghost_neq || (v.noise && v.phi_rho0)) return false;
+  return v.storage != kStoreF32 || !v.noise;
 }
 
 int tma_segment_width(uint32_t nx) {

@@ -1,5 +1,6 @@
 // Step kernels with TMA staging for 16-bit storage (float16, bfloat16), the paper's
-// configuration only (omega_g = 1, local rho in Eq. 10).
+// configuration only (omega_g = 1, local rho in Eq. 10); the Reg-FLBM steps run two sites
+// per thread (step_tma_pair).
 #include "step_tma.cuh"
 
 namespace rflbm_dev {
@@ -11,6 +12,8 @@ static cudaError_t launch_16_w(const TmaMaps& m, const StepParams& p, const Step
   if (v.model == kModelBgk)
     return v.noise ? launch_tma_segment<kStore, kW, kModelBgk, true, false, false>(m, p, st)
                    : launch_tma_segment<kStore, kW, kModelBgk, false, false, false>(m, p, st);
+  if (tma_uses_pairs(v))
+    return v.noise ? launch_tma_pair<kStore, kW, true>(m, p, st) : launch_tma_pair<kStore, kW, false>(m, p, st);
   return v.noise ? launch_tma_segment<kStore, kW, kModelReg, true, false, false>(m, p, st)
                  : launch_tma_segment<kStore, kW, kModelReg, false, false, false>(m, p, st);
 }

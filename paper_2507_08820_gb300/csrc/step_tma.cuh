@@ -141,6 +141,135 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   }
 }
 
+// Output weight of the two-site kernel: the lattice weight times the storage scale of the
+// entry's velocity class (both powers of two apart from the weight, so the product rounds
+// exactly as scaling after the weighting would).
+template <int kStore>
+struct ScaledWeight {
+  const StoreScale& ss;
+  __device__ __forceinline__ float operator()(int a, int b, int c) const {
+    const float wt = float(w1d(a) * w1d(b) * w1d(c));
+    return Storage<kStore>::kScaled ? wt * ss.scale[class_at(a, b, c)] : wt;
+  }
+};
+
+// The same step with two adjacent sites per thread: kW / 2 threads per segment, thread t
+// updates x0 + 2t and x0 + 2t + 1 with the collision in packed f32x2 arithmetic (Reg-FLBM,
+// omega_g = 1, local rho in Eq. 10). Plane c_x = 0 of a site pair is read from shared memory
+// as one aligned pair, the shifted planes c_x = -1, +1 as two elements; the 27 results go
+// out as pairs (16-bit storage: one packed conversion per pair) with the storage scale
+// folded into the lattice weights. Philox calls 0 and 1 of both sites are drawn before the
+// kernel waits for the previous step, the other four inside the collision.
+constexpr int kPairPreDrawn = 2;
+
+template <int kStore, int kW, bool kNoise>
+__global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ CUtensorMap load_map,
+                                                         const __grid_constant__ CUtensorMap store_map,
+                                                         const StepParams p) {
+  using S = Storage<kStore>;
+  using L = TmaLayout<kStore, kW>;
+  using T = typename L::T;
+  constexpr int kH = L::kH;
+  static_assert(kW / 2 >= kGroups, "one lane per source row");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+
+  const int t = threadIdx.x;
+  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t row = blockIdx.x / nseg;
+  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
+
+  grid_launch_dependents();
+  PairNoise<kPairPreDrawn> noise{x0 + 2u * t + p.geo.nx * row, p.step, p.replica, p.key0, p.key1};
+  if (kNoise) noise.draw();
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  grid_dependency_wait();
+
+  T patch_l = T(), patch_r = T();
+  int at_l = -1, at_r = -1;
+  if (t < kGroups) {
+    if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)) + p.test_extra_tx);
+    const int cy = t / 3 - 1, cz = t % 3 - 1;
+    int ys = (int)y - cy, zs = (int)z - cz;
+    ys += ys < 0 ? (int)p.geo.ny : 0;
+    ys -= ys >= (int)p.geo.ny ? (int)p.geo.ny : 0;
+    zs += zs < 0 ? (int)p.geo.nz : 0;
+    zs -= zs >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+    tma_load_4d(sm + t * L::kGroup, &load_map, (int)x0 - kH, ys, zs, 3 * t, &bar);
+    const T* src = static_cast<const T*>(p.src);
+    const int64_t rowoff = (int64_t)p.geo.nx * ((int64_t)ys + (int64_t)p.geo.ny * zs);
+    if (x0 == 0) {
+      patch_l = src[(int64_t)(3 * t + 2) * p.geo.ps + rowoff + (p.geo.nx - 1)];
+      at_l = t * L::kGroup + 2 * L::kSeg + kH - 1;
+    }
+    if (x0 + kW == p.geo.nx) {
+      patch_r = src[(int64_t)(3 * t) * p.geo.ps + rowoff];
+      at_r = t * L::kGroup + kH + kW;
+    }
+  }
+
+  const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
+  if (__syncthreads_or(!ok)) {
+    if (t == 0) atomicOr(p.err, 1);
+    mbar_wait_bounded(&bar, 0, kMaxPolls);
+    return;
+  }
+  if (at_l >= 0) sm[at_l] = patch_l;
+  if (at_r >= 0) sm[at_r] = patch_r;
+  __syncthreads();
+
+  // sites x0 + 2t and x0 + 2t + 1: plane c_x = 0 is read as one aligned pair, the shifted
+  // planes c_x = -+1 as two elements
+  float2 G[3][3][3];
+  const T* mine = sm + kH + 2 * t;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const int gi = 3 * (cy_of(i) + 1) + (cz_of(i) + 1);
+    const T* at = mine + gi * L::kGroup + (cx_of(i) + 1) * L::kSeg - cx_of(i);
+    float2 v = cx_of(i) == 0 ? S::load2(at) : S::load1x2(at);
+    if (S::kScaled) v = kmul(p.ss.inv_scale[class_of(i)], v);
+    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = v;
+  }
+
+  collide_tile<kModelReg, kNoise, false, false>(G, p.cp, noise, KeepTile(),
+                                                    ScaledWeight<kStore>{p.ss});
+
+  __syncthreads();
+  T* out = sm + 2 * t;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) S::store2(out + plane_of(i) * kW, G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1]);
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (t == 0) {
+    tma_store_4d(&store_map, sm, (int)x0, (int)y, (int)z, 0);
+    bulk_commit();
+    bulk_wait_read();
+  }
+}
+
+template <int kStore, int kW, bool kNoise>
+cudaError_t launch_tma_pair(const TmaMaps& m, const StepParams& p, cudaStream_t st) {
+  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.geo.ny * p.geo.nz;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kW / 2);
+  cfg.dynamicSmemBytes = TmaLayout<kStore, kW>::kBytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, step_tma_pair<kStore, kW, kNoise>, *m.load,
+                            *m.store, p);
+}
+
 template <int kStore, int kW, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
 cudaError_t launch_tma_segment(const TmaMaps& m, const StepParams& p, cudaStream_t st) {
   const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.geo.ny * p.geo.nz;

@@ -42,6 +42,15 @@ struct Storage<kStoreF32> {
   static constexpr int kHalo = 4;  // halo elements per side: 16 bytes
   static __device__ __forceinline__ float load(T v, int, const StoreScale&) { return v; }
   static __device__ __forceinline__ T store(float g, int, const StoreScale&) { return g; }
+  // two adjacent elements (8-byte aligned), unscaled
+  static __device__ __forceinline__ float2 load2(const T* p) {
+    return *reinterpret_cast<const float2*>(p);
+  }
+  static __device__ __forceinline__ float2 load1x2(const T* p) { return make_float2(p[0], p[1]); }
+  static __device__ __forceinline__ void store2(T* p, float2 v) {
+    *reinterpret_cast<float2*>(p) = v;
+  }
+  static constexpr bool kScaled = false;
 };
 
 template <>
@@ -54,6 +63,17 @@ struct Storage<kStoreF16> {
   static __device__ __forceinline__ T store(float g, int cls, const StoreScale& s) {
     return __float2half_rn(g * s.scale[cls]);
   }
+  // two adjacent elements (4-byte aligned), converted but not scaled
+  static __device__ __forceinline__ float2 load2(const T* p) {
+    return __half22float2(*reinterpret_cast<const __half2*>(p));
+  }
+  static __device__ __forceinline__ float2 load1x2(const T* p) {
+    return make_float2(__half2float(p[0]), __half2float(p[1]));
+  }
+  static __device__ __forceinline__ void store2(T* p, float2 v) {
+    *reinterpret_cast<__half2*>(p) = __float22half2_rn(v);
+  }
+  static constexpr bool kScaled = true;
 };
 
 template <>
@@ -66,6 +86,16 @@ struct Storage<kStoreBF16> {
   static __device__ __forceinline__ T store(float g, int cls, const StoreScale& s) {
     return __float2bfloat16_rn(g * s.scale[cls]);
   }
+  static __device__ __forceinline__ float2 load2(const T* p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  }
+  static __device__ __forceinline__ float2 load1x2(const T* p) {
+    return make_float2(__bfloat162float(p[0]), __bfloat162float(p[1]));
+  }
+  static __device__ __forceinline__ void store2(T* p, float2 v) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v);
+  }
+  static constexpr bool kScaled = true;
 };
 
 inline size_t storage_bytes(int kind) { return kind == kStoreF32 ? 4 : 2; }

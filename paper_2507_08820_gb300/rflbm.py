@@ -106,6 +106,7 @@ _sig = {
     "rflbm_get_dims": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rflbm_launches_per_step": (C.c_int, [_H]),
     "rflbm_step_path": (C.c_int, [_H, C.POINTER(C.c_int)]),
+    "rflbm_step_sites_per_thread": (C.c_int, [_H]),
     "rflbm_philox4x32_10": (C.c_int, [_P, C.c_uint32, C.c_uint32, _P, C.c_int64]),
     "rflbm_site_normals": (C.c_int, [C.c_uint64, C.c_int64, C.c_uint32, _P, C.c_int64, _P]),
     "rflbm_stats_f32_noalloc": (C.c_int, [_P, C.c_int64, _P, C.POINTER(rflbm_stats_t)]),
@@ -302,6 +303,11 @@ def rflbm_step_path(h):
     w = C.c_int()
     k = _check(lib.rflbm_step_path(h, C.byref(w)))
     return k, w.value
+
+
+def rflbm_step_sites_per_thread(h):
+    """Sites one thread of the step kernel updates (2: the two-site TMA form)."""
+    return _check(lib.rflbm_step_sites_per_thread(h))
 
 
 def rflbm_mode_sums(h):
