@@ -112,6 +112,9 @@ def kernel_source_hash():
 def kernel_name(kind, path, kT, model, storage="f32", pattern="pingpong", sites_per_thread=1):
     noise = "noise" if kT > 0 else "no noise"
     m = "BGK" if model else "Reg"
+    if pattern == "aa" and kind == 2 and sites_per_thread == 2:
+        return (f"step_aa_even_pair+step_aa_odd_pair<{storage}, {path}, {m}, {noise}>",
+                f"step_aa_pair_{storage}_{path}")
     if kind == 2 and sites_per_thread == 2:
         return f"step_tma_pair<{storage}, {path}, {m}, {noise}>", f"step_tma_pair_{storage}_{path}"
     if pattern == "aa":

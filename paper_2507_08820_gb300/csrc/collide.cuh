@@ -125,15 +125,19 @@ struct DrawnNoise {
 // Noise source for two sites per thread (sites site0 and site0 + 1): Philox calls j < kPre
 // drawn beforehand by draw() (raw words, while the tile's copies are in flight), the later
 // calls when the collision needs them.
-template <int kPre>
+template <int kPre, class Key>
 struct PairNoise {
-  uint32_t site0, step, replica, k0, k1;
+  uint32_t site0, step, replica;
+  const Key& key;
   uint4 w[kPre > 0 ? kPre : 1][2];
+  __device__ __forceinline__ uint4 call(uint32_t site, int j) const {
+    return philox4x32_10(make_uint4(site, step, (uint32_t)j, replica), key);
+  }
   __device__ __forceinline__ void draw() {
 #pragma unroll
     for (int j = 0; j < kPre; ++j) {
-      w[j][0] = philox4x32_10(make_uint4(site0, step, (uint32_t)j, replica), k0, k1);
-      w[j][1] = philox4x32_10(make_uint4(site0 + 1u, step, (uint32_t)j, replica), k0, k1);
+      w[j][0] = call(site0, j);
+      w[j][1] = call(site0 + 1u, j);
     }
   }
   __device__ __forceinline__ void operator()(int j, float2 (&r)[2], float2 (&c)[2], float2 (&s)[2]) const {
@@ -142,8 +146,8 @@ struct PairNoise {
       a = w[j < kPre ? j : 0][0];
       b = w[j < kPre ? j : 0][1];
     } else {
-      a = philox4x32_10(make_uint4(site0, step, (uint32_t)j, replica), k0, k1);
-      b = philox4x32_10(make_uint4(site0 + 1u, step, (uint32_t)j, replica), k0, k1);
+      a = call(site0, j);
+      b = call(site0 + 1u, j);
     }
     box_muller(a.x, a.y, r[0].x, c[0].x, s[0].x);
     box_muller(b.x, b.y, r[0].y, c[0].y, s[0].y);

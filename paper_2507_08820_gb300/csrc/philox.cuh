@@ -4,6 +4,8 @@
 // generator of the library's noise contract (rflbm.h).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace rflbm_dev {
@@ -21,6 +23,20 @@ __device__ __forceinline__ void mulhilo(uint32_t a, uint32_t b, uint32_t& hi, ui
   lo = (uint32_t)p;
 }
 
+// The ten round keys of key (k0, k1): round r uses (k0 + r W0, k1 + r W1) mod 2^32. Kernels
+// that take them precomputed from their parameters spend no instructions on the schedule.
+struct PhiloxRoundKeys {
+  uint32_t k0[10], k1[10];
+};
+inline PhiloxRoundKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+  PhiloxRoundKeys rk;
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0 + (uint32_t)r * kPhiloxW0;
+    rk.k1[r] = k1 + (uint32_t)r * kPhiloxW1;
+  }
+  return rk;
+}
+
 // Ten rounds of the Philox4x32 bijection on counter c under key (k0, k1).
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -31,6 +47,26 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     k0 += kPhiloxW0;
     k1 += kPhiloxW1;
+  }
+  return c;
+}
+
+// Key (k0, k1) with its schedule computed in the rounds.
+struct PhiloxKey {
+  uint32_t k0, k1;
+};
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKey& k) {
+  return philox4x32_10(c, k.k0, k.k1);
+}
+
+// The same with the round keys given.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxRoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0, lo0, hi1, lo1;
+    mulhilo(kPhiloxM0, c.x, hi0, lo0);
+    mulhilo(kPhiloxM1, c.z, hi1, lo1);
+    c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
   }
   return c;
 }
@@ -94,6 +130,18 @@ __device__ __forceinline__ void site_noise_part(uint32_t site, uint32_t step, ui
 #pragma unroll
   for (int j = j0; j < j1; ++j) {
     const uint4 w = philox4x32_10(make_uint4(site, step, (uint32_t)j, replica), k0, k1);
+    box_muller(w.x, w.y, out.r[2 * j], out.c[2 * j], out.s[2 * j]);
+    box_muller(w.z, w.w, out.r[2 * j + 1], out.c[2 * j + 1], out.s[2 * j + 1]);
+  }
+}
+
+// The same with the round keys given.
+template <int j0, int j1>
+__device__ __forceinline__ void site_noise_part(uint32_t site, uint32_t step, uint32_t replica,
+                                                const PhiloxRoundKeys& rk, SiteNoise& out) {
+#pragma unroll
+  for (int j = j0; j < j1; ++j) {
+    const uint4 w = philox4x32_10(make_uint4(site, step, (uint32_t)j, replica), rk);
     box_muller(w.x, w.y, out.r[2 * j], out.c[2 * j], out.s[2 * j]);
     box_muller(w.z, w.w, out.r[2 * j + 1], out.c[2 * j + 1], out.s[2 * j + 1]);
   }

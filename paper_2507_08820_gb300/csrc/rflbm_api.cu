@@ -509,6 +509,7 @@ int rflbm_step(rflbm_t* h, int64_t n) {
   p.ss = h->ss;
   p.key0 = (uint32_t)(h->cfg.seed & 0xffffffffu);
   p.key1 = (uint32_t)(h->cfg.seed >> 32);
+  p.rk = philox_round_keys(p.key0, p.key1);
   p.replica = h->cfg.replica;
   p.err = h->err;
   p.test_extra_tx = h->test_extra_tx;
@@ -850,7 +851,7 @@ int rflbm_step_path(const rflbm_t* h, int* width) {
 
 int rflbm_step_sites_per_thread(const rflbm_t* h) {
   if (int e = check_handle(h)) return e;
-  return (h->kernel == RFLBM_KERNEL_TMA && !h->aa && tma_uses_pairs(h->variant)) ? 2 : 1;
+  return (h->kernel == RFLBM_KERNEL_TMA && tma_uses_pairs(h->variant)) ? 2 : 1;
 }
 
 int rflbm_testing_expect_extra_bytes(rflbm_t* h, uint32_t bytes) {

@@ -128,6 +128,7 @@ struct StepParams {
   void* dst;
   int* err;  // device error flag (bit 0: a bounded wait expired)
   uint32_t key0, key1, step, replica;
+  PhiloxRoundKeys rk;  // the round keys of (key0, key1)
   uint32_t test_extra_tx;  // testing hook: bytes a TMA step expects beyond its copies (0)
 };
 

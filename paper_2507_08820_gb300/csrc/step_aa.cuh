@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   grid_launch_dependents();
   const uint32_t s = x0 + t + p.geo.nx * row;
   SiteNoise noise;
-  if (kNoise) site_noise_part<0, 3>(s, p.step, p.replica, p.key0, p.key1, noise);
+  if (kNoise) site_noise_part<0, 3>(s, p.step, p.replica, p.rk, noise);
 
   if (t == 0) {
     mbar_init(&bar, 1);
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
     tma_load_4d(sm, &map, (int)x0, (int)y, (int)z, 0, &bar);
   }
 
-  if (kNoise) site_noise_part<3, 6>(s, p.step, p.replica, p.key0, p.key1, noise);
+  if (kNoise) site_noise_part<3, 6>(s, p.step, p.replica, p.rk, noise);
 
   const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
   if (__syncthreads_or(!ok)) {
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   const uint32_t x = x0 + t;
   const uint32_t s = x + p.geo.nx * row;
   SiteNoise noise;
-  if (kNoise) site_noise_part<0, 3>(s, p.step, p.replica, p.key0, p.key1, noise);
+  if (kNoise) site_noise_part<0, 3>(s, p.step, p.replica, p.rk, noise);
 
   if (t == 0) {
     mbar_init(&bar, 1);
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
     }
   }
 
-  if (kNoise) site_noise_part<3, 6>(s, p.step, p.replica, p.key0, p.key1, noise);
+  if (kNoise) site_noise_part<3, 6>(s, p.step, p.replica, p.rk, noise);
   const PullDeltas d = deltas_at(x, y, z, p.geo);
 
   const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
@@ -249,6 +249,224 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
         S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
 }
 
+// ---- two sites per thread (x0 + 2t, x0 + 2t + 1), the collision in packed f32x2
+// arithmetic, Reg-FLBM: the same copies, waits and addresses as the one-site forms above;
+// the storage scale is folded into the lattice weights as in step_tma_pair.
+
+template <int kStore, int kW, bool kNoise>
+__global__ void __launch_bounds__(kW / 2) step_aa_even_pair(const __grid_constant__ CUtensorMap map,
+                                                            const StepParams p) {
+  using S = Storage<kStore>;
+  using T = typename S::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+
+  const int t = threadIdx.x;
+  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t row = blockIdx.x / nseg;
+  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
+
+  grid_launch_dependents();
+  const PhiloxKey key{p.key0, p.key1};
+  PairNoise<kPairPreDrawn, PhiloxKey> noise{x0 + 2u * t + p.geo.nx * row, p.step, p.replica, key};
+  if (kNoise) noise.draw();
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  grid_dependency_wait();
+
+  if (t == 0) {
+    mbar_arrive_expect_tx(&bar, (uint32_t)AaEvenLayout<kStore, kW>::kTileBytes);
+    tma_load_4d(sm, &map, (int)x0, (int)y, (int)z, 0, &bar);
+  }
+  const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
+  if (__syncthreads_or(!ok)) {
+    if (t == 0) atomicOr(p.err, 1);
+    mbar_wait_bounded(&bar, 0, kMaxPolls);
+    return;
+  }
+
+  float2 G[3][3][3];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    float2 v = S::load2(sm + plane_of(i) * kW + 2 * t);
+    if (S::kScaled) v = kmul(p.ss.inv_scale[class_of(i)], v);
+    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = v;
+  }
+  collide_tile<kModelReg, kNoise, false, false>(G, p.cp, noise, KeepTile(), ScaledWeight<kStore>{p.ss});
+
+  __syncthreads();  // all inputs are read: the tile can take the outputs
+#pragma unroll
+  for (int i = 0; i < kQ; ++i)
+    S::store2(sm + (kQ - 1 - plane_of(i)) * kW + 2 * t, G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1]);
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (t == 0) {
+    tma_store_4d(&map, sm, (int)x0, (int)y, (int)z, 0);
+    bulk_commit();
+    bulk_wait_read();
+  }
+}
+
+template <int kStore, int kW, bool kNoise, bool kFullRow>
+__global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant__ CUtensorMap load_map,
+                                                           const __grid_constant__ CUtensorMap row_map,
+                                                           const StepParams p) {
+  using S = Storage<kStore>;
+  using L = TmaLayout<kStore, kW>;
+  using T = typename L::T;
+  constexpr int kH = L::kH;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+
+  const int t = threadIdx.x;
+  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t row = blockIdx.x / nseg;
+  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
+
+  grid_launch_dependents();
+  const uint32_t x = x0 + 2u * t;  // and x + 1
+  const uint32_t s = x + p.geo.nx * row;
+  const PhiloxKey key{p.key0, p.key1};
+  PairNoise<kPairPreDrawn, PhiloxKey> noise{s, p.step, p.replica, key};
+  if (kNoise) noise.draw();
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  grid_dependency_wait();
+
+  // the loads of the one-site odd form: mirrored group 8 - g of source row g
+  T* const buf = static_cast<T*>(p.dst);
+  T patch_l = T(), patch_r = T();
+  int at_l = -1, at_r = -1;
+  if (t < kGroups) {
+    if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)));
+    const int cy = t / 3 - 1, cz = t % 3 - 1;
+    int ys = (int)y - cy, zs = (int)z - cz;
+    ys += ys < 0 ? (int)p.geo.ny : 0;
+    ys -= ys >= (int)p.geo.ny ? (int)p.geo.ny : 0;
+    zs += zs < 0 ? (int)p.geo.nz : 0;
+    zs -= zs >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+    const int mirror = kGroups - 1 - t;
+    tma_load_4d(sm + t * L::kGroup, &load_map, (int)x0 - kH, ys, zs, 3 * mirror, &bar);
+    const int64_t rowoff = (int64_t)p.geo.nx * ((int64_t)ys + (int64_t)p.geo.ny * zs);
+    if (x0 == 0) {
+      patch_l = buf[(int64_t)(3 * mirror) * p.geo.ps + rowoff + (p.geo.nx - 1)];
+      at_l = t * L::kGroup + kH - 1;
+    }
+    if (x0 + kW == p.geo.nx) {
+      patch_r = buf[(int64_t)(3 * mirror + 2) * p.geo.ps + rowoff];
+      at_r = t * L::kGroup + 2 * L::kSeg + kH + kW;
+    }
+  }
+  const PullDeltas d = deltas_at(x, y, z, p.geo);
+
+  const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
+  if (__syncthreads_or(!ok)) {
+    if (t == 0) atomicOr(p.err, 1);
+    mbar_wait_bounded(&bar, 0, kMaxPolls);
+    return;
+  }
+  if (at_l >= 0) sm[at_l] = patch_l;
+  if (at_r >= 0) sm[at_r] = patch_r;
+  __syncthreads();
+
+  float2 G[3][3][3];
+  const T* mine = sm + kH + 2 * t;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const int gi = 3 * (cy_of(i) + 1) + (cz_of(i) + 1);
+    const T* at = mine + gi * L::kGroup + (1 - cx_of(i)) * L::kSeg - cx_of(i);
+    float2 v = cx_of(i) == 0 ? S::load2(at) : S::load1x2(at);
+    if (S::kScaled) v = kmul(p.ss.inv_scale[class_of(i)], v);
+    G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = v;
+  }
+  collide_tile<kModelReg, kNoise, false, false>(G, p.cp, noise, KeepTile(), ScaledWeight<kStore>{p.ss});
+
+  if (kFullRow) {
+    using O = AaRowOut<kStore, kW>;
+    __syncthreads();  // all inputs are read: the tile can take the outputs
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const int g = 3 * (cy_of(i) + 1) + (cz_of(i) + 1);
+      T* const prow = sm + g * O::kGroup + (cx_of(i) + 1) * kW;
+      const float2 v = G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1];
+      if (cx_of(i) == 0) {
+        S::store2(prow + 2 * t, v);
+      } else {
+        // positions x + c_x and x + 1 + c_x, wrapped within the row
+        const int p0 = 2 * t + cx_of(i), p1 = p0 + 1;
+        prow[p0 < 0 ? p0 + kW : p0] = S::pack(v.x);
+        prow[p1 >= kW ? p1 - kW : p1] = S::pack(v.y);
+      }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t < kGroups) {
+      const int cy = t / 3 - 1, cz = t % 3 - 1;
+      int yd = (int)y + cy, zd = (int)z + cz;
+      yd += yd < 0 ? (int)p.geo.ny : 0;
+      yd -= yd >= (int)p.geo.ny ? (int)p.geo.ny : 0;
+      zd += zd < 0 ? (int)p.geo.nz : 0;
+      zd -= zd >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+      tma_store_4d(&row_map, sm + t * O::kGroup, 0, yd, zd, 3 * t);
+      bulk_commit();
+      bulk_wait_read();
+    }
+    return;
+  }
+
+  // population i of x and x + 1 goes to plane P(i) at x + c_i and x + 1 + c_i: the rows
+  // (y, z) shifts are shared; along x, x + 1 never wraps from x (x is even, nx is even),
+  // x - 1 wraps when x = 0, and x + 2 wraps when x + 2 = nx
+  T* const dst = buf + s;
+  const int32_t dxb_plus = (x + 2u == p.geo.nx) ? 1 - (int32_t)p.geo.nx : 1;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const float2 v = G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1];
+    const int64_t base = plane_of(i) * p.geo.ps + d.DY[1 - cy_of(i)] + d.DZ[1 - cz_of(i)];
+    if (cx_of(i) == 0) {
+      S::store2(dst + base, v);
+    } else if (cx_of(i) > 0) {
+      dst[base + 1] = S::pack(v.x);
+      dst[base + 1 + dxb_plus] = S::pack(v.y);
+    } else {
+      dst[base + d.DX[2]] = S::pack(v.x);
+      dst[base] = S::pack(v.y);  // x + 1 - 1
+    }
+  }
+}
+
+template <int kStore, int kW, bool kNoise>
+cudaError_t launch_aa_pair(const TmaMaps& m, const StepParams& p, bool odd, cudaStream_t st) {
+  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.geo.ny * p.geo.nz;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kW / 2);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (odd) {
+    cfg.dynamicSmemBytes = TmaLayout<kStore, kW>::kBytes;
+    if (m.row3 && p.geo.nx == (uint32_t)kW)
+      return cudaLaunchKernelEx(&cfg, step_aa_odd_pair<kStore, kW, kNoise, true>, *m.load, *m.row3, p);
+    return cudaLaunchKernelEx(&cfg, step_aa_odd_pair<kStore, kW, kNoise, false>, *m.load, *m.load, p);
+  }
+  cfg.dynamicSmemBytes = AaEvenLayout<kStore, kW>::kBytes;
+  return cudaLaunchKernelEx(&cfg, step_aa_even_pair<kStore, kW, kNoise>, *m.store, p);
+}
+
 template <int kStore, int kW, int kModel, bool kNoise>
 cudaError_t launch_aa_segment(const TmaMaps& m, const StepParams& p, bool odd, cudaStream_t st) {
   const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.geo.ny * p.geo.nz;
@@ -275,6 +493,8 @@ template <int kStore, int kW>
 cudaError_t launch_aa_variant(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
                               cudaStream_t st) {
   if (v.ghost_neq || v.phi_rho0) return cudaErrorInvalidValue;
+  if (tma_uses_pairs(v))
+    return v.noise ? launch_aa_pair<kStore, kW, true>(m, p, odd, st) : launch_aa_pair<kStore, kW, false>(m, p, odd, st);
   if (v.model == kModelBgk)
     return v.noise ? launch_aa_segment<kStore, kW, kModelBgk, true>(m, p, odd, st)
                    : launch_aa_segment<kStore, kW, kModelBgk, false>(m, p, odd, st);

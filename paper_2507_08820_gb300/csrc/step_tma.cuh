@@ -11,7 +11,8 @@
 // segment touches the periodic x edge the wrapped neighbour is fetched with a plain load.
 // The first half of the 24 normals is drawn before the kernel waits for the previous step
 // (programmatic dependent launch lets this grid start while the previous one drains), the
-// second half while the copies are in flight. Each thread then reads its 27 values from
+// second half while the copies are in flight, with the Philox round keys precomputed in the
+// launch parameters. Each thread then reads its 27 values from
 // shared memory at fixed offsets (x - c_x within its group row), collides in registers in
 // float32 and writes its 27 results into a dense [plane][kW] tile, which lane 0 stores
 // with one TMA copy of all 27 planes.
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   grid_launch_dependents();
   const uint32_t s = x0 + t + p.geo.nx * row;
   SiteNoise noise;
-  if (kNoise) site_noise_part<0, 3>(s, p.step, p.replica, p.key0, p.key1, noise);
+  if (kNoise) site_noise_part<0, 3>(s, p.step, p.replica, p.rk, noise);
 
   if (t == 0) {
     mbar_init(&bar, 1);
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
     }
   }
 
-  if (kNoise) site_noise_part<3, 6>(s, p.step, p.replica, p.key0, p.key1, noise);
+  if (kNoise) site_noise_part<3, 6>(s, p.step, p.replica, p.rk, noise);
 
   const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
   if (__syncthreads_or(!ok)) {
@@ -182,7 +183,9 @@ __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ 
   const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
 
   grid_launch_dependents();
-  PairNoise<kPairPreDrawn> noise{x0 + 2u * t + p.geo.nx * row, p.step, p.replica, p.key0, p.key1};
+  // (round keys computed in the rounds: from the parameter bank they measured 5 % slower here)
+  const PhiloxKey key{p.key0, p.key1};
+  PairNoise<kPairPreDrawn, PhiloxKey> noise{x0 + 2u * t + p.geo.nx * row, p.step, p.replica, key};
   if (kNoise) noise.draw();
   if (t == 0) {
     mbar_init(&bar, 1);

@@ -50,6 +50,7 @@ struct Storage<kStoreF32> {
   static __device__ __forceinline__ void store2(T* p, float2 v) {
     *reinterpret_cast<float2*>(p) = v;
   }
+  static __device__ __forceinline__ T pack(float v) { return v; }  // already scaled
   static constexpr bool kScaled = false;
 };
 
@@ -63,7 +64,8 @@ struct Storage<kStoreF16> {
   static __device__ __forceinline__ T store(float g, int cls, const StoreScale& s) {
     return __float2half_rn(g * s.scale[cls]);
   }
-  // two adjacent elements (4-byte aligned), converted but not scaled
+  // two adjacent elements (4-byte aligned), converted but not scaled; store2 and pack
+  // convert values whose scale the caller has applied
   static __device__ __forceinline__ float2 load2(const T* p) {
     return __half22float2(*reinterpret_cast<const __half2*>(p));
   }
@@ -73,6 +75,7 @@ struct Storage<kStoreF16> {
   static __device__ __forceinline__ void store2(T* p, float2 v) {
     *reinterpret_cast<__half2*>(p) = __float22half2_rn(v);
   }
+  static __device__ __forceinline__ T pack(float v) { return __float2half_rn(v); }
   static constexpr bool kScaled = true;
 };
 
@@ -95,6 +98,7 @@ struct Storage<kStoreBF16> {
   static __device__ __forceinline__ void store2(T* p, float2 v) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v);
   }
+  static __device__ __forceinline__ T pack(float v) { return __float2bfloat16_rn(v); }
   static constexpr bool kScaled = true;
 };
 

@@ -1,6 +1,7 @@
-"""The two-site form of the TMA step kernel (two adjacent sites per thread, packed f32x2
-arithmetic): where it runs, and that it computes every site bit for bit like the one-site
-kernels (the general gather kernel here; the AA kernels in test_gpu_aa.py)."""
+"""The two-site form of the TMA step kernels (two adjacent sites per thread, packed f32x2
+arithmetic), ping-pong and AA: where it runs, and that it computes every site bit for bit
+like the one-site general gather kernels (and, in test_gpu_aa.py, like the one-site AA
+kernels of the float32 fluctuating step)."""
 import numpy as np
 import pytest
 
@@ -31,8 +32,10 @@ def _state(shape, seed=21):
     (dict(kT=1e-4), 1), (dict(kT=0.0), 2), (dict(kT=1e-4, storage=1), 2), (dict(kT=0.0, storage=1), 2),
     (dict(kT=1e-4, storage=2), 2), (dict(kT=0.0, storage=2), 2), (dict(kT=1e-4, model=1), 1),
     (dict(kT=0.0, model=1, storage=1), 1), (dict(kT=0.0, omega_g=0.7), 1), (dict(kT=1e-4, phi_rho=1), 1),
-    (dict(kT=0.0, phi_rho=1), 2), (dict(kT=0.0, pattern=1), 1), (dict(kT=1e-4, storage=1, pattern=1), 1),
+    (dict(kT=0.0, phi_rho=1), 2), (dict(kT=0.0, pattern=1), 2), (dict(kT=1e-4, storage=1, pattern=1), 2),
+    (dict(kT=1e-4, pattern=1), 1), (dict(kT=1e-4, model=1, storage=2, pattern=1), 1),
     (dict(kT=0.0, kernel=1), 1), (dict(kT=1e-4, storage=1, kernel=1), 1),
+    (dict(kT=0.0, kernel=1, pattern=1), 1),
 ])
 def test_sites_per_thread(R, kw, pairs):
     box = R.Box(128, 3, 2, tau=0.8, **kw)
@@ -46,16 +49,19 @@ SHAPES = [(32, 5, 4), (64, 6, 5), (96, 4, 3), (128, 3, 3), (192, 3, 2), (256, 3,
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("kw", [dict(kT=0.0), dict(kT=1e-4, storage=1), dict(kT=0.0, storage=1),
                                 dict(kT=3e-4, storage=2), dict(kT=0.0, storage=2)])
-def test_two_site_form_matches_the_gather_kernel_bitwise(R, shape, kw):
+@pytest.mark.parametrize("pattern", [0, 1])
+def test_two_site_form_matches_the_gather_kernel_bitwise(R, shape, kw, pattern):
+    """Ping-pong and AA (whose odd steps store whole rows where a segment is a row, else
+    straight to the neighbours), after 1, 2, 4 and 7 steps (both AA parities)."""
     f0 = _state(shape, seed=7)
     out = []
     for kernel in (R.RFLBM_KERNEL_TMA, R.RFLBM_KERNEL_GATHER):
-        box = R.Box(*shape, tau=0.7, seed=3, kernel=kernel, **kw)
+        box = R.Box(*shape, tau=0.7, seed=3, kernel=kernel, pattern=pattern, **kw)
         assert R.rflbm_step_sites_per_thread(box.h) == (2 if kernel == R.RFLBM_KERNEL_TMA else 1)
         R.rflbm_set_populations(box.h, f0)
         R.rflbm_set_step(box.h, 5)
         snaps = []
-        for steps in (1, 2, 4):
+        for steps in (1, 1, 2, 3):
             R.rflbm_step(box.h, steps)
             f = np.empty((27, box.n), np.float32)
             R.rflbm_get_populations_f32(box.h, f)
