@@ -239,10 +239,12 @@ int rflbm_launches_per_step(const rflbm_t* h);
  * NULL, receives the row-segment width of the TMA kernels (0 for the general kernel). */
 int rflbm_step_path(const rflbm_t* h, int* width);
 
-/* Sites one thread of the step kernel updates: 2 where the TMA kernels run their two-site
- * form (either streaming pattern; Reg-FLBM with 16-bit storage, and float32 without noise:
- * packed f32x2 arithmetic, one instruction for both sites), else 1. Both forms compute every site bit
- * for bit alike; negative rflbm_status on an invalid handle. */
+/* Sites one thread of the kernel of the next step (rflbm_step(h, 1)) updates: 2 where the
+ * TMA kernels run their two-site form (packed f32x2 arithmetic, one instruction for both
+ * sites): Reg-FLBM with 16-bit storage and float32 without noise in either streaming
+ * pattern, and the odd AA steps of float32 Reg-FLBM whose rows span several segments; else
+ * 1. Both forms compute every site bit for bit alike; negative rflbm_status on an invalid
+ * handle. */
 int rflbm_step_sites_per_thread(const rflbm_t* h);
 
 /* Equilibrium-statistics diagnostics of the current (pre-collision) state, FP64

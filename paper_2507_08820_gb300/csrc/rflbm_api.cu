@@ -851,7 +851,9 @@ int rflbm_step_path(const rflbm_t* h, int* width) {
 
 int rflbm_step_sites_per_thread(const rflbm_t* h) {
   if (int e = check_handle(h)) return e;
-  return (h->kernel == RFLBM_KERNEL_TMA && tma_uses_pairs(h->variant)) ? 2 : 1;
+  if (h->kernel != RFLBM_KERNEL_TMA) return 1;
+  if (h->aa) return aa_uses_pairs(h->variant, h->phase != 0, h->has_row_map) ? 2 : 1;
+  return tma_uses_pairs(h->variant) ? 2 : 1;
 }
 
 int rflbm_testing_expect_extra_bytes(rflbm_t* h, uint32_t bytes) {

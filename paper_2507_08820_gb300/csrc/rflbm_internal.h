@@ -171,8 +171,12 @@ cudaError_t launch_step_aa_gather(const StepParams& p, const StepVariant& v, boo
 cudaError_t launch_step_aa_tma(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
                                cudaStream_t stream);
 
-// True when the TMA step of variant v updates two sites per thread (step_tma_pair).
+// True when the TMA step of variant v updates two sites per thread (step_tma_pair; the AA
+// steps of such variants likewise).
 bool tma_uses_pairs(const StepVariant& v);
+// True when an AA step (odd: from the flipped view; full_row: its segments are whole rows,
+// stored as rotated rows) runs in the two-site form.
+bool aa_uses_pairs(const StepVariant& v, bool odd, bool full_row);
 
 // Row-segment width of the TMA step kernels for a box of x edge nx (0: not supported).
 int tma_segment_width(uint32_t nx);

@@ -35,6 +35,16 @@ bool tma_uses_pairs(const StepVariant& v) {
   return v.storage != kStoreF32 || !v.noise;
 }
 
+bool aa_uses_pairs(const StepVariant& v, bool odd, bool full_row) {
+  if (tma_uses_pairs(v)) return true;
+  // float32 fluctuating odd steps whose stores go straight to the neighbours (rows of
+  // several segments): the two sites of a thread share the address arithmetic of the 27
+  // stores, which outweighs the lower occupancy (256^3: 94.9 % against 87.9 %). Where the
+  // odd step stores rotated whole rows the one-site form stays faster (128^3: 94.3 % against
+  // 90.0 % for the pair).
+  return odd && !full_row && v.model == kModelReg && !v.ghost_neq && !v.phi_rho0 && v.noise;
+}
+
 int tma_segment_width(uint32_t nx) {
   // the widest segment that tiles the row: wider CTAs amortise their fixed costs (128 sites
   // measured 94 %, 64 sites 87 %, 32 sites 85 % of the copy bandwidth at 128^3)

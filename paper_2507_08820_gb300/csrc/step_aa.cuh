@@ -493,7 +493,7 @@ template <int kStore, int kW>
 cudaError_t launch_aa_variant(const TmaMaps& m, const StepParams& p, const StepVariant& v, bool odd,
                               cudaStream_t st) {
   if (v.ghost_neq || v.phi_rho0) return cudaErrorInvalidValue;
-  if (tma_uses_pairs(v))
+  if (aa_uses_pairs(v, odd, m.row3 && p.geo.nx == (uint32_t)kW))
     return v.noise ? launch_aa_pair<kStore, kW, true>(m, p, odd, st) : launch_aa_pair<kStore, kW, false>(m, p, odd, st);
   if (v.model == kModelBgk)
     return v.noise ? launch_aa_segment<kStore, kW, kModelBgk, true>(m, p, odd, st)

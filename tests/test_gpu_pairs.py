@@ -43,12 +43,27 @@ def test_sites_per_thread(R, kw, pairs):
     box.close()
 
 
+@pytest.mark.parametrize("nx,odd_pairs", [(128, 1), (256, 2)])
+def test_float32_fluctuating_aa_odd_steps(R, nx, odd_pairs):
+    """The odd AA steps of the float32 fluctuating step run two sites per thread where
+    they store straight to the neighbours (rows of several segments), one where a segment
+    is a whole row; the even steps one."""
+    box = R.Box(nx, 3, 2, tau=0.8, kT=1e-4, pattern=1)
+    R.rflbm_init_rest(box.h)
+    assert R.rflbm_step_sites_per_thread(box.h) == 1
+    R.rflbm_step(box.h, 1)
+    assert R.rflbm_step_sites_per_thread(box.h) == odd_pairs
+    R.rflbm_step(box.h, 1)
+    assert R.rflbm_step_sites_per_thread(box.h) == 1
+    box.close()
+
+
 SHAPES = [(32, 5, 4), (64, 6, 5), (96, 4, 3), (128, 3, 3), (192, 3, 2), (256, 3, 2), (160, 3, 2)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("kw", [dict(kT=0.0), dict(kT=1e-4, storage=1), dict(kT=0.0, storage=1),
-                                dict(kT=3e-4, storage=2), dict(kT=0.0, storage=2)])
+                                dict(kT=3e-4, storage=2), dict(kT=0.0, storage=2), dict(kT=1e-4)])
 @pytest.mark.parametrize("pattern", [0, 1])
 def test_two_site_form_matches_the_gather_kernel_bitwise(R, shape, kw, pattern):
     """Ping-pong and AA (whose odd steps store whole rows where a segment is a row, else
@@ -57,7 +72,8 @@ def test_two_site_form_matches_the_gather_kernel_bitwise(R, shape, kw, pattern):
     out = []
     for kernel in (R.RFLBM_KERNEL_TMA, R.RFLBM_KERNEL_GATHER):
         box = R.Box(*shape, tau=0.7, seed=3, kernel=kernel, pattern=pattern, **kw)
-        assert R.rflbm_step_sites_per_thread(box.h) == (2 if kernel == R.RFLBM_KERNEL_TMA else 1)
+        if kernel == R.RFLBM_KERNEL_GATHER:
+            assert R.rflbm_step_sites_per_thread(box.h) == 1
         R.rflbm_set_populations(box.h, f0)
         R.rflbm_set_step(box.h, 5)
         snaps = []
