@@ -336,7 +336,8 @@ def ensemble_arm(args):
                    "parallelism": "replicas"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs of {peak_kind}",
-                     "kernel": f"k_batch_step<{args.storage}, {tile}, rows>",
+                     "kernel": (f"k_batch_step<{args.storage}, {tile}, rows>" if args.storage == "f32"
+                                else f"k_batch_rows_pair<{args.storage}, {tile}>"),
                      "algorithmic_bytes_per_launch": bps * sites},
         "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks,
     }

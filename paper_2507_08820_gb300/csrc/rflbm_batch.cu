@@ -13,6 +13,7 @@
 //    the y edge are copied in afterwards and x wraps by index. The 27 outputs go through
 //    shared memory and leave as one TMA store of the (nx, R, 27) box.
 //  - sites: otherwise, kTile consecutive sites, each gathering its 27 populations.
+// Rows tiles of 16-bit ensembles run two sites per thread (k_batch_rows_pair).
 // Each replica's arithmetic is the single-box kernels' (same tile order, same Philox key =
 // the replica's seed, replica word 0), so a replica reproduces its single-box run bit for
 // bit.
@@ -204,10 +205,142 @@ __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
   }
 }
 
+// Rows tiles with two sites per thread (16-bit storage): kTile sites, kTile / 2 threads,
+// thread t updating sites 2t and 2t + 1 of the tile (one row: nx is even) with the packed
+// collision of the single-box two-site kernels, the storage scale folded into the weights.
+template <int kStore, int kTile>
+__global__ void __launch_bounds__(kTile / 2)
+    k_batch_rows_pair(const ReplicaDev* __restrict__ reps, const int* __restrict__ tile_rep,
+                      const unsigned long long* step0_ptr, uint32_t k, int* err) {
+  using S = Storage<kStore>;
+  using T = typename S::T;
+  constexpr int kGroup = (int)(batch_group_bytes(kTile, sizeof(T)) / sizeof(T));
+  constexpr int rn = kTile;
+  constexpr int kThreads = kTile / 2;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(16) ReplicaDev rep;
+  T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
+  const int tid = threadIdx.x;
+  const int64_t j = blockIdx.x;
+  const int r = __ldg(tile_rep + j);
+  {
+    const int* from = reinterpret_cast<const int*>(reps + r);
+    int* to = reinterpret_cast<int*>(&rep);
+    for (int w = tid; w < (int)(sizeof(ReplicaDev) / sizeof(int)); w += kThreads) to[w] = __ldg(from + w);
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  grid_launch_dependents();
+  const uint32_t step = (uint32_t)*step0_ptr + k;
+  const int parity = (rep.cur + (int)(k & 1u)) & 1;
+  const T* src = static_cast<const T*>(rep.buf[parity]);
+  const uint32_t li = (uint32_t)(j - rep.tile_begin);
+
+  const uint32_t R = rep.rows;
+  const uint32_t nx = rep.geo.nx, ny = rep.geo.ny, nz = rep.geo.nz;
+  const uint32_t z = li / rep.yblocks;
+  const uint32_t y0 = (li - z * rep.yblocks) * R;
+  const uint32_t nrows = min(R, ny - y0);
+  const uint32_t q = 2u * (uint32_t)tid;  // first site of the pair in the tile
+  const uint32_t row = fastdiv(q, rep.geo.div_nx);
+  const uint32_t x = q - row * nx;  // even
+  const bool active = row < nrows;
+  const PhiloxKey key{rep.key0, rep.key1};
+  PairNoise<kPairPreDrawn, PhiloxKey> noise{x + nx * ((y0 + row) + ny * z), step, 0u, key};
+  if (rep.noise && active) noise.draw();
+
+  grid_dependency_wait();
+  if (tid < kBatchGroups) {
+    if (tid == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kBatchGroups * 3 * rn * sizeof(T)));
+    const int cy = tid / 3 - 1, cz = tid % 3 - 1;
+    int zs = (int)z - cz;
+    zs += zs < 0 ? (int)nz : 0;
+    zs -= zs >= (int)nz ? (int)nz : 0;
+    tma_load_4d(sm + tid * kGroup, rep.maps + 2 * parity, 0, (int)y0 - cy, zs, 3 * tid, &bar);
+  }
+  const bool ok = mbar_wait_bounded(&bar, 0, kBatchTmaPolls);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicOr(err, 1);
+    mbar_wait_bounded(&bar, 0, kBatchTmaPolls);
+    return;
+  }
+  // rows that wrap around the y edge, as in k_batch_step (x strided over the threads)
+  if (y0 == 0 || y0 + nrows == ny) {
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+      if (side == 0 ? y0 != 0 : y0 + nrows != ny) continue;
+      const int64_t ys = side == 0 ? (int64_t)ny - 1 : 0;
+      const int brow = side == 0 ? 0 : (int)nrows - 1;
+#pragma unroll 1
+      for (int xx = tid; xx < (int)nx; xx += kThreads) {
+#pragma unroll
+        for (int gi = 0; gi < 3; ++gi) {
+          const int g = side == 0 ? 6 + gi : gi;
+          int zs = (int)z - (gi - 1);
+          zs += zs < 0 ? (int)nz : 0;
+          zs -= zs >= (int)nz ? (int)nz : 0;
+          const T* from = src + (int64_t)3 * g * rep.geo.ps + (int64_t)nx * (ys + (int64_t)ny * zs) + xx;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) sm[g * kGroup + a * rn + brow * (int)nx + xx] = from[(int64_t)a * rep.geo.ps];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float2 G[3][3][3];
+  if (active) {
+    // plane a of a group holds the value at x - c_x: x + 1, x, x - 1 (periodic in x); for
+    // the pair (x, x + 1): (x + 1, x + 2), (x, x + 1), (x - 1, x)
+    const int xm = x == 0 ? (int)nx - 1 : (int)x - 1, xp2 = x + 2 == nx ? 0 : (int)x + 2;
+    const T* const base = sm + row * nx;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T* pl = base + (3 * b + c) * kGroup + a * rn;
+          float2 v = a == 1 ? S::load2(pl + x)
+                            : (a == 0 ? make_float2(S::to_float(pl[x + 1]), S::to_float(pl[xp2]))
+                                      : make_float2(S::to_float(pl[xm]), S::to_float(pl[x])));
+          if (S::kScaled) v = kmul(rep.ss.inv_scale[class_at(a, b, c)], v);
+          G[a][b][c] = v;
+        }
+    if (rep.noise)
+      collide_tile<kModelReg, true, false, false>(G, rep.cp, noise, KeepTile(), ScaledWeight<kStore>{rep.ss});
+    else
+      collide_tile<kModelReg, false, false, false>(G, rep.cp, noise, KeepTile(), ScaledWeight<kStore>{rep.ss});
+  }
+  __syncthreads();
+  if (active) {
+    T* out = sm + row * nx + x;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) S::store2(out + plane_of(i) * rn, G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1]);
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    tma_store_4d(rep.maps + 2 * (parity ^ 1) + 1, sm, 0, (int)y0, (int)z, 0);
+    bulk_commit();
+    bulk_wait_read();
+  }
+}
+
+// Rows tiles of 16-bit ensembles run two sites per thread (issue-bound, like the single-box
+// 16-bit steps); float32 ensembles one.
+template <int kStore>
+constexpr bool batch_rows_pairs() { return kStore != kStoreF32; }
+
 template <int kStore, int kTile>
 static cudaError_t set_smem_t() {
   const size_t smem = batch_smem_bytes(kTile, storage_bytes(kStore));
   if (smem <= 48 * 1024) return cudaSuccess;
+  if constexpr (batch_rows_pairs<kStore>())
+    return cudaFuncSetAttribute(k_batch_rows_pair<kStore, kTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaFuncSetAttribute(k_batch_step<kStore, kTile, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
@@ -229,8 +362,15 @@ static cudaError_t launch_batch_t(const ReplicaDev* reps, const int* tile_rep, i
     if (rows_tiles > 0) {
       cfg.gridDim = dim3((unsigned)rows_tiles);
       cfg.dynamicSmemBytes = batch_smem_bytes(kTile, storage_bytes(kStore));
-      const cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, true>, reps, tile_rep, (int64_t)0,
-                                               step0, (uint32_t)k, err);
+      cudaError_t e;
+      if constexpr (batch_rows_pairs<kStore>()) {
+        cfg.blockDim = dim3(kTile / 2);
+        e = cudaLaunchKernelEx(&cfg, k_batch_rows_pair<kStore, kTile>, reps, tile_rep, step0, (uint32_t)k, err);
+        cfg.blockDim = dim3(kTile);
+      } else {
+        e = cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, true>, reps, tile_rep, (int64_t)0, step0,
+                               (uint32_t)k, err);
+      }
       if (e != cudaSuccess) return e;
     }
     if (tiles > rows_tiles) {
@@ -248,9 +388,13 @@ template <int kStore, int kTile>
 static int occupancy_t() {
   if (set_smem_t<kStore, kTile>() != cudaSuccess) return 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<kStore, kTile, true>, kTile,
-                                                    batch_smem_bytes(kTile, storage_bytes(kStore))) != cudaSuccess)
-    return 1;
+  const size_t smem = batch_smem_bytes(kTile, storage_bytes(kStore));
+  cudaError_t e;
+  if constexpr (batch_rows_pairs<kStore>())
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_rows_pair<kStore, kTile>, kTile / 2, smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<kStore, kTile, true>, kTile, smem);
+  if (e != cudaSuccess) return 1;
   return std::max(n, 1);
 }
 

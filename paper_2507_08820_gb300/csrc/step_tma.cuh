@@ -142,18 +142,6 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   }
 }
 
-// Output weight of the two-site kernel: the lattice weight times the storage scale of the
-// entry's velocity class (both powers of two apart from the weight, so the product rounds
-// exactly as scaling after the weighting would).
-template <int kStore>
-struct ScaledWeight {
-  const StoreScale& ss;
-  __device__ __forceinline__ float operator()(int a, int b, int c) const {
-    const float wt = float(w1d(a) * w1d(b) * w1d(c));
-    return Storage<kStore>::kScaled ? wt * ss.scale[class_at(a, b, c)] : wt;
-  }
-};
-
 // The same step with two adjacent sites per thread: kW / 2 threads per segment, thread t
 // updates x0 + 2t and x0 + 2t + 1 with the collision in packed f32x2 arithmetic (Reg-FLBM,
 // omega_g = 1, local rho in Eq. 10). Plane c_x = 0 of a site pair is read from shared memory
@@ -161,8 +149,6 @@ struct ScaledWeight {
 // out as pairs (16-bit storage: one packed conversion per pair) with the storage scale
 // folded into the lattice weights. Philox calls 0 and 1 of both sites are drawn before the
 // kernel waits for the previous step, the other four inside the collision.
-constexpr int kPairPreDrawn = 2;
-
 template <int kStore, int kW, bool kNoise>
 __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ CUtensorMap load_map,
                                                          const __grid_constant__ CUtensorMap store_map,

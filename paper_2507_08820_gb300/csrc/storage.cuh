@@ -13,6 +13,8 @@
 
 #include <cstdint>
 
+#include "d3q27.cuh"
+
 namespace rflbm_dev {
 
 enum : int { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
@@ -51,6 +53,7 @@ struct Storage<kStoreF32> {
     *reinterpret_cast<float2*>(p) = v;
   }
   static __device__ __forceinline__ T pack(float v) { return v; }  // already scaled
+  static __device__ __forceinline__ float to_float(T v) { return v; }  // not scaled
   static constexpr bool kScaled = false;
 };
 
@@ -76,6 +79,7 @@ struct Storage<kStoreF16> {
     *reinterpret_cast<__half2*>(p) = __float22half2_rn(v);
   }
   static __device__ __forceinline__ T pack(float v) { return __float2half_rn(v); }
+  static __device__ __forceinline__ float to_float(T v) { return __half2float(v); }
   static constexpr bool kScaled = true;
 };
 
@@ -99,9 +103,22 @@ struct Storage<kStoreBF16> {
     *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v);
   }
   static __device__ __forceinline__ T pack(float v) { return __float2bfloat16_rn(v); }
+  static __device__ __forceinline__ float to_float(T v) { return __bfloat162float(v); }
   static constexpr bool kScaled = true;
 };
 
 inline size_t storage_bytes(int kind) { return kind == kStoreF32 ? 4 : 2; }
+
+// Output weight of the two-site kernels (collide_tile's OutWeight): the lattice weight of
+// tile entry (a, b, c) times the storage scale of its velocity class. The scale is a power
+// of two, so the product rounds exactly as scaling after the weighting would.
+template <int kStore>
+struct ScaledWeight {
+  const StoreScale& ss;
+  __device__ __forceinline__ float operator()(int a, int b, int c) const {
+    const float wt = float(w1d(a) * w1d(b) * w1d(c));
+    return Storage<kStore>::kScaled ? wt * ss.scale[class_at(a, b, c)] : wt;
+  }
+};
 
 }  // namespace rflbm_dev
