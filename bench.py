@@ -109,19 +109,22 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def kernel_name(kind, path, kT, model, storage="f32", pattern="pingpong", sites_per_thread=1):
+def kernel_name(kind, path, kT, model, storage="f32", pattern="pingpong", sites_per_thread=1,
+                odd_sites_per_thread=None):
+    """(name, profile stem) of the step kernel; for AA, sites_per_thread is that of the
+    even steps and odd_sites_per_thread that of the odd steps (default: the same)."""
     noise = "noise" if kT > 0 else "no noise"
     m = "BGK" if model else "Reg"
-    if pattern == "aa" and kind == 2 and sites_per_thread == 2:
-        return (f"step_aa_even_pair+step_aa_odd_pair<{storage}, {path}, {m}, {noise}>",
-                f"step_aa_pair_{storage}_{path}")
-    if kind == 2 and sites_per_thread == 2:
-        return f"step_tma_pair<{storage}, {path}, {m}, {noise}>", f"step_tma_pair_{storage}_{path}"
     if pattern == "aa":
         if kind == 2:
-            return (f"step_aa_even+step_aa_odd<{storage}, {path}, {m}, {noise}>",
-                    f"step_aa_{storage}_{path}")
+            odd = sites_per_thread if odd_sites_per_thread is None else odd_sites_per_thread
+            even_k = "step_aa_even_pair" if sites_per_thread == 2 else "step_aa_even"
+            odd_k = "step_aa_odd_pair" if odd == 2 else "step_aa_odd"
+            tag = {(1, 1): "", (2, 2): "pair_", (1, 2): "oddpair_", (2, 1): "evenpair_"}[(sites_per_thread, odd)]
+            return f"{even_k}+{odd_k}<{storage}, {path}, {m}, {noise}>", f"step_aa_{tag}{storage}_{path}"
         return f"step_aa_gather<{storage}, {m}, {noise}>", f"step_aa_gather_{storage}"
+    if kind == 2 and sites_per_thread == 2:
+        return f"step_tma_pair<{storage}, {path}, {m}, {noise}>", f"step_tma_pair_{storage}_{path}"
     if kind == 2:
         return f"step_tma<{storage}, {path}, {m}, {noise}>", f"step_tma_{storage}_{path}"
     return f"step_pull<{storage}, {m}, {noise}>", f"step_pull_{storage}"
@@ -387,7 +390,13 @@ def gb300_arm(args):
         torch.cuda.empty_cache()
     kind, path = R.rflbm_step_path(box.h)
     pairs = R.rflbm_step_sites_per_thread(box.h)
-    R.rflbm_step(box.h, args.warmup)
+    odd_pairs = pairs
+    warm = args.warmup
+    if args.pattern == "aa" and warm > 0:  # the odd AA steps may run the other form
+        R.rflbm_step(box.h, 1)
+        odd_pairs = R.rflbm_step_sites_per_thread(box.h)
+        warm -= 1
+    R.rflbm_step(box.h, warm)
     R.rflbm_synchronize(box.h)
 
     sampler = ClockSampler(device_uuid(torch))
@@ -479,7 +488,7 @@ def gb300_arm(args):
     per_launch_s = ms * 1e-3 / args.steps
     achieved = BYTES_PER_SITE[args.storage] * n / per_launch_s / 1e9
     peak, peak_kind = measured_peak()
-    kname, kstem = kernel_name(kind, path, args.kT, 0, args.storage, args.pattern, pairs)
+    kname, kstem = kernel_name(kind, path, args.kT, 0, args.storage, args.pattern, pairs, odd_pairs)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(kstem, e),
                 "peak_source": f"hbm_gbs of {peak_kind}", "kernel": kname,

@@ -54,4 +54,6 @@ def test_workload_and_kernel_names():
     assert bench.kernel_name(2, 128, 1e-4, 0, "f16", "pingpong", 2) == (
         "step_tma_pair<f16, 128, Reg, noise>", "step_tma_pair_f16_128")
     assert bench.kernel_name(2, 128, 0.0, 0, "f16", "aa", 2)[1] == "step_aa_pair_f16_128"
+    assert bench.kernel_name(2, 128, 1e-4, 0, "f32", "aa", 1, 2) == (
+        "step_aa_even+step_aa_odd_pair<f32, 128, Reg, noise>", "step_aa_oddpair_f32_128")
     assert len(bench.kernel_source_hash()) == 16
