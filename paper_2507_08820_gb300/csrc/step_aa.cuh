@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   grid_dependency_wait();
 
   if (t == 0) {
-    mbar_arrive_expect_tx(&bar, (uint32_t)AaEvenLayout<kStore, kW>::kTileBytes);
+    mbar_arrive_expect_tx(&bar, (uint32_t)AaEvenLayout<kStore, kW>::kTileBytes + p.test_extra_tx);
     tma_load_4d(sm, &map, (int)x0, (int)y, (int)z, 0, &bar);
   }
 
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   T patch_l = T(), patch_r = T();
   int at_l = -1, at_r = -1;
   if (t < kGroups) {
-    if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)));
+    if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)) + p.test_extra_tx);
     const int cy = t / 3 - 1, cz = t % 3 - 1;
     int ys = (int)y - cy, zs = (int)z - cz;
     ys += ys < 0 ? (int)p.geo.ny : 0;
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_even_pair(const __grid_constan
   grid_dependency_wait();
 
   if (t == 0) {
-    mbar_arrive_expect_tx(&bar, (uint32_t)AaEvenLayout<kStore, kW>::kTileBytes);
+    mbar_arrive_expect_tx(&bar, (uint32_t)AaEvenLayout<kStore, kW>::kTileBytes + p.test_extra_tx);
     tma_load_4d(sm, &map, (int)x0, (int)y, (int)z, 0, &bar);
   }
   const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
   T patch_l = T(), patch_r = T();
   int at_l = -1, at_r = -1;
   if (t < kGroups) {
-    if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)));
+    if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)) + p.test_extra_tx);
     const int cy = t / 3 - 1, cz = t % 3 - 1;
     int ys = (int)y - cy, zs = (int)z - cz;
     ys += ys < 0 ? (int)p.geo.ny : 0;

@@ -20,10 +20,20 @@ def R():
     return rflbm
 
 
-def test_expired_copy_wait_reports_timeout_and_recovers(R):
-    box = R.Box(32, 1, 1, tau=0.8, kT=1e-4, seed=3)  # one CTA of 32 sites
-    assert R.rflbm_step_path(box.h) == (R.RFLBM_KERNEL_TMA, 32)
+@pytest.mark.parametrize("nx,kw,pre_steps,pairs", [
+    (32, dict(kT=1e-4), 0, 1),                      # one-site ping-pong step, one CTA
+    (32, dict(kT=1e-4, storage=1), 0, 2),           # two-site ping-pong step
+    (32, dict(kT=1e-4, pattern=1), 0, 1),           # AA even step
+    (32, dict(kT=1e-4, pattern=1), 1, 1),           # AA odd step, whole-row stores
+    (32, dict(kT=0.0, storage=1, pattern=1), 0, 2),  # two-site AA even step
+    (256, dict(kT=1e-4, pattern=1), 1, 2),          # two-site AA odd step, direct stores
+])
+def test_expired_copy_wait_reports_timeout_and_recovers(R, nx, kw, pre_steps, pairs):
+    box = R.Box(nx, 1, 1, tau=0.8, seed=3, **kw)
+    assert R.rflbm_step_path(box.h)[0] == R.RFLBM_KERNEL_TMA
     R.rflbm_init_rest(box.h)
+    R.rflbm_step(box.h, pre_steps)
+    assert R.rflbm_step_sites_per_thread(box.h) == pairs
     R.rflbm_testing_expect_extra_bytes(box.h, 16)
     t0 = time.time()
     R.rflbm_step(box.h, 1)
@@ -37,7 +47,7 @@ def test_expired_copy_wait_reports_timeout_and_recovers(R):
     R.rflbm_step(box.h, 5)
     R.rflbm_synchronize(box.h)
     st, status = R.rflbm_stats(box.h)
-    assert status == R.RFLBM_OK and abs(st.mass - 32.0) < 1e-5
+    assert status == R.RFLBM_OK and abs(st.mass - nx) < 1e-5 * nx
     f = box.populations()
     assert np.all(np.isfinite(f))
     with pytest.raises(R.RflbmError):
