@@ -16,7 +16,8 @@
 extern "C" {
 #endif
 
-/* Every later step launch of h on the TMA path (ping-pong pattern) expects `bytes` more
+/* Every later step launch of h on the TMA path (either streaming pattern, one-site and
+ * two-site forms) expects `bytes` more
  * bytes on its copy barrier than its copies deliver, so that barrier never completes and
  * each CTA's bounded wait runs out (about one second per wait). 0 restores normal
  * operation. bytes <= 2^20, else RFLBM_EINVAL. The state after such a step is undefined;
