@@ -3,7 +3,8 @@
 1024 x 1024 x 2047 = 2,146,435,072 sites is just below the 2^31 site limit: site indices,
 Philox counters and neighbour offsets use their full 31-bit range. 1024^3 in float32 has
 4.3 GB planes, so every plane offset beyond the first needs 64 bits. Both run in the AA
-pattern (one 116 GB buffer), through both of its forms, from rest.
+pattern (one 116 GB buffer), through both of its forms, from rest; a 1024 x 1024 x 1536
+float16 box (two 87 GB buffers) runs the two-site ping-pong kernel at 64-bit plane offsets.
 
 After one step the populations are site-local functions of the noise; after two they
 depend on the 27 neighbours. get_sites returns f_i(x, t) = f*_i(x - c_i, t - 1), so the
@@ -69,12 +70,13 @@ def _check(got, want, storage):
         assert np.all(np.abs(got - want) <= bound), np.max(np.abs(got - want) / bound)
 
 
-@pytest.mark.parametrize("shape,storage", [((1024, 1024, 2047), 1), ((1024, 1024, 1024), 0)])
-def test_largest_boxes_two_steps_at_sampled_sites(R, shape, storage):
+@pytest.mark.parametrize("shape,storage,pattern", [((1024, 1024, 2047), 1, 1), ((1024, 1024, 1024), 0, 1),
+                                                   ((1024, 1024, 1536), 1, 0)])
+def test_largest_boxes_two_steps_at_sampled_sites(R, shape, storage, pattern):
     n = int(np.prod(shape))
     assert n < 2 ** 31
     tau, kT, seed = 0.8, 1e-4, 5
-    box = R.Box(*shape, tau=tau, kT=kT, seed=seed, storage=storage, pattern=R.RFLBM_PATTERN_AA)
+    box = R.Box(*shape, tau=tau, kT=kT, seed=seed, storage=storage, pattern=pattern)
     try:
         R.rflbm_init_rest(box.h)
         sites = _sites(shape, 160, seed=3)
