@@ -100,12 +100,37 @@ STEP_KERNEL_SOURCES = ("collide.cuh", "d3q27.cuh", "philox.cuh", "rflbm_internal
                        "tma.cuh")
 
 
+def strip_comments(src):
+    """C/C++ source without its comments and blank lines (string and character literals
+    kept), so that the hash below changes with the code only."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(line.rstrip() for line in "".join(out).splitlines() if line.strip())
+
+
 def kernel_source_hash():
+    """Hash of the code (comments excluded) the step kernels are compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_08820_gb300", "csrc")
     for name in STEP_KERNEL_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(name.encode() + fh.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as fh:
+            h.update((name + strip_comments(fh.read())).encode())
     return h.hexdigest()[:16]
 
 

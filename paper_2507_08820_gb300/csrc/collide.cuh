@@ -122,12 +122,12 @@ struct DrawnNoise {
   }
 };
 
-// Noise source for two sites per thread (sites site0 and site0 + 1): Philox calls j < kPre
-// drawn beforehand by draw() (raw words, while the tile's copies are in flight), the later
-// calls when the collision needs them.
 // Philox calls the two-site kernels draw before they wait for the previous step.
 constexpr int kPairPreDrawn = 2;
 
+// Noise source for two sites per thread (sites site0 and site0 + 1): Philox calls j < kPre
+// drawn beforehand by draw() (raw words, while the previous step drains), the later calls
+// when the collision needs them. Key: PhiloxKey or PhiloxRoundKeys.
 template <int kPre, class Key>
 struct PairNoise {
   uint32_t site0, step, replica;

@@ -41,6 +41,12 @@ def test_profiled_traffic_requires_the_current_sources(tmp_path, monkeypatch):
     assert bench.profiled_traffic("k", 64) == 1234.0
 
 
+def test_source_hash_ignores_comments():
+    src = 'int a = 1; // one\n/* block\n comment */ const char* s = "//not a comment";\nchar q = \'"\';\n'
+    assert bench.strip_comments(src) == 'int a = 1;\n const char* s = "//not a comment";\nchar q = \'"\';'
+    assert bench.strip_comments("x = 1;\n\n// gone\ny = 2;") == "x = 1;\ny = 2;"
+
+
 def test_workload_and_kernel_names():
     args = types.SimpleNamespace(edge=128, tau=0.8, kT=1e-4, storage="f32", init="rest", pattern="pingpong")
     w = bench.workload(args)
