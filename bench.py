@@ -98,6 +98,8 @@ def measured_peak():
 STEP_KERNEL_SOURCES = ("collide.cuh", "d3q27.cuh", "philox.cuh", "rflbm_internal.h",
                        "rflbm_step_tma.cu", "rflbm_step_tma16.cu", "step_tma.cuh", "storage.cuh",
                        "tma.cuh")
+AA_KERNEL_SOURCES = STEP_KERNEL_SOURCES + ("step_aa.cuh", "rflbm_step_aa_f32.cu", "rflbm_step_aa_f16.cu",
+                                           "rflbm_step_aa_bf16.cu")
 
 
 def strip_comments(src):
@@ -124,11 +126,11 @@ def strip_comments(src):
     return "\n".join(line.rstrip() for line in "".join(out).splitlines() if line.strip())
 
 
-def kernel_source_hash():
+def kernel_source_hash(names=STEP_KERNEL_SOURCES):
     """Hash of the code (comments excluded) the step kernels are compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_08820_gb300", "csrc")
-    for name in STEP_KERNEL_SOURCES:
+    for name in names:
         with open(os.path.join(csrc, name), encoding="utf-8") as fh:
             h.update((name + strip_comments(fh.read())).encode())
     return h.hexdigest()[:16]
@@ -163,7 +165,8 @@ def profiled_traffic(profile_stem, edge):
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(sources ([0-9a-f]+)\)", text)
-    if not m or m.group(2) != kernel_source_hash():
+    names = AA_KERNEL_SOURCES if profile_stem.startswith("step_aa") else STEP_KERNEL_SOURCES
+    if not m or m.group(2) != kernel_source_hash(names):
         return None
     return float(m.group(1))
 

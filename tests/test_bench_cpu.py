@@ -39,6 +39,12 @@ def test_profiled_traffic_requires_the_current_sources(tmp_path, monkeypatch):
     assert bench.profiled_traffic("k", 64) is None  # other sources
     f.write_text(f"traffic_bytes_per_launch: 1234 (sources {bench.kernel_source_hash()})\n")
     assert bench.profiled_traffic("k", 64) == 1234.0
+    # AA summaries are checked against the hash that also covers the AA sources
+    g = tmp_path / "step_aa_pair_f16_128_64cubed.md"
+    g.write_text(f"traffic_bytes_per_launch: 99 (sources {bench.kernel_source_hash()})\n")
+    assert bench.profiled_traffic("step_aa_pair_f16_128", 64) is None
+    g.write_text(f"traffic_bytes_per_launch: 99 (sources {bench.kernel_source_hash(bench.AA_KERNEL_SOURCES)})\n")
+    assert bench.profiled_traffic("step_aa_pair_f16_128", 64) == 99.0
 
 
 def test_source_hash_ignores_comments():
