@@ -100,6 +100,8 @@ STEP_KERNEL_SOURCES = ("collide.cuh", "d3q27.cuh", "philox.cuh", "rflbm_internal
                        "tma.cuh")
 AA_KERNEL_SOURCES = STEP_KERNEL_SOURCES + ("step_aa.cuh", "rflbm_step_aa_f32.cu", "rflbm_step_aa_f16.cu",
                                            "rflbm_step_aa_bf16.cu")
+BATCH_KERNEL_SOURCES = ("collide.cuh", "d3q27.cuh", "philox.cuh", "rflbm_internal.h", "storage.cuh", "tma.cuh",
+                        "rflbm_aux.h", "rflbm_batch.cu")
 
 
 def strip_comments(src):
@@ -158,14 +160,17 @@ def kernel_name(kind, path, kT, model, storage="f32", pattern="pingpong", sites_
 
 
 def profiled_traffic(profile_stem, edge):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
-    when the summary is missing or was taken on different kernel sources."""
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (<stem>_<edge>cubed.md, or <stem>_<edge>.md when edge is a workload name), or None when
+    the summary is missing or was taken on different kernel sources."""
+    suffix = f"{edge}cubed" if isinstance(edge, int) else edge
     try:
-        text = open(os.path.join(PROFILES, f"{profile_stem}_{edge}cubed.md")).read()
+        text = open(os.path.join(PROFILES, f"{profile_stem}_{suffix}.md")).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(sources ([0-9a-f]+)\)", text)
-    names = AA_KERNEL_SOURCES if profile_stem.startswith("step_aa") else STEP_KERNEL_SOURCES
+    names = (AA_KERNEL_SOURCES if profile_stem.startswith("step_aa") else
+             BATCH_KERNEL_SOURCES if profile_stem.startswith("k_batch") else STEP_KERNEL_SOURCES)
     if not m or m.group(2) != kernel_source_hash(names):
         return None
     return float(m.group(1))
@@ -366,7 +371,10 @@ def ensemble_arm(args):
                    "tile": tile, "ctas_per_sm": per_sm, "tiles_per_step": tiles,
                    "parallelism": "replicas"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs of {peak_kind}",
+                     "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
+                     "traffic": profiled_traffic(
+                         (f"k_batch_step_{args.storage}_{tile}" if args.storage == "f32"
+                          else f"k_batch_rows_pair_{args.storage}_{tile}"), "ensemble64"),
                      "kernel": (f"k_batch_step<{args.storage}, {tile}, rows>" if args.storage == "f32"
                                 else f"k_batch_rows_pair<{args.storage}, {tile}>"),
                      "algorithmic_bytes_per_launch": bps * sites},
