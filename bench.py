@@ -141,7 +141,14 @@ def kernel_source_hash(names=STEP_KERNEL_SOURCES):
 def kernel_name(kind, path, kT, model, storage="f32", pattern="pingpong", sites_per_thread=1,
                 odd_sites_per_thread=None):
     """(name, profile stem) of the step kernel; for AA, sites_per_thread is that of the
-    even steps and odd_sites_per_thread that of the odd steps (default: the same)."""
+    even steps and odd_sites_per_thread that of the odd steps (default: the same). The stem
+    of a kernel without noise or of the BGK model carries a suffix, so that it never reads
+    the profile of the Reg-FLBM fluctuating kernel."""
+    name, stem = _kernel_name(kind, path, kT, model, storage, pattern, sites_per_thread, odd_sites_per_thread)
+    return name, stem + ("" if kT > 0 else "_kt0") + ("_bgk" if model else "")
+
+
+def _kernel_name(kind, path, kT, model, storage, pattern, sites_per_thread, odd_sites_per_thread):
     noise = "noise" if kT > 0 else "no noise"
     m = "BGK" if model else "Reg"
     if pattern == "aa":

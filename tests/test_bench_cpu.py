@@ -61,11 +61,11 @@ def test_workload_and_kernel_names():
     w = bench.workload(args)
     assert w["streaming"] == "AA, one buffer in place" and "1 population buffer" in w["l2"]
     assert bench.kernel_name(2, 128, 1e-4, 0) == ("step_tma<f32, 128, Reg, noise>", "step_tma_f32_128")
-    assert bench.kernel_name(2, 64, 0.0, 1, "f16", "aa")[1] == "step_aa_f16_64"
+    assert bench.kernel_name(2, 64, 0.0, 1, "f16", "aa")[1] == "step_aa_f16_64_kt0_bgk"
     assert bench.kernel_name(1, 0, 1e-4, 0)[0] == "step_pull<f32, Reg, noise>"
     assert bench.kernel_name(2, 128, 1e-4, 0, "f16", "pingpong", 2) == (
         "step_tma_pair<f16, 128, Reg, noise>", "step_tma_pair_f16_128")
-    assert bench.kernel_name(2, 128, 0.0, 0, "f16", "aa", 2)[1] == "step_aa_pair_f16_128"
+    assert bench.kernel_name(2, 128, 0.0, 0, "f16", "aa", 2)[1] == "step_aa_pair_f16_128_kt0"
     assert bench.kernel_name(2, 128, 1e-4, 0, "f32", "aa", 1, 2) == (
         "step_aa_even+step_aa_odd_pair<f32, 128, Reg, noise>", "step_aa_oddpair_f32_128")
     assert len(bench.kernel_source_hash()) == 16
