@@ -81,7 +81,8 @@ typedef enum {
 /* Step kernels. Both compute the same step; they differ in how the 27 neighbours are
  * fetched. The TMA kernel needs nx to be a multiple of 32 (row segments of 128, 192, 96,
  * 64 or 32 sites, the first that divides nx); on other boxes every choice runs the
- * general kernel. */
+ * general kernel. Some variants of the TMA kernel update two sites per thread with packed
+ * arithmetic (rflbm_step_sites_per_thread), bit for bit like the one-site forms. */
 typedef enum {
   RFLBM_KERNEL_AUTO = 0,    /* TMA when the box allows it, else the general kernel */
   RFLBM_KERNEL_GATHER = 1,  /* one thread per site, 27 addressed loads */
