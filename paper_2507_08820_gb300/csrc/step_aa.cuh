@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   grid_launch_dependents();
   const uint32_t s = x0 + t + p.geo.nx * row;
   SiteNoise noise;
-  if (kNoise) site_noise_part<0, 3>(s, p.step, p.replica, p.rk, noise);
+  if (kNoise) site_noise_part<0, kPreWaitCalls>(s, p.step, p.replica, p.rk, noise);
 
   if (t == 0) {
     mbar_init(&bar, 1);
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
     tma_load_4d(sm, &map, (int)x0, (int)y, (int)z, 0, &bar);
   }
 
-  if (kNoise) site_noise_part<3, 6>(s, p.step, p.replica, p.rk, noise);
+  if (kNoise) site_noise_part<kPreWaitCalls, 6>(s, p.step, p.replica, p.rk, noise);
 
   const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
   if (__syncthreads_or(!ok)) {
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   const uint32_t x = x0 + t;
   const uint32_t s = x + p.geo.nx * row;
   SiteNoise noise;
-  if (kNoise) site_noise_part<0, 3>(s, p.step, p.replica, p.rk, noise);
+  if (kNoise) site_noise_part<0, kPreWaitCalls>(s, p.step, p.replica, p.rk, noise);
 
   if (t == 0) {
     mbar_init(&bar, 1);
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
     }
   }
 
-  if (kNoise) site_noise_part<3, 6>(s, p.step, p.replica, p.rk, noise);
+  if (kNoise) site_noise_part<kPreWaitCalls, 6>(s, p.step, p.replica, p.rk, noise);
   const PullDeltas d = deltas_at(x, y, z, p.geo);
 
   const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
