@@ -58,6 +58,7 @@ __host__ __device__ constexpr size_t batch_smem_bytes(int tile, size_t elem) {
 }
 
 constexpr uint32_t kBatchTmaPolls = 1u << 22;
+constexpr int kBatchPreWaitCalls = 2;  // Philox calls a row tile draws before the dependency wait
 constexpr int kBatchGroups = 9;  // source rows (c_y, c_z) of a site
 
 // One step of the tiles [tile0, tile0 + gridDim.x) of the tile table, all of one kind
@@ -131,9 +132,11 @@ __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
   const uint32_t row = fastdiv((uint32_t)tid, rep.geo.div_nx);
   const uint32_t x = (uint32_t)tid - row * nx;
   const bool active = row < nrows;
-  // the noise is drawn while the previous step drains and the copies are in flight
+  // the noise is drawn while the previous step drains (calls 0 and 1) and while the copies
+  // are in flight (calls 2 to 5), as in the single-box kernel
   SiteNoise noise;
-  if (rep.noise && active) site_noise(x + nx * ((y0 + row) + ny * z), step, 0u, rep.key0, rep.key1, noise);
+  const uint32_t site = x + nx * ((y0 + row) + ny * z);
+  if (rep.noise && active) site_noise_part<0, kBatchPreWaitCalls>(site, step, 0u, rep.key0, rep.key1, noise);
 
   grid_dependency_wait();  // the previous step's writes (our source) are complete
   if (tid < kBatchGroups) {
@@ -144,6 +147,7 @@ __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
     zs -= zs >= (int)nz ? (int)nz : 0;
     tma_load_4d(sm + tid * kGroup, rep.maps + 2 * parity, 0, (int)y0 - cy, zs, 3 * tid, &bar);
   }
+  if (rep.noise && active) site_noise_part<kBatchPreWaitCalls, 6>(site, step, 0u, rep.key0, rep.key1, noise);
   const bool ok = mbar_wait_bounded(&bar, 0, kBatchTmaPolls);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) atomicOr(err, 1);
