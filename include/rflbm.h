@@ -52,7 +52,8 @@ typedef enum {
   RFLBM_EINVAL = -1,     /* invalid argument (sizes, tau <= 1/2, kT < 0, rho0 <= 0, ...) */
   RFLBM_ENOMEM = -2,     /* device or host allocation failed */
   RFLBM_ECUDA = -3,      /* CUDA runtime error (no device, launch or kernel failure) */
-  RFLBM_EUNSTABLE = -4,  /* the state holds non-finite values (reported by rflbm_stats) */
+  RFLBM_EUNSTABLE = -4,  /* the state holds non-finite values or non-positive densities
+                            (reported by rflbm_stats) */
   RFLBM_ETIMEOUT = -5,   /* a bounded device wait expired */
   RFLBM_ESTATE = -6      /* call not valid in the handle's current state */
 } rflbm_status;
@@ -130,7 +131,8 @@ typedef struct {
   double mass;           /* sum_s rho(s) (Eq. 3), FP64 accumulation */
   double momentum[3];    /* sum_s rho u(s) (Eq. 4), FP64 accumulation */
   double max_speed;      /* max_s |u(s)| */
-  int64_t nonfinite;     /* sites whose density or momentum is not finite */
+  int64_t nonfinite;     /* unstable sites: density or momentum not finite, or density
+                            not positive (such sites enter no sum and no max_speed) */
 } rflbm_stats_t;
 
 /* Fills cfg with the defaults: 32^3, tau 0.8, kT 0, rho0 1, seed 1, omega_g 1, Reg model,
@@ -190,7 +192,7 @@ int rflbm_step(rflbm_t* h, int64_t n);
 int rflbm_moments(rflbm_t* h, double* rho, double* u, double* pi, int on_device);
 
 /* Global diagnostics of the current state in FP64 (see rflbm_stats_t). Synchronous.
- * Returns RFLBM_EUNSTABLE (with *out filled) when non-finite values are present. */
+ * Returns RFLBM_EUNSTABLE (with *out filled) when unstable sites are present. */
 int rflbm_stats(rflbm_t* h, rflbm_stats_t* out);
 
 /* Current populations f_i(x, t) as 27*N doubles / floats (layout above). Synchronous.
@@ -284,28 +286,6 @@ int rflbm_philox4x32_10(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t*
 int rflbm_site_normals(uint64_t seed, int64_t step, uint32_t replica,
                        const uint32_t* sites, int64_t n, float* out);
 
-/* Global diagnostics of caller-owned populations that allocate nothing.
- *
- * The paper has no counterpart: this entry point exists for callers that cannot allocate
- * device memory at the moment they need these numbers, typically because their
- * framework has already reserved the device memory for its own pool (a cudaMalloc would
- * fail, or would synchronise the device inside a pipeline that must not stall), or
- * because they run as a hook between the steps of another solver. It computes what
- * rflbm_stats computes (FP64 sums of density and momentum, maximum speed, non-finite
- * sites; step is set to 0) for populations in the public layout: f holds 27 planes of
- * n_sites float32 values in device memory of the current device (element [i*n_sites + s]),
- * owned by the caller. `stream` is a cudaStream_t or NULL; the call waits for it and fills
- * *out (host memory).
- *
- * Scratch: a fixed area in the library's static device memory (about 512 KB, held by
- * every GPU that loads the library until the process exits); no cudaMalloc, cudaFree or
- * other allocating routine is called. Capacity: n_sites <= RFLBM_STATS_NOALLOC_MAX_SITES
- * (8192 partial sums of 16384 sites); larger inputs are rejected with RFLBM_EINVAL. The
- * first call on a device looks up the area's device address (once per device, with that
- * device current); make that first call before any stream capture. All calls share the
- * area: calls that overlap on the GPU (two streams or two host threads at once) race and
- * must be serialised by the caller. Returns RFLBM_OK, RFLBM_EUNSTABLE (non-finite values;
- * *out filled), RFLBM_EINVAL or RFLBM_ECUDA (message in rflbm_last_error). */
 /* Batched ensembles: many independent periodic boxes ("replicas") of uneven sizes, seeds,
  * tau and kT, advanced together: each step is one launch over the tiles of every replica,
  * and the n steps of a call replay as one CUDA graph (captured once per n). Each replica
@@ -332,6 +312,8 @@ int rflbm_batch_tuning(const rflbm_batch_t* b, int* tile, int* ctas_per_sm, int6
 /* Kernel launches per step: 1 when every replica takes one kind of tile, 2 when both
  * kinds are present (row tiles and site tiles run as separate launches). */
 int rflbm_batch_launches_per_step(const rflbm_batch_t* b);
+/* Box edges of replica r (any pointer may be NULL). */
+int rflbm_batch_replica_dims(const rflbm_batch_t* b, int r, int* nx, int* ny, int* nz);
 /* Every replica at rest, step 0. */
 int rflbm_batch_init_rest(rflbm_batch_t* b);
 /* n steps of every replica (asynchronous on the default stream). */
@@ -341,6 +323,28 @@ int rflbm_batch_synchronize(rflbm_batch_t* b);
 int rflbm_batch_get_populations(rflbm_batch_t* b, int r, double* f);
 int rflbm_batch_stats(rflbm_batch_t* b, int r, rflbm_stats_t* out);
 
+/* Global diagnostics of caller-owned populations that allocate nothing.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory at the moment they need these numbers, typically because their
+ * framework has already reserved the device memory for its own pool (a cudaMalloc would
+ * fail, or would synchronise the device inside a pipeline that must not stall), or
+ * because they run as a hook between the steps of another solver. It computes what
+ * rflbm_stats computes (FP64 sums of density and momentum, maximum speed, unstable
+ * sites; step is set to 0) for populations in the public layout: f holds 27 planes of
+ * n_sites float32 values in device memory of the current device (element [i*n_sites + s]),
+ * owned by the caller. `stream` is a cudaStream_t or NULL; the call waits for it and fills
+ * *out (host memory).
+ *
+ * Scratch: a fixed area in the library's static device memory (about 512 KB, held by
+ * every GPU that loads the library until the process exits); no cudaMalloc, cudaFree or
+ * other allocating routine is called. Capacity: n_sites <= RFLBM_STATS_NOALLOC_MAX_SITES
+ * (8192 partial sums of 16384 sites); larger inputs are rejected with RFLBM_EINVAL. Every
+ * call looks up the area's device address on the current device (cudaGetSymbolAddress,
+ * which allocates nothing), so a call stays valid after a cudaDeviceReset. All calls share the
+ * area: calls that overlap on the GPU (two streams or two host threads at once) race and
+ * must be serialised by the caller. Returns RFLBM_OK, RFLBM_EUNSTABLE (unstable sites;
+ * *out filled), RFLBM_EINVAL or RFLBM_ECUDA (message in rflbm_last_error). */
 #define RFLBM_STATS_NOALLOC_MAX_SITES 134217728LL
 int rflbm_stats_f32_noalloc(const float* f, int64_t n_sites, void* stream, rflbm_stats_t* out);
 

@@ -587,7 +587,7 @@ int rflbm_stats(rflbm_t* h, rflbm_stats_t* out) {
   out->max_speed = host[4];
   out->nonfinite = (int64_t)host[5];
   if (out->nonfinite > 0)
-    return fail(RFLBM_EUNSTABLE, "%lld sites hold non-finite values at step %lld",
+    return fail(RFLBM_EUNSTABLE, "%lld sites are unstable (non-finite values or non-positive density) at step %lld",
                 (long long)out->nonfinite, (long long)h->step);
   return RFLBM_OK;
 }

@@ -199,7 +199,8 @@ __global__ void k_moments(Geometry g, float rho0, StoreScale ss,
   }
 }
 
-// Per-block partial sums: drho, j (3), max |u|, count of non-finite sites.
+// Per-block partial sums: drho, j (3), max |u|, count of unstable sites (non-finite, or
+// density not positive).
 constexpr int kStatFields = 6;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -222,9 +223,10 @@ __global__ void k_stats_partial(Geometry g, float rho0, StoreScale ss,
        s += (int64_t)gridDim.x * kAuxBlock) {
     const SiteMoments m = site_moments<kStore, float>(g, site_of(s), src, ss);
     const double r = (double)rho0 + m.drho;
-    const bool finite = isfinite(m.drho) && isfinite(m.j[0]) && isfinite(m.j[1]) &&
-                        isfinite(m.j[2]);
-    if (finite) {
+    // a non-finite site, or one whose density is not positive, counts as unstable
+    const bool stable = isfinite(m.drho) && isfinite(m.j[0]) && isfinite(m.j[1]) &&
+                        isfinite(m.j[2]) && r > 0.0;
+    if (stable) {
       acc[0] += m.drho;
       acc[1] += m.j[0]; acc[2] += m.j[1]; acc[3] += m.j[2];
       const float sp = sqrtf((float)(m.j[0] * m.j[0] + m.j[1] * m.j[1] + m.j[2] * m.j[2])) / fabsf((float)r);

@@ -783,6 +783,15 @@ int rflbm_batch_tuning(const rflbm_batch_t* b, int* tile, int* ctas_per_sm, int6
   return RFLBM_OK;
 }
 
+int rflbm_batch_replica_dims(const rflbm_batch_t* b, int r, int* nx, int* ny, int* nz) {
+  if (!b || r < 0 || r >= b->n) return bfail(RFLBM_EINVAL, "invalid batch or replica");
+  const Geometry& g = b->host[r].geo;
+  if (nx) *nx = (int)g.nx;
+  if (ny) *ny = (int)g.ny;
+  if (nz) *nz = (int)g.nz;
+  return RFLBM_OK;
+}
+
 int rflbm_batch_init_rest(rflbm_batch_t* b) {
   if (!b) return bfail(RFLBM_EINVAL, "batch handle is NULL");
   for (auto& d : b->host) {
@@ -848,7 +857,7 @@ int rflbm_batch_stats(rflbm_batch_t* b, int r, rflbm_stats_t* out) {
   out->momentum[2] = host[3];
   out->max_speed = host[4];
   out->nonfinite = (int64_t)host[5];
-  if (out->nonfinite > 0) return bfail(RFLBM_EUNSTABLE, "replica %d holds non-finite values", r);
+  if (out->nonfinite > 0) return bfail(RFLBM_EUNSTABLE, "replica %d holds unstable sites (non-finite values or non-positive densities)", r);
   return RFLBM_OK;
 }
 

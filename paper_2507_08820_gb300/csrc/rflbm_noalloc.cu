@@ -9,17 +9,19 @@
 // kNoAllocScratchBytes (about 512 KB) until the process exits.
 //
 // The reduction is the same as rflbm_stats (FP64 sums of density and momentum, maximum
-// speed, non-finite sites), applied to populations in the public layout (27 planes of
-// n_sites float32 values) rather than to a handle's internal storage. Each block of 256
-// threads reduces a fixed chunk of kNoAllocChunk sites into one partial (deterministic for
-// a given n_sites); the last block to finish sums the partials in a fixed order.
+// speed, unstable sites), applied to populations in the public layout (27 planes of
+// n_sites float32 values) rather than to a handle's internal storage. Like rflbm_stats it
+// sums the populations shifted by the rest state of unit density, f_i - w_i (the shift
+// cancels in the momentum, and sum_i w_i = 1 restores the density), so the per-site
+// float32 sums keep the relative precision of the fluctuations. Each block of 256 threads
+// reduces a fixed chunk of kNoAllocChunk sites into one partial (deterministic for a given
+// n_sites); the last block to finish sums the partials in a fixed order.
 //
 // The scratch is shared by all calls in the process: calls that overlap on the GPU (two
 // streams, or two host threads at once) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "../../include/rflbm.h"
 #include "rflbm_internal.h"
@@ -51,39 +53,29 @@ __device__ __forceinline__ double na_warp_max(double v) {
   return v;
 }
 
-// c_x, c_y, c_z of population i in the public order (see rflbm.h).
-__device__ __forceinline__ void na_velocity(int i, int& cx, int& cy, int& cz) {
-  constexpr int tx[27] = {0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 0, 0, 0, 0, 1, 1, 1, 1, -1, -1, -1, -1};
-  constexpr int ty[27] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1, 1, 1, -1, -1};
-  constexpr int tz[27] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 1, -1, 1, -1, 1, -1, 1, -1};
-  cx = tx[i];
-  cy = ty[i];
-  cz = tz[i];
-}
-
 __global__ void __launch_bounds__(kNaThreads) k_stats_noalloc(const float* __restrict__ f,
                                                               int64_t n, double* scratch) {
   double acc[kNaFields] = {0, 0, 0, 0, 0, 0};
   const int64_t begin = (int64_t)blockIdx.x * kNoAllocChunk;
   const int64_t end = begin + kNoAllocChunk < n ? begin + kNoAllocChunk : n;
   for (int64_t s = begin + threadIdx.x; s < end; s += kNaThreads) {
-    float rho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 27; ++i) {
-      int cx, cy, cz;
-      na_velocity(i, cx, cy, cz);
-      const float v = __ldg(f + i * n + s);
-      rho += v;
-      jx += cx * v;
-      jy += cy * v;
-      jz += cz * v;
+    for (int i = 0; i < rflbm_dev::kQ; ++i) {
+      const float v = __ldg(f + i * n + s) - (float)rflbm_dev::weight_of(i);
+      drho += v;
+      if (rflbm_dev::cx_of(i)) jx += rflbm_dev::cx_of(i) * v;
+      if (rflbm_dev::cy_of(i)) jy += rflbm_dev::cy_of(i) * v;
+      if (rflbm_dev::cz_of(i)) jz += rflbm_dev::cz_of(i) * v;
     }
-    if (isfinite(rho) && isfinite(jx) && isfinite(jy) && isfinite(jz)) {
-      acc[0] += rho;
+    const float rho = 1.0f + drho;
+    // a non-finite site, or one whose density is not positive, counts as unstable
+    if (isfinite(drho) && isfinite(jx) && isfinite(jy) && isfinite(jz) && rho > 0.0f) {
+      acc[0] += drho;
       acc[1] += jx;
       acc[2] += jy;
       acc[3] += jz;
-      acc[4] = fmax(acc[4], (double)(sqrtf(jx * jx + jy * jy + jz * jz) / fabsf(rho)));
+      acc[4] = fmax(acc[4], (double)(sqrtf(jx * jx + jy * jy + jz * jz) / rho));
     } else {
       acc[5] += 1.0;
     }
@@ -126,11 +118,6 @@ __global__ void __launch_bounds__(kNaThreads) k_stats_noalloc(const float* __res
   if (threadIdx.x == 0) *counter = 0u;  // ready for the next call
 }
 
-// Per-device address of the scratch array, looked up once per device.
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double* g_scratch_ptr[kMaxDevices] = {};
-
 int na_fail(int code, const char* msg, cudaError_t e = cudaSuccess) {
   return rflbm_dev::record_error(code, msg, e == cudaSuccess ? nullptr : cudaGetErrorString(e));
 }
@@ -147,23 +134,14 @@ extern "C" int rflbm_stats_f32_noalloc(const float* f, int64_t n_sites, void* st
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_fail(RFLBM_ECUDA, "rflbm_stats_f32_noalloc: no current device", e);
-  if (dev < 0 || dev >= kMaxDevices) return na_fail(RFLBM_EINVAL, "rflbm_stats_f32_noalloc: device ordinal too large");
-  double* scratch = nullptr;
-  {
-    // set-up, once per device, with that device current: the device address of the
-    // static scratch array (the host-side symbol is not a device address) and a cleared
-    // completion counter
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return na_fail(RFLBM_ECUDA, "rflbm_stats_f32_noalloc: cudaGetSymbolAddress failed", e);
-      e = cudaMemset((char*)p + (size_t)(kNoAllocMaxBlocks + 1) * kSlot * sizeof(double), 0, sizeof(double));
-      if (e != cudaSuccess) return na_fail(RFLBM_ECUDA, "rflbm_stats_f32_noalloc: clearing the counter failed", e);
-      g_scratch_ptr[dev] = (double*)p;
-    }
-    scratch = g_scratch_ptr[dev];
-  }
+  // the device address of the static scratch array on the current device (the host-side
+  // symbol is not a device address). Looked up on every call: it allocates nothing, and a
+  // cached address would go stale if the caller reset the device (cudaDeviceReset recreates
+  // the module's static memory).
+  void* sym = nullptr;
+  e = cudaGetSymbolAddress(&sym, g_noalloc_scratch);
+  if (e != cudaSuccess) return na_fail(RFLBM_ECUDA, "rflbm_stats_f32_noalloc: cudaGetSymbolAddress failed", e);
+  double* const scratch = static_cast<double*>(sym);
   cudaStream_t st = (cudaStream_t)stream;
   double* counter = scratch + (int64_t)(kNoAllocMaxBlocks + 1) * kSlot;
   double* result = scratch + (int64_t)kNoAllocMaxBlocks * kSlot;
@@ -179,12 +157,12 @@ extern "C" int rflbm_stats_f32_noalloc(const float* f, int64_t n_sites, void* st
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return na_fail(RFLBM_ECUDA, "rflbm_stats_f32_noalloc: reduction failed", e);
   out->step = 0;
-  out->mass = host[0];
+  out->mass = (double)n_sites + host[0];  // sum_s rho = N + sum_s sum_i (f_i - w_i)
   out->momentum[0] = host[1];
   out->momentum[1] = host[2];
   out->momentum[2] = host[3];
   out->max_speed = host[4];
   out->nonfinite = (int64_t)host[5];
-  if (out->nonfinite > 0) return na_fail(RFLBM_EUNSTABLE, "rflbm_stats_f32_noalloc: non-finite populations");
+  if (out->nonfinite > 0) return na_fail(RFLBM_EUNSTABLE, "rflbm_stats_f32_noalloc: non-finite or non-positive densities");
   return RFLBM_OK;
 }

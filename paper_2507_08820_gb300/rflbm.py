@@ -115,6 +115,8 @@ _sig = {
     "rflbm_batch_destroy": (None, [_H]),
     "rflbm_batch_tuning": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "rflbm_batch_launches_per_step": (C.c_int, [_H]),
+    "rflbm_batch_replica_dims": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                           C.POINTER(C.c_int)]),
     "rflbm_batch_init_rest": (C.c_int, [_H]),
     "rflbm_batch_run": (C.c_int, [_H, C.c_int64]),
     "rflbm_batch_synchronize": (C.c_int, [_H]),
@@ -136,19 +138,38 @@ def _check(status):
     return status
 
 
-def _ptr(a, dtype=None):
-    """(pointer, on_device) of a numpy array or a CUDA tensor; None -> (None, 0)."""
+_TORCH_DTYPE = {np.dtype(np.float32): "torch.float32", np.dtype(np.float64): "torch.float64"}
+
+
+def _ptr(a, dtype=None, count=None):
+    """(pointer, on_device) of a numpy array or a CUDA tensor; None -> (None, 0).
+
+    dtype: the element type the C function reads or writes (numpy dtype); count: the
+    number of elements it touches. Both are checked before any pointer reaches the
+    library, so a wrong element type or a short buffer raises ValueError here instead of
+    letting a kernel run past the end of the allocation."""
     if a is None:
         return None, 0
     if hasattr(a, "data_ptr"):
         if not a.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if dtype is not None and str(a.dtype) != _TORCH_DTYPE[np.dtype(dtype)]:
+            raise ValueError(f"expected a tensor of {_TORCH_DTYPE[np.dtype(dtype)]}, got {a.dtype}")
+        if count is not None and a.numel() < count:
+            raise ValueError(f"tensor holds {a.numel()} elements, the call needs {count}")
         return a.data_ptr(), 1 if a.is_cuda else 0
     if not isinstance(a, np.ndarray) or not a.flags.c_contiguous:
         raise ValueError("expected a C-contiguous numpy array or a torch tensor")
     if dtype is not None and a.dtype != dtype:
         raise ValueError(f"expected dtype {np.dtype(dtype)}, got {a.dtype}")
+    if count is not None and a.size < count:
+        raise ValueError(f"array holds {a.size} elements, the call needs {count}")
     return a.ctypes.data, 0
+
+
+def _sites(h):
+    nx, ny, nz = rflbm_get_dims(h)
+    return nx * ny * nz
 
 
 def _same_side(*pairs):
@@ -204,7 +225,8 @@ def rflbm_init_thermal(h):
 
 
 def rflbm_init_field(h, rho=None, u=None):
-    pr, pu = _ptr(rho, np.float64), _ptr(u, np.float64)
+    n = _sites(h)
+    pr, pu = _ptr(rho, np.float64, n), _ptr(u, np.float64, 3 * n)
     return _check(lib.rflbm_init_field(h, pr[0], pu[0], _same_side(pr, pu)))
 
 
@@ -213,7 +235,8 @@ def rflbm_step(h, n=1):
 
 
 def rflbm_moments(h, rho=None, u=None, pi=None):
-    ps = [_ptr(a, np.float64) for a in (rho, u, pi)]
+    n = _sites(h)
+    ps = [_ptr(a, np.float64, k * n) for a, k in ((rho, 1), (u, 3), (pi, 6))]
     return _check(lib.rflbm_moments(h, ps[0][0], ps[1][0], ps[2][0], _same_side(*ps)))
 
 
@@ -226,28 +249,28 @@ def rflbm_stats(h):
 
 
 def rflbm_get_populations(h, f):
-    p, d = _ptr(f, np.float64)
+    p, d = _ptr(f, np.float64, 27 * _sites(h))
     return _check(lib.rflbm_get_populations(h, p, d))
 
 
 def rflbm_get_populations_f32(h, f):
-    p, d = _ptr(f, np.float32)
+    p, d = _ptr(f, np.float32, 27 * _sites(h))
     return _check(lib.rflbm_get_populations_f32(h, p, d))
 
 
 def rflbm_set_populations(h, f):
-    p, d = _ptr(f, np.float64)
+    p, d = _ptr(f, np.float64, 27 * _sites(h))
     return _check(lib.rflbm_set_populations(h, p, d))
 
 
 def rflbm_set_populations_f32(h, f):
-    p, d = _ptr(f, np.float32)
+    p, d = _ptr(f, np.float32, 27 * _sites(h))
     return _check(lib.rflbm_set_populations_f32(h, p, d))
 
 
 def rflbm_get_sites(h, sites, out):
     sites = np.ascontiguousarray(sites, dtype=np.int64)
-    p, _ = _ptr(out, np.float64)
+    p, _ = _ptr(out, np.float64, 27 * sites.size)
     return _check(lib.rflbm_get_sites(h, sites.ctypes.data, sites.size, p))
 
 
@@ -255,12 +278,20 @@ def rflbm_state_bytes(h):
     return _check(lib.rflbm_state_bytes(h))
 
 
+def _image_bytes(image):
+    return image.numel() * image.element_size() if hasattr(image, "data_ptr") else image.nbytes
+
+
 def rflbm_save_state(h, image):
+    if _image_bytes(image) < rflbm_state_bytes(h):
+        raise ValueError("the image buffer is smaller than rflbm_state_bytes")
     p, d = _ptr(image)
     return _check(lib.rflbm_save_state(h, p, d))
 
 
 def rflbm_load_state(h, image):
+    if _image_bytes(image) < rflbm_state_bytes(h):
+        raise ValueError("the image buffer is smaller than rflbm_state_bytes")
     p, d = _ptr(image)
     return _check(lib.rflbm_load_state(h, p, d))
 
@@ -353,11 +384,15 @@ def rflbm_stats_f32_noalloc(f, n_sites, stream=None):
     """Diagnostics of caller-owned float32 populations (a CUDA tensor of 27 * n_sites
     values, public layout) with the library's fixed scratch area: nothing is allocated.
     Returns (stats, status) like rflbm_stats."""
-    p, d = _ptr(f, np.float32)
+    n_sites = int(n_sites)
+    if n_sites > RFLBM_STATS_NOALLOC_MAX_SITES:  # the library rejects it before any launch
+        p, d = _ptr(f, np.float32)
+    else:
+        p, d = _ptr(f, np.float32, 27 * max(n_sites, 0))
     if not d:
         raise ValueError("populations must be in device memory")
     st = rflbm_stats_t()
-    status = lib.rflbm_stats_f32_noalloc(p, int(n_sites), stream, C.byref(st))
+    status = lib.rflbm_stats_f32_noalloc(p, n_sites, stream, C.byref(st))
     if status < 0 and status != RFLBM_EUNSTABLE:
         _check(status)
     return st, status
@@ -389,6 +424,17 @@ def rflbm_batch_tuning(b):
     return t.value, c.value, n.value
 
 
+def rflbm_batch_replica_dims(b, r):
+    nx, ny, nz = C.c_int(), C.c_int(), C.c_int()
+    _check(lib.rflbm_batch_replica_dims(b, int(r), C.byref(nx), C.byref(ny), C.byref(nz)))
+    return nx.value, ny.value, nz.value
+
+
+def _batch_sites(b, r):
+    nx, ny, nz = rflbm_batch_replica_dims(b, r)
+    return nx * ny * nz
+
+
 def rflbm_batch_init_rest(b):
     return _check(lib.rflbm_batch_init_rest(b))
 
@@ -402,7 +448,7 @@ def rflbm_batch_synchronize(b):
 
 
 def rflbm_batch_get_populations(b, r, f):
-    p, _ = _ptr(f, np.float64)
+    p, _ = _ptr(f, np.float64, 27 * _batch_sites(b, r))
     return _check(lib.rflbm_batch_get_populations(b, int(r), p))
 
 

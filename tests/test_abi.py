@@ -92,3 +92,29 @@ def test_null_handle_is_rejected(lib):
         R.rflbm_step(None, 1)
     assert e.value.status == R.RFLBM_EINVAL
     assert "NULL" in R.rflbm_last_error()
+
+
+def test_binding_rejects_wrong_dtype_and_short_buffers_before_any_launch(lib):
+    """A tensor of the wrong element type, or one shorter than the call touches, raises
+    ValueError in the binding: no pointer reaches a kernel that would run past the end of
+    the allocation."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    from paper_2507_08820_gb300 import rflbm as R
+    with pytest.raises(ValueError):
+        R._ptr(torch.zeros(64, dtype=torch.float16), np.float32)
+    with pytest.raises(ValueError):
+        R._ptr(torch.zeros(64, dtype=torch.float32), np.float64)
+    with pytest.raises(ValueError):
+        R._ptr(torch.zeros(26, dtype=torch.float32), np.float32, 27)
+    with pytest.raises(ValueError):
+        R._ptr(np.zeros(26, dtype=np.float64), np.float64, 27)
+    with pytest.raises(ValueError):
+        R._ptr(np.zeros(27, dtype=np.float32), np.float64, 27)
+    assert R._ptr(np.zeros(27), np.float64, 27)[1] == 0
+    assert R._ptr(torch.zeros(27, dtype=torch.float64), np.float64, 27)[1] == 0
+    # the allocation-free diagnostics: float16 populations, or fewer than 27 n values
+    with pytest.raises(ValueError):
+        R.rflbm_stats_f32_noalloc(torch.zeros(27 * 10, dtype=torch.float16), 10)
+    with pytest.raises(ValueError):
+        R.rflbm_stats_f32_noalloc(torch.zeros(27 * 10 - 1, dtype=torch.float32), 10)

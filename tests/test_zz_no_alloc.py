@@ -5,7 +5,9 @@ framework has already reserved the device memory for its own pool, or they run a
 between the steps of another solver): it reduces caller-owned float32 populations with a
 fixed scratch area in the library's static device memory. Here it must agree with
 rflbm_stats, which uses scratch allocated with its handle, on two different states in
-consecutive calls, within the tests' relative tolerance of 1e-5.
+consecutive calls, within the tests' relative tolerance of 1e-5; repeated calls must leave
+the device's free memory unchanged; and a site of negative density must count as unstable
+in both reductions.
 """
 import numpy as np
 import pytest
@@ -33,9 +35,7 @@ def _agree(a, b):
     assert abs(a.max_speed - b.max_speed) <= RTOL * b.max_speed
 
 
-def test_noalloc_stats_match_handle_stats_on_two_calls(R):
-    import torch
-    shape = (64, 48, 40)  # 122880 sites: eight partial sums of the fixed scratch
+def _box_state(R, shape):
     n = int(np.prod(shape))
     g = np.random.default_rng(3)
     rho = 1.0 + 0.01 * g.uniform(-1, 1, n)
@@ -44,6 +44,13 @@ def test_noalloc_stats_match_handle_stats_on_two_calls(R):
     u += 0.005 * g.uniform(-1, 1, (3, n))
     box = R.Box(*shape, tau=0.8, kT=1e-4, seed=4)
     R.rflbm_init_field(box.h, rho, np.ascontiguousarray(u))
+    return box, n
+
+
+def test_noalloc_stats_match_handle_stats_on_two_calls(R):
+    import torch
+    shape = (64, 48, 40)  # 122880 sites: eight partial sums of the fixed scratch
+    box, n = _box_state(R, shape)
     f = torch.empty((27, n), dtype=torch.float32, device="cuda")
     for steps in (2, 3):  # two consecutive calls on two different states
         R.rflbm_step(box.h, steps)
@@ -54,6 +61,48 @@ def test_noalloc_stats_match_handle_stats_on_two_calls(R):
         got, status = R.rflbm_stats_f32_noalloc(f, n)
         assert status == R.RFLBM_OK
         _agree(got, ref)
+    box.close()
+
+
+def test_noalloc_stats_leave_free_device_memory_unchanged(R):
+    """The property the entry point exists for: after a first call, further calls do not
+    change the driver's count of free device memory (which also sees allocations made
+    outside PyTorch's caching allocator)."""
+    import torch
+    shape = (32, 32, 32)
+    box, n = _box_state(R, shape)
+    f = torch.empty((27, n), dtype=torch.float32, device="cuda")
+    R.rflbm_get_populations_f32(box.h, f)
+    torch.cuda.synchronize()
+    R.rflbm_stats_f32_noalloc(f, n)
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        got, status = R.rflbm_stats_f32_noalloc(f, n)
+        assert status == R.RFLBM_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    box.close()
+
+
+def test_non_positive_density_site_counts_as_unstable(R):
+    """A finite site whose 27 populations sum to a negative density is reported as
+    unstable by both reductions, and its |j| / rho does not enter max_speed."""
+    import torch
+    shape = (32, 8, 8)
+    box, n = _box_state(R, shape)
+    fh = box.populations()
+    fh[:, 77] = 0.0
+    fh[0, 77] = -1e-3  # rho = -1e-3 with momentum 2e-3 along x
+    fh[1, 77] = 1e-3
+    fh[2, 77] = -1e-3
+    R.rflbm_set_populations(box.h, np.ascontiguousarray(fh))
+    ref, status = R.rflbm_stats(box.h)
+    assert status == R.RFLBM_EUNSTABLE and ref.nonfinite == 1
+    assert ref.max_speed < 1.0
+    f = torch.tensor(fh, dtype=torch.float32, device="cuda").contiguous()
+    got, status = R.rflbm_stats_f32_noalloc(f, n)
+    assert status == R.RFLBM_EUNSTABLE and got.nonfinite == 1
+    assert got.max_speed < 1.0
     box.close()
 
 
