@@ -78,7 +78,7 @@ def workload(args):
             "storage": f"{args.storage} shifted by w_i rho0",
             "streaming": "pull, ping-pong" if nbuf == 2 else "AA, one buffer in place",
             "l2": f"inputs {nbytes / 1e6:.0f} MB ({nbuf} population buffer{'s' if nbuf == 2 else ''})"
-                  " > 129 MB L2, no flush",
+                  + (" > 129 MB L2, no flush" if nbytes > 129e6 else " fit in the 129 MB L2"),
             "parallelism": "replicas"}
 
 
@@ -248,40 +248,85 @@ def device_uuid(torch):
 
 
 # ------------------------------------------------------------------ CPU oracle timing
-def oracle_sample_rate(edge, tau, kT, budget_s, min_sites=64, max_sites=None, steps=None):
-    """Times the FP64 oracle's per-site collision plus streaming on sampled sites of the
-    same box in a single-threaded subprocess; returns (MLUPS, sites, steps, seconds)."""
-    code = f"""
-import os, sys, time, json
-sys.path.insert(0, {ROOT!r})
+# One oracle worker: imports, calibrates its per-site cost, waits for the common start
+# time, then collides and streams its own chunk of the box's sites (every `workers`-th site,
+# starting at its index) for the given number of steps in one thread.
+_ORACLE_WORKER = r"""
+import json, sys, time
+cfg = json.loads(sys.argv[1])
+sys.path.insert(0, cfg["root"])
 import numpy as np
 from oracle import rflbm_oracle as o
 from paper_2507_08820_gb300 import workloads as W
-edge, tau, kT, budget = {edge}, {tau}, {kT}, {budget_s}
-n = edge ** 3
-# calibrate on a small sample, then size the per-step sample to the budget
+n, k, workers = cfg["edge"] ** 3, cfg["index"], cfg["workers"]
 f = o.rest_state(512) + W.population_perturbation(512, 3, 1e-4)
-t0 = time.perf_counter(); o.collide(f, tau, kT, 1, 0, np.arange(512, dtype=np.uint64)); dt = time.perf_counter() - t0
-per_site = dt / 512
-steps = {steps if steps else 0} or 3
-m = int(budget / steps / per_site)
-m = max({min_sites}, min(m, {max_sites if max_sites else 'n'}, n))
-sites = W.sample_sites(n, m, 7)
-f = o.rest_state(sites.size) + W.population_perturbation(sites.size, 5, 1e-4)
-t0 = time.perf_counter()
+t0 = time.perf_counter(); o.collide(f, cfg["tau"], cfg["kT"], 1, 0, np.arange(512, dtype=np.uint64))
+per_site = (time.perf_counter() - t0) / 512
+chunk = np.arange(k, n, workers, dtype=np.int64)
+steps = cfg["steps"] or 2  # None: at least two steps, more while the budget allows
+m = int(cfg["budget"] / steps / per_site)
+m = max(min(cfg["min_sites"], chunk.size), min(m, chunk.size))
+if not cfg["steps"]:
+    steps = max(2, int(cfg["budget"] / (m * per_site)))
+sites = chunk[:m]
+f = o.rest_state(sites.size) + W.population_perturbation(sites.size, 5 + k, 1e-4)
+while time.time() < cfg["t_go"]:
+    time.sleep(0.005)
+t0 = time.time()
 for t in range(steps):
-    fs = o.collide(f, tau, kT, 1, t, sites.astype(np.uint64))
+    fs = o.collide(f, cfg["tau"], cfg["kT"], 1, t, sites.astype(np.uint64))
     f = o.stream(fs, (sites.size, 1, 1))
-el = time.perf_counter() - t0
-print(json.dumps(dict(mlups=sites.size * steps / el / 1e6, sites=int(sites.size), steps=steps, seconds=el)))
+t1 = time.time()
+print(json.dumps(dict(sites=int(sites.size), steps=steps, t0=t0, t1=t1)))
 """
+
+
+def host_cores():
+    """Host cores this process may use (the affinity mask where the OS reports one)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_rate(edge, tau, kT, budget_s, steps, workers=None, min_sites=16):
+    """Times the FP64 oracle's per-site collision plus streaming on a bounded sample of the
+    box's sites, on every host core: one single-threaded worker process per core, each on
+    its own chunk of sites (every `workers`-th site), all starting at one agreed wall-clock
+    time. Each worker's sample is sized so that its `steps` steps take about `budget_s`
+    seconds (steps=None: at least two, more while the budget allows). Returns dict(mlups,
+    sites, steps, seconds, workers): site updates of all workers over the wall time from
+    the first start to the last finish."""
+    workers = workers or host_cores()
+    t_go = time.time() + 3.0 + 0.2 * workers  # after every worker's imports and calibration
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         timeout=max(600, 20 * budget_s))
-    if res.returncode != 0:
-        raise RuntimeError("oracle timing failed:\n" + res.stderr[-2000:])
-    return json.loads(res.stdout.strip().splitlines()[-1])
+    procs = []
+    for k in range(workers):
+        cfg = dict(root=ROOT, edge=edge, tau=tau, kT=kT, budget=budget_s, steps=steps, index=k,
+                   workers=workers, min_sites=min_sites, t_go=t_go)
+        procs.append(subprocess.Popen([sys.executable, "-c", _ORACLE_WORKER, json.dumps(cfg)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env))
+    results = []
+    for p in procs:
+        out, err = p.communicate(timeout=max(600, 20 * budget_s))
+        if p.returncode != 0:
+            raise RuntimeError("oracle timing failed:\n" + err[-2000:])
+        results.append(json.loads(out.strip().splitlines()[-1]))
+    wall = max(r["t1"] for r in results) - min(r["t0"] for r in results)
+    updates = sum(r["sites"] * r["steps"] for r in results)
+    return dict(mlups=updates / wall / 1e6, sites=sum(r["sites"] for r in results),
+                steps=max(r["steps"] for r in results), seconds=wall, workers=workers)
+
+
+def cpu_baseline_entry(r, edge, per_step):
+    """The cpu_baseline object of a JSON line from an oracle_sample_rate result."""
+    return {"value": r["mlups"], "unit": "MLUPS", "cores": r["workers"], "nproc": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle collision + streaming of {r['sites']} sampled sites of the "
+                      f"{edge}^3 box{' per step' if per_step else ''}, {r['steps']} steps, "
+                      f"{r['seconds']:.1f} s, {r['workers']} single-threaded processes "
+                      f"(one per host core, each on its own chunk of sites)"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -290,21 +335,17 @@ def reference_arm(args):
     info = dist.rank_info()
     if info.rank != 0:
         return 0
-    # each of the warmup + steps "steps" collides a bounded sample of the box's sites;
-    # the whole run is held to about two minutes of CPU
+    # each of the warmup + steps "steps" collides a bounded sample of the box's sites on
+    # every host core; the whole run is held to about two minutes
     total = max(1, args.steps + args.warmup)
-    r = oracle_sample_rate(args.edge, args.tau, args.kT, budget_s=min(120.0, 2.0 * total),
-                           min_sites=16, steps=total)
+    r = oracle_sample_rate(args.edge, args.tau, args.kT, budget_s=min(120.0, 2.0 * total), steps=total)
     line = {
         "impl": "reference", "metric": METRIC, "value": r["mlups"], "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * r["seconds"] / r["steps"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload(args),
-        "cpu_baseline": {"value": r["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"FP64 oracle collision + streaming of {r['sites']} sampled "
-                                   f"sites of the {args.edge}^3 box per step, {r['steps']} steps, "
-                                   f"{r['seconds']:.1f} s, one thread"},
+        "cpu_baseline": cpu_baseline_entry(r, args.edge, True),
         "e2e": {"value": r["mlups"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -392,6 +433,116 @@ def ensemble_arm(args):
     return 0
 
 
+def init_taylor_green(R, torch, box, e, dev, u0=0.01):
+    """The Taylor-Green vortex u0 (-cos kx sin ky, sin kx cos ky, 0), k = 2 pi / e, with its
+    incompressible pressure as density (the workloads module's fields), built on the device
+    (the host would need 4 N doubles) and loaded as the equilibrium of Eq. 26."""
+    import numpy as np
+    k = 2.0 * np.pi / e
+    x = torch.arange(e, dtype=torch.float64, device=dev)
+    cx, sx = torch.cos(k * x), torch.sin(k * x)
+    u = torch.zeros((3, e, e, e), dtype=torch.float64, device=dev)  # (3, z, y, x)
+    u[0] = -u0 * (cx[None, None, :] * sx[None, :, None])
+    u[1] = u0 * (sx[None, None, :] * cx[None, :, None])
+    c2 = torch.cos(2 * k * x)
+    rho = 1.0 - u0 ** 2 * 3.0 / 4.0 * (c2[None, None, :] + c2[None, :, None]).expand(e, e, e)
+    rho = rho.contiguous()
+    R.rflbm_init_field(box.h, rho, u)
+    torch.cuda.synchronize()
+    del u, rho
+    torch.cuda.empty_cache()
+
+
+def time_variant(R, torch, stream, shape, k, peak, bps, init="rest", warm=3, **kw):
+    """MLUPS and roofline fraction of one configuration: a box of its own (freed before the
+    next), `warm` untimed steps (the first AA step reveals the odd-step form), then k steps
+    timed with CUDA events on the launching stream."""
+    e = shape[0]
+    vb = R.Box(*shape, tau=kw.pop("tau", 0.8), seed=1, stream=stream.cuda_stream, **kw)
+    try:
+        if init == "rest":
+            R.rflbm_init_rest(vb.h)
+        else:
+            init_taylor_green(R, torch, vb, e, torch.device("cuda", torch.cuda.current_device()))
+        kind, path = R.rflbm_step_path(vb.h)
+        pairs = R.rflbm_step_sites_per_thread(vb.h)
+        R.rflbm_step(vb.h, 1)
+        odd_pairs = R.rflbm_step_sites_per_thread(vb.h)
+        R.rflbm_step(vb.h, max(0, warm - 1))
+        R.rflbm_synchronize(vb.h)
+        vms = time_steps(R, torch, vb, stream, k)
+        st, status = R.rflbm_stats(vb.h)
+        n = vb.n
+        pattern = "aa" if kw.get("pattern") == R.RFLBM_PATTERN_AA else "pingpong"
+        storage = {R.RFLBM_STORE_F32: "f32", R.RFLBM_STORE_F16: "f16",
+                   R.RFLBM_STORE_BF16: "bf16"}[kw.get("storage", R.RFLBM_STORE_F32)]
+        kname, _ = kernel_name(kind, path, kw.get("kT", 0.0), kw.get("model", 0), storage, pattern,
+                               pairs, odd_pairs)
+        sites_s = n * k / (vms * 1e-3)
+        return {"value": sites_s / 1e6, "unit": "MLUPS", "steps": k, "box": list(shape),
+                "ms_per_step": vms / k, "roofline_frac": bps * sites_s / 1e9 / peak,
+                "bytes_per_site": bps, "kernel": kname, "init": init,
+                "finite_after": bool(status == R.RFLBM_OK)}
+    finally:
+        vb.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+
+def storage_accuracy(R, torch, stream, edge=128, steps=20, tau=0.8, kT=1e-4):
+    """Error of each storage format "at fixed FDT error": from the same thermal initial
+    state (rflbm_init_thermal draws it identically in every format), `steps` steps of each
+    format; rho, u and Pi of every site against the float32 run, as RMS and maximum in units
+    of each field's thermal standard deviation (float32 itself is within 2.2e-7 RMS of the
+    FP64 oracle in the parity tests), and the largest deviation of the 27 per-site mode
+    variances from the fluctuation-dissipation value rho0 kT b_k / cs2 (Sec. II.A)."""
+    import numpy as np
+    n = edge ** 3
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cs2 = 1.0 / 3.0
+    # thermal standard deviations of rho, u_a, Pi_aa, Pi_ab at rho0 = 1
+    sd = [np.sqrt(kT / cs2)] + [np.sqrt(kT)] * 3 + [np.sqrt(2 * kT * cs2)] * 3 + [np.sqrt(kT * cs2)] * 3
+    fields, out = {}, {}
+    for name, st in (("f32", R.RFLBM_STORE_F32), ("f16", R.RFLBM_STORE_F16), ("bf16", R.RFLBM_STORE_BF16)):
+        box = R.Box(edge, edge, edge, tau=tau, kT=kT, seed=1, stream=stream.cuda_stream, storage=st)
+        R.rflbm_init_thermal(box.h)
+        R.rflbm_step(box.h, steps)
+        rho = torch.empty(n, dtype=torch.float64, device=dev)
+        u = torch.empty((3, n), dtype=torch.float64, device=dev)
+        pi = torch.empty((6, n), dtype=torch.float64, device=dev)
+        R.rflbm_moments(box.h, rho, u, pi)
+        s1, s2 = R.rflbm_mode_sums(box.h)
+        box.close()
+        var = s2 / n - (s1 / n) ** 2
+        ratio = var / (kT * mode_norms() / cs2)
+        fields[name] = torch.cat([rho[None], u, pi])
+        entry = {"fdt_mode_variance_max_dev": float(np.max(np.abs(ratio - 1.0))),
+                 "fdt_mode_variance_mean": float(np.mean(ratio))}
+        if name != "f32":
+            d = (fields[name] - fields["f32"]).abs() / torch.tensor(sd, dtype=torch.float64, device=dev)[:, None]
+            entry["vs_f32_rms_in_thermal_sd"] = float(torch.sqrt((d * d).mean()))
+            entry["vs_f32_max_in_thermal_sd"] = float(d.max())
+        out[name] = entry
+        del rho, u, pi
+    del fields
+    torch.cuda.empty_cache()
+    return {"workload": f"{edge}^3 thermal initial state, tau {tau}, kT {kT:g}, {steps} steps, seed 1",
+            "fields": "rho, u, Pi per site", **out}
+
+
+def mode_norms():
+    """b_k of the 27 modes of Table II (products of the 1-D norms 1, 1/3, 2/9 over the
+    Hermite exponents of each mode, in the order rflbm_mode_sums reports)."""
+    import numpy as np
+    beta = (1.0, 1.0 / 3.0, 2.0 / 9.0)
+    # Table II order: exponent triples (p, q, r) per mode k
+    pqr = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0),
+           (1, 0, 1), (0, 1, 1), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 0, 2), (0, 1, 2), (0, 2, 1),
+           (1, 1, 1), (2, 2, 0), (2, 0, 2), (0, 2, 2), (1, 1, 2), (1, 2, 1), (2, 1, 1), (2, 1, 2),
+           (2, 2, 1), (1, 2, 2), (2, 2, 2)]
+    return np.array([beta[p] * beta[q] * beta[r] for p, q, r in pqr])
+
+
 def gb300_arm(args):
     import numpy as np
     import torch
@@ -417,20 +568,7 @@ def gb300_arm(args):
     if args.init == "rest":
         R.rflbm_init_rest(box.h)
     else:
-        # Taylor-Green fields built on the device (the host would need 4 N doubles)
-        k = 2.0 * np.pi / e
-        x = torch.arange(e, dtype=torch.float64, device=dev)
-        cx, sx = torch.cos(k * x), torch.sin(k * x)
-        u = torch.zeros((3, e, e, e), dtype=torch.float64, device=dev)  # (3, z, y, x)
-        u[0] = -0.01 * (cx[None, None, :] * sx[None, :, None])
-        u[1] = 0.01 * (sx[None, None, :] * cx[None, :, None])
-        c2 = torch.cos(2 * k * x)
-        rho = 1.0 - 0.01 ** 2 * 3.0 / 4.0 * (c2[None, None, :] + c2[None, :, None]).expand(e, e, e)
-        rho = rho.contiguous()
-        R.rflbm_init_field(box.h, rho, u)
-        torch.cuda.synchronize()
-        del u, rho
-        torch.cuda.empty_cache()
+        init_taylor_green(R, torch, box, e, dev)
     kind, path = R.rflbm_step_path(box.h)
     pairs = R.rflbm_step_sites_per_thread(box.h)
     odd_pairs = pairs
@@ -439,67 +577,74 @@ def gb300_arm(args):
         R.rflbm_step(box.h, 1)
         odd_pairs = R.rflbm_step_sites_per_thread(box.h)
         warm -= 1
-    R.rflbm_step(box.h, warm)
     R.rflbm_synchronize(box.h)
 
     sampler = ClockSampler(device_uuid(torch))
-    dist.barrier(info, info.local_rank)
-    torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)  # let the sampler take its first reading
+    # the warm-up steps run directly before the timed region, so that the GPU enters it busy
+    R.rflbm_step(box.h, warm)
+    R.rflbm_synchronize(box.h)
+    dist.barrier(info, info.local_rank)
+    torch.cuda.synchronize()
     ms = time_steps(R, torch, box, stream, args.steps)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     dist.barrier(info, info.local_rank)
     ms_max = dist.max_over_ranks(info, ms, dev)
+    launches = R.rflbm_launches_per_step(box.h) * args.steps
     st, status = R.rflbm_stats(box.h)
 
-    # end to end through the ABI with host buffers: pinned populations in, stats out
+    # end to end through the ABI with host buffers: every step imports the populations from
+    # page-locked host memory, steps, and exports the step's result (the populations) back
     e2e = None
     if not args.no_e2e:
         k_e2e = max(3, min(args.steps, 2000) // 10)
-        host = torch.empty((27, n), dtype=torch.float32).pin_memory()
-        R.rflbm_get_populations_f32(box.h, host)
-        R.rflbm_set_populations_f32(box.h, host)   # untimed: allocates the staging buffer
+        host_in = torch.empty((27, n), dtype=torch.float32).pin_memory()
+        host_out = torch.empty((27, n), dtype=torch.float32).pin_memory()
+        R.rflbm_get_populations_f32(box.h, host_in)
+        R.rflbm_set_populations_f32(box.h, host_in)   # untimed: allocates the staging buffer
         dist.barrier(info, info.local_rank)
         t0 = time.perf_counter()
         for _ in range(k_e2e):
-            R.rflbm_set_populations_f32(box.h, host)
+            R.rflbm_set_populations_f32(box.h, host_in)
             R.rflbm_step(box.h, 1)
-            R.rflbm_stats(box.h)
+            R.rflbm_get_populations_f32(box.h, host_out)
         e2e_s = dist.max_over_ranks(info, time.perf_counter() - t0, dev)
         e2e = {"value": info.world * n * k_e2e / e2e_s / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": 27 * 4 * n, "d2h_bytes_per_step": 6 * 8, "steps": k_e2e,
-               "path": "rflbm_set_populations_f32 (pinned host) + rflbm_step + rflbm_stats"}
-        del host
+               "h2d_bytes_per_step": 27 * 4 * n, "d2h_bytes_per_step": 27 * 4 * n, "steps": k_e2e,
+               "path": "rflbm_set_populations_f32 (pinned host) + rflbm_step + "
+                       "rflbm_get_populations_f32 (pinned host)"}
+        del host_in, host_out
 
     variants = {}
+    accuracy = None
     if not args.no_variants and info.world == 1:
         peak_v, _ = measured_peak()
         st_main = storage[args.storage]
-        for name, kw, bps in (
-                ("reg_lbm_kT0", dict(kT=0.0, storage=st_main), BYTES_PER_SITE[args.storage]),
-                ("bgk_flbm", dict(kT=args.kT, model=R.RFLBM_MODEL_BGK, storage=st_main),
+        k = max(10, args.steps // 4)
+        F32, F16, BF16, AA = R.RFLBM_STORE_F32, R.RFLBM_STORE_F16, R.RFLBM_STORE_BF16, R.RFLBM_PATTERN_AA
+        for name, shape, init, kw, bps in (
+                ("reg_lbm_kT0", (e, e, e), "rest", dict(kT=0.0, storage=st_main), BYTES_PER_SITE[args.storage]),
+                ("bgk_flbm", (e, e, e), "rest", dict(kT=args.kT, model=R.RFLBM_MODEL_BGK, storage=st_main),
                  BYTES_PER_SITE[args.storage]),
-                ("f16_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_F16), 108),
-                ("f16_reg_lbm_kT0", dict(kT=0.0, storage=R.RFLBM_STORE_F16), 108),
-                ("bf16_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_BF16), 108),
-                ("aa_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_F32,
-                                     pattern=R.RFLBM_PATTERN_AA), 216),
-                ("aa_reg_lbm_kT0", dict(kT=0.0, storage=R.RFLBM_STORE_F32,
-                                        pattern=R.RFLBM_PATTERN_AA), 216),
-                ("aa_f16_reg_flbm", dict(kT=args.kT, storage=R.RFLBM_STORE_F16,
-                                         pattern=R.RFLBM_PATTERN_AA), 108)):
-            vb = R.Box(e, e, e, tau=args.tau, seed=1, stream=stream.cuda_stream, kernel=kernel, **kw)
-            R.rflbm_init_rest(vb.h)
-            R.rflbm_step(vb.h, 50)
-            k = max(10, args.steps // 4)
-            vms = time_steps(R, torch, vb, stream, k)
-            sites_s = n * k / (vms * 1e-3)
-            variants[name] = {"value": sites_s / 1e6, "unit": "MLUPS", "steps": k,
-                              "roofline_frac": bps * sites_s / 1e9 / peak_v,
-                              "bytes_per_site": bps}
-            vb.close()
+                ("f16_reg_flbm", (e, e, e), "rest", dict(kT=args.kT, storage=F16), 108),
+                ("f16_reg_lbm_kT0", (e, e, e), "rest", dict(kT=0.0, storage=F16), 108),
+                ("bf16_reg_flbm", (e, e, e), "rest", dict(kT=args.kT, storage=BF16), 108),
+                ("aa_reg_flbm", (e, e, e), "rest", dict(kT=args.kT, storage=F32, pattern=AA), 216),
+                ("aa_reg_lbm_kT0", (e, e, e), "rest", dict(kT=0.0, storage=F32, pattern=AA), 216),
+                ("aa_f16_reg_flbm", (e, e, e), "rest", dict(kT=args.kT, storage=F16, pattern=AA), 108),
+                # mixed precision at 512^3 (134 M sites), float32 beside it on the same GPU
+                ("c3_512_f32_reg_flbm", (512,) * 3, "rest", dict(kT=1e-4, storage=F32), 216),
+                ("c3_512_f16_reg_flbm", (512,) * 3, "rest", dict(kT=1e-4, storage=F16), 108),
+                ("c3_512_bf16_reg_flbm", (512,) * 3, "rest", dict(kT=1e-4, storage=BF16), 108),
+                # large single boxes from the Taylor-Green vortex (u0 0.01) with noise
+                ("c5_768_f32_reg_flbm", (768,) * 3, "taylor-green", dict(kT=1e-4, storage=F32), 216),
+                ("c5_1024_f16_aa_reg_flbm", (1024,) * 3, "taylor-green",
+                 dict(kT=1e-4, storage=F16, pattern=AA), 108)):
+            variants[name] = time_variant(R, torch, stream, shape, k, peak_v, bps, init=init,
+                                          kernel=kernel, **kw)
+        accuracy = storage_accuracy(R, torch, stream)
         # batched ensemble: 64 replicas of uneven sizes, one CUDA graph of per-step launches per call
         from paper_2507_08820_gb300 import workloads as W
         reps = W.replica_ensemble(64, seed=0)
@@ -538,10 +683,8 @@ def gb300_arm(args):
                 "algorithmic_bytes_per_launch": BYTES_PER_SITE[args.storage] * n}
     cpu = None
     if not args.no_cpu_baseline and info.world == 1:  # the oracle baseline is an N = 1 figure
-        r = oracle_sample_rate(e, args.tau, args.kT, budget_s=15.0, steps=2)
-        cpu = {"value": r["mlups"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"FP64 oracle collision + streaming of {r['sites']} sampled sites of "
-                         f"the {e}^3 box, {r['steps']} steps, {r['seconds']:.1f} s, one thread"}
+        r = oracle_sample_rate(e, args.tau, args.kT, budget_s=12.0, steps=None)
+        cpu = cpu_baseline_entry(r, e, False)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": info.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -550,11 +693,12 @@ def gb300_arm(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": launches,
         "clocks": clocks,
         "stats_after": {"mass_rel_drift": (st.mass - n) / n, "max_speed": st.max_speed,
                         "nonfinite": st.nonfinite},
         "variants": variants,
+        "storage_accuracy": accuracy,
     }
     print(json.dumps(line))
     dist.finalize(info)

@@ -124,6 +124,9 @@ typedef struct {
   int device;            /* CUDA device ordinal, -1 = the current device */
   int kernel;            /* rflbm_kernel */
   int pattern;           /* rflbm_pattern */
+  int z0;                /* z-slab: global z of the handle's first row (0 for a whole box) */
+  int nz_global;         /* z-slab: z edge of the decomposed box (nx*ny*nz_global < 2^31);
+                            0 = the handle holds a whole periodic box (see "z-slabs" below) */
 } rflbm_config_t;
 
 typedef struct {
@@ -137,7 +140,7 @@ typedef struct {
 
 /* Fills cfg with the defaults: 32^3, tau 0.8, kT 0, rho0 1, seed 1, omega_g 1, Reg model,
  * float32 storage, local rho in Eq. 10, replica 0, default stream, library buffers,
- * current device, automatic kernel choice, ping-pong streaming. */
+ * current device, automatic kernel choice, ping-pong streaming, a whole box (no z-slab). */
 void rflbm_config_default(rflbm_config_t* cfg);
 
 /* sizeof(rflbm_config_t) as compiled into the library (for bindings to check their
@@ -322,6 +325,54 @@ int rflbm_batch_synchronize(rflbm_batch_t* b);
 /* Populations (27*N doubles, public layout) and diagnostics of replica r. Synchronous. */
 int rflbm_batch_get_populations(rflbm_batch_t* b, int r, double* f);
 int rflbm_batch_stats(rflbm_batch_t* b, int r, rflbm_stats_t* out);
+
+/* z-slabs: one box split along z across several handles (the paper's linear domain
+ * decomposition for its multi-GPU runs, Sec. IV), typically one per GPU.
+ *
+ * A handle created with nz_global > 0 is the z-slab of rows z0 .. z0 + nz - 1 of a periodic
+ * box of nx x ny x nz_global sites. Its buffers hold the nz rows between two ghost rows (the
+ * row below z0 and the row above z0 + nz - 1), x and y stay periodic inside the handle, and
+ * z is periodic across the slabs. The noise of a site is keyed by its global index
+ * x + nx (y + ny z) (rflbm.h conventions), so slabs that exchange their faces after every
+ * step reproduce the run of the undecomposed box bit for bit, in both streaming patterns
+ * and every storage format. Sites, fields and populations of the public layout are the
+ * slab's own nx*ny*nz sites. rflbm_step takes one step per call on a slab: it updates the
+ * two boundary rows first and then the interior rows, so that the faces can move while the
+ * interior updates. Until the exchange of that step is complete, the slab accepts no other
+ * call that reads or advances its state (RFLBM_ESTATE). The structure factor needs the
+ * whole box and is not available on a slab; state images of AA slabs are not supported.
+ *
+ * A face is 9 rows of nx*ny values (the populations with c_z = +1 going up, or c_z = -1
+ * going down), given as three runs of three planes: run r starts at run[r]; plane p of the
+ * run (p = 0, 1, 2) starts plane_pitch * p bytes further; each plane row is row_bytes
+ * contiguous bytes of device memory of the handle's device. After each step, the bytes of
+ * send_up must reach the upper neighbour's recv_below and those of send_down the lower
+ * neighbour's recv_above, run by run and plane by plane (the neighbours of the top and the
+ * bottom slab wrap around periodically). Which rows these are depends on the pattern and
+ * the step's parity: query them after every step. */
+typedef struct {
+  void* run[3];          /* first byte of each run of three plane rows */
+  int64_t plane_pitch;   /* bytes from one plane row of a run to the next */
+  int64_t row_bytes;     /* contiguous bytes of one plane row (nx*ny values) */
+} rflbm_face_t;
+
+/* The four faces of the exchange that the slab's last step requires (any pointer may be
+ * NULL). RFLBM_ESTATE if no exchange is pending, RFLBM_EINVAL for a handle that is not a
+ * slab. */
+int rflbm_slab_faces(rflbm_t* h, rflbm_face_t* send_up, rflbm_face_t* send_down,
+                     rflbm_face_t* recv_below, rflbm_face_t* recv_above);
+/* Makes `stream` (a cudaStream_t of the handle's device) wait until the boundary rows of
+ * the slab's last step are written: work enqueued on it afterwards may read the send faces
+ * and write the receive faces. */
+int rflbm_slab_faces_ready(rflbm_t* h, void* stream);
+/* Declares the exchange complete once the work enqueued on `stream` so far has run: the
+ * slab's next work waits for it, and its state may be read and stepped again. */
+int rflbm_slab_exchange_done(rflbm_t* h, void* stream);
+/* The whole exchange for n slabs of one box on one device, given in z order (slab k + 1 is
+ * above slab k, the last below the first): plain device-to-device copies on a stream of
+ * the library that waits for every slab's boundary rows and overlaps their interior rows;
+ * then every slab's next step waits for the copies. n = 1 makes one slab periodic in z. */
+int rflbm_slab_exchange(rflbm_t* const* slabs, int n);
 
 /* Global diagnostics of caller-owned populations that allocate nothing.
  *

@@ -55,6 +55,12 @@ struct rflbm {
   bool fft_ready = false;
   void* staging = nullptr;     // device staging for host<->device transfers
   size_t staging_bytes = 0;
+  // z-slab of a decomposed box (cfg.nz_global > 0): ghost rows at both z faces
+  bool slab = false;
+  int exchange = 0;            // the face exchange the last step requires (kExchange*)
+  cudaEvent_t faces_ready = nullptr;  // recorded after the boundary rows of the last step
+  cudaEvent_t exchanged = nullptr;    // recorded where the exchange ends
+  cudaStream_t halo_stream = nullptr; // copies of rflbm_slab_exchange
 };
 
 namespace {
@@ -97,6 +103,19 @@ struct DeviceGuard {
 
 int64_t plane_stride(int64_t n) { return (n + 63) / 64 * 64; }
 
+// Sites one plane of a buffer holds: the box, or a z-slab's rows with its two ghost rows.
+int64_t buffer_sites(const rflbm_config_t* c) {
+  return (int64_t)c->nx * c->ny * (c->nz + (c->nz_global > 0 ? 2 : 0));
+}
+
+// The face exchange a z-slab needs after a step (see rflbm_slab_faces).
+enum : int {
+  kExchangeNone = 0,
+  kExchangePull = 1,    // ping-pong: the pulled planes of the new state
+  kExchangeAaFill = 2,  // AA after an even step: values the neighbours' odd step pulls
+  kExchangeAaDrain = 3  // AA after an odd step: values it pushed into its ghost rows
+};
+
 int validate(const rflbm_config_t* c) {
   if (!c) return fail(RFLBM_EINVAL, "config is NULL");
   if (c->nx < 1 || c->ny < 1 || c->nz < 1)
@@ -124,6 +143,19 @@ int validate(const rflbm_config_t* c) {
   if (c->pattern == RFLBM_PATTERN_AA &&
       ((c->model == RFLBM_MODEL_REG && c->omega_g != 1.0) || c->phi_rho != RFLBM_PHI_LOCAL_RHO))
     return fail(RFLBM_EINVAL, "the AA pattern supports omega_g = 1 and the local density in Eq. 10 only");
+  if (c->nz_global < 0) return fail(RFLBM_EINVAL, "nz_global must be >= 0 (got %d)", c->nz_global);
+  if (c->nz_global == 0 && c->z0 != 0)
+    return fail(RFLBM_EINVAL, "z0 = %d needs a z-slab (nz_global > 0)", c->z0);
+  if (c->nz_global > 0) {
+    if (c->z0 < 0 || (int64_t)c->z0 + c->nz > c->nz_global)
+      return fail(RFLBM_EINVAL, "z-slab rows [%d, %d) outside the box of %d rows", c->z0, c->z0 + c->nz,
+                  c->nz_global);
+    if ((int64_t)c->nx * c->ny * c->nz_global >= (int64_t(1) << 31))
+      return fail(RFLBM_EINVAL, "the decomposed box of %lld sites exceeds 2^31 - 1",
+                  (long long)((int64_t)c->nx * c->ny * c->nz_global));
+    if (buffer_sites(c) >= (int64_t(1) << 31))
+      return fail(RFLBM_EINVAL, "the z-slab with its ghost rows exceeds 2^31 - 1 sites");
+  }
   return RFLBM_OK;
 }
 
@@ -201,6 +233,9 @@ int check_handle(const rflbm* h) {
 int check_ready(const rflbm* h) {
   if (int e = check_handle(h)) return e;
   if (!h->initialised) return fail(RFLBM_ESTATE, "state not initialised (call rflbm_init_rest, rflbm_init_field or rflbm_set_populations)");
+  if (h->exchange != kExchangeNone)
+    return fail(RFLBM_ESTATE, "the z-slab's face exchange of its last step is pending (rflbm_slab_exchange, or "
+                              "rflbm_slab_faces and rflbm_slab_exchange_done)");
   return RFLBM_OK;
 }
 
@@ -286,7 +321,8 @@ bool rflbm_dev::encode_population_map(CUtensorMap* map, void* base, const Geomet
   EncodeTiledFn fn = encode_tiled_fn();
   if (!fn) return false;
   const cuuint64_t e = storage_bytes(storage);
-  const cuuint64_t dims[4] = {g.nx, g.ny, g.nz, (cuuint64_t)kQ};
+  // a z-slab's buffer holds its ghost rows too
+  const cuuint64_t dims[4] = {g.nx, g.ny, (cuuint64_t)g.nz + 2 * g.zlo, (cuuint64_t)kQ};
   const cuuint64_t strides[3] = {(cuuint64_t)g.nx * e, (cuuint64_t)g.nxy * e, (cuuint64_t)g.ps * e};
   const cuuint32_t box[4] = {box_x, box_y, 1, box_planes};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
@@ -318,14 +354,15 @@ void rflbm_config_default(rflbm_config_t* cfg) {
   cfg->device = -1;
   cfg->kernel = RFLBM_KERNEL_AUTO;
   cfg->pattern = RFLBM_PATTERN_PINGPONG;
+  cfg->z0 = 0;
+  cfg->nz_global = 0;
 }
 
 int64_t rflbm_config_size(void) { return (int64_t)sizeof(rflbm_config_t); }
 
 int64_t rflbm_buffer_bytes(const rflbm_config_t* cfg) {
   if (int e = validate(cfg)) return e;
-  const int64_t n = (int64_t)cfg->nx * cfg->ny * cfg->nz;
-  return plane_stride(n) * kQ * (int64_t)(cfg->storage == RFLBM_STORE_F32 ? 4 : 2);
+  return plane_stride(buffer_sites(cfg)) * kQ * (int64_t)(cfg->storage == RFLBM_STORE_F32 ? 4 : 2);
 }
 
 const char* rflbm_last_error(void) { return g_error.c_str(); }
@@ -365,9 +402,12 @@ rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
   g.nxy = (uint32_t)cfg->nx * (uint32_t)cfg->ny;
   g.n = (uint32_t)n;
   g.view = kViewPull;
-  g.ps = plane_stride(n);
+  g.ps = plane_stride(buffer_sites(cfg));
   g.div_nx = make_fastdiv(g.nx);
   g.div_nxy = make_fastdiv(g.nxy);
+  h->slab = cfg->nz_global > 0;
+  g.zlo = h->slab ? 1u : 0u;
+  g.site0 = h->slab ? g.nxy * (uint32_t)cfg->z0 : 0u;
   fill_collide_params(h);
 
   const size_t bytes = (size_t)g.ps * kQ * h->elem;
@@ -409,6 +449,8 @@ rflbm_t* rflbm_create_ex(const rflbm_config_t* cfg) {
                  sizeof(double) * ((size_t)h->stat_blocks * kStatOutFields + 8));
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->err, 0, sizeof(int));
+  if (e == cudaSuccess && h->slab) e = cudaEventCreateWithFlags(&h->faces_ready, cudaEventDisableTiming);
+  if (e == cudaSuccess && h->slab) e = cudaEventCreateWithFlags(&h->exchanged, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cuda_fail(e, "allocating the reduction scratch");
     rflbm_destroy(h);
@@ -441,6 +483,12 @@ void rflbm_destroy(rflbm_t* h) {
   cudaFree(h->diag_spec);
   if (h->fft_ready) cufftDestroy(h->fft_plan);
   cudaFree(h->staging);
+  if (h->faces_ready) cudaEventDestroy(h->faces_ready);
+  if (h->exchanged) cudaEventDestroy(h->exchanged);
+  if (h->halo_stream) {
+    cudaStreamSynchronize(h->halo_stream);
+    cudaStreamDestroy(h->halo_stream);
+  }
   delete h;
 }
 
@@ -453,6 +501,7 @@ int rflbm_init_rest(rflbm_t* h) {
   h->cur = 0;
   h->phase = 0;
   h->step = 0;
+  h->exchange = kExchangeNone;
   h->initialised = true;
   return RFLBM_OK;
 }
@@ -467,6 +516,7 @@ int rflbm_init_thermal(rflbm_t* h) {
                                  h->cfg.replica, h->buf[0], h->stream),
              "launching init_thermal");
   h->step = 0;
+  h->exchange = kExchangeNone;
   h->initialised = true;
   return RFLBM_OK;
 }
@@ -494,14 +544,63 @@ int rflbm_init_field(rflbm_t* h, const double* rho, const double* u, int on_devi
   RFLBM_CUDA(launch_init_field(vgeo(h), h->cp.rho0, h->ss, h->variant.storage, drho, du, h->buf[0], h->stream),
              "launching init_field");
   h->step = 0;
+  h->exchange = kExchangeNone;
   h->initialised = true;
   if (!on_device) return sync(h, "rflbm_init_field");
   return RFLBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Launches rows row0 .. row0 + nrows - 1 (row = y + ny z) of the handle's next step.
+cudaError_t launch_rows(rflbm* h, StepParams& p, uint32_t row0, uint32_t nrows) {
+  p.row0 = row0;
+  p.nrows = nrows;
+  if (h->aa) {
+    p.src = p.dst = h->buf[0];
+    const bool odd = h->phase != 0;
+    if (h->tma_width) {
+      const TmaMaps m{&h->load_map[0], &h->store_map[0], h->tma_width, h->has_row_map ? &h->row_map : nullptr};
+      return launch_step_aa_tma(m, p, h->variant, odd, h->stream);
+    }
+    return launch_step_aa_gather(p, h->variant, odd, h->stream);
+  }
+  p.src = h->buf[h->cur];
+  p.dst = h->buf[1 - h->cur];
+  if (h->tma_width) {
+    const TmaMaps m{&h->load_map[h->cur], &h->store_map[1 - h->cur], h->tma_width};
+    return launch_step_tma(m, p, h->variant, h->stream);
+  }
+  return launch_step_gather(p, h->variant, h->stream);
+}
+
+// One step of a z-slab: its two boundary rows first (they write the faces its neighbours
+// need), the faces-ready event, then its interior rows, which run while the faces move.
+cudaError_t slab_step(rflbm* h, StepParams& p) {
+  const uint32_t ny = h->geo.ny, nz = h->geo.nz;
+  cudaError_t e;
+  if (nz <= 2) {
+    e = launch_rows(h, p, 0, ny * nz);
+  } else {
+    e = launch_rows(h, p, 0, ny);
+    if (e == cudaSuccess) e = launch_rows(h, p, (nz - 1) * ny, ny);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->faces_ready, h->stream);
+  if (e == cudaSuccess && nz > 2) e = launch_rows(h, p, ny, (nz - 2) * ny);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
 int rflbm_step(rflbm_t* h, int64_t n) {
   if (int e = check_ready(h)) return e;
   if (n < 0) return fail(RFLBM_EINVAL, "negative step count %lld", (long long)n);
+  if (h->slab && n > 1)
+    return fail(RFLBM_EINVAL, "a z-slab takes one step per call (its faces are exchanged between steps)");
   DeviceGuard guard(h->device);
   StepParams p;
   p.geo = h->geo;
@@ -515,32 +614,11 @@ int rflbm_step(rflbm_t* h, int64_t n) {
   p.test_extra_tx = h->test_extra_tx;
   for (int64_t t = 0; t < n; ++t) {
     p.step = (uint32_t)h->step;
-    cudaError_t e;
-    if (h->aa) {
-      p.src = p.dst = h->buf[0];
-      const bool odd = h->phase != 0;
-      if (h->tma_width) {
-        const TmaMaps m{&h->load_map[0], &h->store_map[0], h->tma_width,
-                        h->has_row_map ? &h->row_map : nullptr};
-        e = launch_step_aa_tma(m, p, h->variant, odd, h->stream);
-      } else {
-        e = launch_step_aa_gather(p, h->variant, odd, h->stream);
-      }
-      if (e != cudaSuccess) return cuda_fail(e, "launching the AA step kernel");
-      h->phase ^= 1;
-      ++h->step;
-      continue;
-    }
-    p.src = h->buf[h->cur];
-    p.dst = h->buf[1 - h->cur];
-    if (h->tma_width) {
-      const TmaMaps m{&h->load_map[h->cur], &h->store_map[1 - h->cur], h->tma_width};
-      e = launch_step_tma(m, p, h->variant, h->stream);
-    } else {
-      e = launch_step_gather(p, h->variant, h->stream);
-    }
+    const cudaError_t e = h->slab ? slab_step(h, p) : launch_rows(h, p, 0, h->geo.ny * h->geo.nz);
     if (e != cudaSuccess) return cuda_fail(e, "launching the step kernel");
-    h->cur = 1 - h->cur;
+    if (h->slab) h->exchange = !h->aa ? kExchangePull : (h->phase ? kExchangeAaDrain : kExchangeAaFill);
+    if (h->aa) h->phase ^= 1;
+    else h->cur = 1 - h->cur;
     ++h->step;
   }
   return RFLBM_OK;
@@ -640,6 +718,7 @@ static int set_pops(rflbm_t* h, const void* f, int on_device, bool f64) {
   cudaError_t e = f64 ? launch_set_populations_f64(g, h->cp.rho0, h->ss, st, (const double*)src, h->buf[0], h->stream)
                       : launch_set_populations_f32(g, h->cp.rho0, h->ss, st, (const float*)src, h->buf[0], h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "launching set_populations");
+  h->exchange = kExchangeNone;
   h->initialised = true;
   if (!on_device) return sync(h, "rflbm_set_populations");
   return RFLBM_OK;
@@ -710,6 +789,7 @@ int rflbm_structure_factor(rflbm_t* h, int field, int nshell, double* s_sum, dou
   if (field < RFLBM_FIELD_RHO || field > RFLBM_FIELD_PYZ) return fail(RFLBM_EINVAL, "unknown field %d", field);
   if (nshell < 1 || nshell > 3072) return fail(RFLBM_EINVAL, "nshell must lie in [1, 3072] (got %d)", nshell);
   if (!s_sum || !count) return fail(RFLBM_EINVAL, "outputs are NULL");
+  if (h->slab) return fail(RFLBM_ESTATE, "the structure factor needs the whole box, not one z-slab of it");
   DeviceGuard guard(h->device);
   const Geometry& g = h->geo;
   const size_t nspec = (size_t)g.nz * g.ny * (g.nx / 2 + 1);
@@ -749,6 +829,8 @@ int64_t rflbm_state_bytes(const rflbm_t* h) {
 int rflbm_save_state(rflbm_t* h, void* image, int on_device) {
   if (int e = check_ready(h)) return e;
   if (!image) return fail(RFLBM_EINVAL, "image is NULL");
+  if (h->slab && h->aa)
+    return fail(RFLBM_ESTATE, "state images of z-slabs are supported in the ping-pong pattern only");
   DeviceGuard guard(h->device);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (!h->aa) {
@@ -785,6 +867,8 @@ int rflbm_save_state(rflbm_t* h, void* image, int on_device) {
 int rflbm_load_state(rflbm_t* h, const void* image, int on_device) {
   if (int e = check_handle(h)) return e;
   if (!image) return fail(RFLBM_EINVAL, "image is NULL");
+  if (h->slab && h->aa)
+    return fail(RFLBM_ESTATE, "state images of z-slabs are supported in the ping-pong pattern only");
   DeviceGuard guard(h->device);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (!h->aa) {
@@ -801,6 +885,7 @@ int rflbm_load_state(rflbm_t* h, const void* image, int on_device) {
     h->phase = 1;
   }
   h->cur = 0;
+  h->exchange = kExchangeNone;
   h->initialised = true;
   return sync(h, "rflbm_load_state");
 }
@@ -840,7 +925,8 @@ int rflbm_get_dims(const rflbm_t* h, int* nx, int* ny, int* nz) {
 
 int rflbm_launches_per_step(const rflbm_t* h) {
   if (int e = check_handle(h)) return e;
-  return 1;
+  if (!h->slab) return 1;
+  return h->geo.nz <= 2 ? 1 : 3;  // a z-slab: boundary rows (one or two launches), interior
 }
 
 int rflbm_step_path(const rflbm_t* h, int* width) {
@@ -854,6 +940,127 @@ int rflbm_step_sites_per_thread(const rflbm_t* h) {
   if (h->kernel != RFLBM_KERNEL_TMA) return 1;
   if (h->aa) return aa_uses_pairs(h->variant, h->phase != 0, h->has_row_map) ? 2 : 1;
   return tma_uses_pairs(h->variant) ? 2 : 1;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One face of a z-slab's buffer: the 9 planes of the populations with c_z = cz at buffer
+// row zb, as three runs of three adjacent planes (internal plane order: run b holds the
+// planes 3 (3 b + cz + 1) + (0, 1, 2), i.e. c_y = b - 1 and c_x = -1, 0, +1).
+rflbm_face_t face_of(const rflbm* h, void* buffer, uint32_t zb, int cz) {
+  rflbm_face_t f;
+  const int64_t pitch = h->geo.ps * (int64_t)h->elem;
+  for (int b = 0; b < 3; ++b) {
+    const int plane = 3 * (3 * b + cz + 1);
+    f.run[b] = static_cast<char*>(buffer) + plane * pitch + (int64_t)zb * h->geo.nxy * (int64_t)h->elem;
+  }
+  f.plane_pitch = pitch;
+  f.row_bytes = (int64_t)h->geo.nxy * (int64_t)h->elem;
+  return f;
+}
+
+int check_slab(const rflbm* h) {
+  if (int e = check_handle(h)) return e;
+  if (!h->slab) return fail(RFLBM_EINVAL, "not a z-slab handle (nz_global = 0)");
+  return RFLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rflbm_slab_faces(rflbm_t* h, rflbm_face_t* send_up, rflbm_face_t* send_down, rflbm_face_t* recv_below,
+                     rflbm_face_t* recv_above) {
+  if (int e = check_slab(h)) return e;
+  if (h->exchange == kExchangeNone) return fail(RFLBM_ESTATE, "no face exchange is pending");
+  const uint32_t nz = h->geo.nz;
+  void* const buf = h->aa ? h->buf[0] : h->buf[h->cur];
+  // buffer rows: 0 ghost below, 1 .. nz own rows, nz + 1 ghost above
+  rflbm_face_t f[4];
+  switch (h->exchange) {
+    case kExchangePull:  // the new state's populations that cross a face, pulled next step
+      f[0] = face_of(h, buf, nz, +1); f[1] = face_of(h, buf, 1, -1);
+      f[2] = face_of(h, buf, 0, +1);  f[3] = face_of(h, buf, nz + 1, -1);
+      break;
+    case kExchangeAaFill:  // an even AA step left them in the slots of the opposite direction
+      f[0] = face_of(h, buf, nz, -1); f[1] = face_of(h, buf, 1, +1);
+      f[2] = face_of(h, buf, 0, -1);  f[3] = face_of(h, buf, nz + 1, +1);
+      break;
+    default:  // an odd AA step pushed them into the ghost rows; they return to their owners
+      f[0] = face_of(h, buf, nz + 1, +1); f[1] = face_of(h, buf, 0, -1);
+      f[2] = face_of(h, buf, 1, +1);      f[3] = face_of(h, buf, nz, -1);
+      break;
+  }
+  if (send_up) *send_up = f[0];
+  if (send_down) *send_down = f[1];
+  if (recv_below) *recv_below = f[2];
+  if (recv_above) *recv_above = f[3];
+  return RFLBM_OK;
+}
+
+int rflbm_slab_faces_ready(rflbm_t* h, void* stream) {
+  if (int e = check_slab(h)) return e;
+  if (h->exchange == kExchangeNone) return fail(RFLBM_ESTATE, "no face exchange is pending");
+  DeviceGuard guard(h->device);
+  RFLBM_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, h->faces_ready, 0), "waiting for the faces");
+  return RFLBM_OK;
+}
+
+int rflbm_slab_exchange_done(rflbm_t* h, void* stream) {
+  if (int e = check_slab(h)) return e;
+  if (h->exchange == kExchangeNone) return fail(RFLBM_ESTATE, "no face exchange is pending");
+  DeviceGuard guard(h->device);
+  RFLBM_CUDA(cudaEventRecord(h->exchanged, (cudaStream_t)stream), "recording the end of the exchange");
+  RFLBM_CUDA(cudaStreamWaitEvent(h->stream, h->exchanged, 0), "ordering the next step after the exchange");
+  h->exchange = kExchangeNone;
+  return RFLBM_OK;
+}
+
+int rflbm_slab_exchange(rflbm_t* const* slabs, int n) {
+  if (!slabs || n < 1) return fail(RFLBM_EINVAL, "no slabs given");
+  for (int k = 0; k < n; ++k) {
+    if (int e = check_slab(slabs[k])) return e;
+    const rflbm* a = slabs[k];
+    const rflbm* b = slabs[0];
+    if (a->exchange == kExchangeNone) return fail(RFLBM_ESTATE, "slab %d has no face exchange pending", k);
+    if (a->exchange != b->exchange || a->device != b->device || a->geo.nx != b->geo.nx || a->geo.ny != b->geo.ny ||
+        a->elem != b->elem || a->aa != b->aa || a->cfg.nz_global != b->cfg.nz_global)
+      return fail(RFLBM_EINVAL, "slab %d does not match slab 0 (device, row shape, storage, pattern or step)", k);
+    const int up = (k + 1) % n;
+    if ((slabs[up]->cfg.z0 - (a->cfg.z0 + a->cfg.nz)) % a->cfg.nz_global != 0)
+      return fail(RFLBM_EINVAL, "slab %d is not followed by its upper neighbour (slabs must be given in z order)", k);
+  }
+  rflbm* h0 = slabs[0];
+  DeviceGuard guard(h0->device);
+  if (!h0->halo_stream)
+    RFLBM_CUDA(cudaStreamCreateWithFlags(&h0->halo_stream, cudaStreamNonBlocking), "creating the halo stream");
+  cudaStream_t hs = h0->halo_stream;
+  // the copies start once every slab's boundary rows are written (which also means that
+  // its previous step, the last reader of the rows the copies overwrite, is complete)
+  for (int k = 0; k < n; ++k)
+    RFLBM_CUDA(cudaStreamWaitEvent(hs, slabs[k]->faces_ready, 0), "waiting for the faces");
+  for (int k = 0; k < n; ++k) {
+    rflbm_face_t up_k, down_k, below_k, above_k, up_u, down_u, below_u, above_u;
+    rflbm* lo = slabs[k];
+    rflbm* hi = slabs[(k + 1) % n];
+    rflbm_slab_faces(lo, &up_k, &down_k, &below_k, &above_k);
+    rflbm_slab_faces(hi, &up_u, &down_u, &below_u, &above_u);
+    for (int b = 0; b < 3; ++b) {
+      // lower slab's upward face into the upper slab's row below it, and back down
+      RFLBM_CUDA(cudaMemcpy2DAsync(below_u.run[b], (size_t)below_u.plane_pitch, up_k.run[b], (size_t)up_k.plane_pitch,
+                                   (size_t)up_k.row_bytes, 3, cudaMemcpyDeviceToDevice, hs),
+                 "copying a face up");
+      RFLBM_CUDA(cudaMemcpy2DAsync(above_k.run[b], (size_t)above_k.plane_pitch, down_u.run[b],
+                                   (size_t)down_u.plane_pitch, (size_t)down_u.row_bytes, 3, cudaMemcpyDeviceToDevice,
+                                   hs),
+                 "copying a face down");
+    }
+  }
+  for (int k = 0; k < n; ++k)
+    if (int e = rflbm_slab_exchange_done(slabs[k], hs)) return e;
+  return RFLBM_OK;
 }
 
 int rflbm_testing_expect_extra_bytes(rflbm_t* h, uint32_t bytes) {

@@ -54,7 +54,7 @@ __global__ void k_init_thermal(Geometry g, float rho0, float kT, StoreScale ss, 
   float nrm[28];
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
-    const uint4 w = philox4x32_10(make_uint4(site_of(s), 0u, 6u + (uint32_t)j, replica), key0, key1);
+    const uint4 w = philox4x32_10(make_uint4(site_of(s) + g.site0, 0u, 6u + (uint32_t)j, replica), key0, key1);
     float r, c, sn;
     box_muller(w.x, w.y, r, c, sn);
     nrm[4 * j] = r * c;

@@ -42,12 +42,29 @@ constexpr uint32_t kViewNatural = 1;
 constexpr uint32_t kViewFlipped = 2;
 
 // Geometry of a box and the view of its buffer.
+//
+// A whole periodic box wraps in z. A z-slab (one part of a box split along z, Sec. IV)
+// holds its nz local rows between two ghost rows: buffer row 0 is the row below the slab
+// (global z0 - 1), rows 1..nz its own rows, row nz + 1 the row above; z does not wrap
+// inside the slab, and the ghost rows are filled by the exchange between slabs.
 struct Geometry {
-  uint32_t nx, ny, nz, nxy, n;
+  uint32_t nx, ny, nz, nxy, n;  // n = nx ny nz local sites
   uint32_t view;  // kViewPull / kViewNatural / kViewFlipped (read by the non-step kernels)
-  int64_t ps;     // plane stride in elements (n rounded up to 64)
+  int64_t ps;     // plane stride in elements ((nz + 2 zlo) nx ny rounded up to 64)
   FastDiv div_nx, div_nxy;
+  uint32_t zlo = 0;    // buffer row of local row 0: 0 (periodic box) or 1 (z-slab)
+  uint32_t site0 = 0;  // global index of local site 0 (the Philox site counter): nx ny z0
 };
+
+// Buffer row of local row z moved by dz in {-1, 0, +1}: periodic wrap for a whole box;
+// for a z-slab the rows beyond its faces are its ghost rows.
+__host__ __device__ __forceinline__ int zrow(const Geometry& g, int z, int dz) {
+  int zs = z + dz;
+  if (g.zlo) return zs + 1;
+  zs += zs < 0 ? (int)g.nz : 0;
+  zs -= zs >= (int)g.nz ? (int)g.nz : 0;
+  return zs;
+}
 
 // Periodic neighbour coordinates of site s: X[a] is the x coordinate of x - (a - 1),
 // Y[b] and Z[c] the row and slab offsets of y - (b - 1), z - (c - 1).
@@ -55,6 +72,7 @@ struct Neighbours {
   uint32_t X[3], Y[3], Z[3];
 };
 
+// (Z offsets are buffer rows: for a z-slab they include its ghost row below.)
 __device__ __forceinline__ Neighbours neighbours(uint32_t s, const Geometry& g) {
   const uint32_t z = fastdiv(s, g.div_nxy);
   const uint32_t rem = s - z * g.nxy;
@@ -62,11 +80,11 @@ __device__ __forceinline__ Neighbours neighbours(uint32_t s, const Geometry& g) 
   const uint32_t x = rem - y * g.nx;
   const uint32_t xm = (x == 0 ? g.nx : x) - 1, xp = (x + 1 == g.nx) ? 0 : x + 1;
   const uint32_t ym = (y == 0 ? g.ny : y) - 1, yp = (y + 1 == g.ny) ? 0 : y + 1;
-  const uint32_t zm = (z == 0 ? g.nz : z) - 1, zp = (z + 1 == g.nz) ? 0 : z + 1;
+  const uint32_t zm = (uint32_t)zrow(g, (int)z, -1), zp = (uint32_t)zrow(g, (int)z, 1);
   Neighbours nb;
   nb.X[0] = xp; nb.X[1] = x; nb.X[2] = xm;
   nb.Y[0] = yp * g.nx; nb.Y[1] = y * g.nx; nb.Y[2] = ym * g.nx;
-  nb.Z[0] = zp * g.nxy; nb.Z[1] = z * g.nxy; nb.Z[2] = zm * g.nxy;
+  nb.Z[0] = zp * g.nxy; nb.Z[1] = (z + g.zlo) * g.nxy; nb.Z[2] = zm * g.nxy;
   return nb;
 }
 
@@ -77,7 +95,7 @@ __device__ __forceinline__ uint32_t pull_site(const Neighbours& nb, int i) {
 
 // Element offset of g_i(s, t) in a buffer of view g.view (nb = neighbours(s, g)).
 __device__ __forceinline__ int64_t pop_slot(const Geometry& g, const Neighbours& nb, uint32_t s, int i) {
-  if (g.view == kViewNatural) return plane_of(i) * g.ps + s;
+  if (g.view == kViewNatural) return plane_of(i) * g.ps + s + g.zlo * g.nxy;
   const int plane = g.view == kViewFlipped ? kQ - 1 - plane_of(i) : plane_of(i);
   return plane * g.ps + pull_site(nb, i);
 }
@@ -99,8 +117,8 @@ __device__ __forceinline__ PullDeltas deltas_at(uint32_t x, uint32_t y, uint32_t
   d.DY[0] = (y + 1 == g.ny) ? nx - nxy : nx;
   d.DY[2] = (y == 0) ? nxy - nx : -nx;
   d.DZ[1] = 0;
-  d.DZ[0] = (z + 1 == g.nz) ? -nyz : nxy;
-  d.DZ[2] = (z == 0) ? nyz : -nxy;
+  d.DZ[0] = (!g.zlo && z + 1 == g.nz) ? -nyz : nxy;  // a z-slab reaches its ghost rows
+  d.DZ[2] = (!g.zlo && z == 0) ? nyz : -nxy;
   return d;
 }
 
@@ -122,6 +140,7 @@ __device__ __forceinline__ int32_t push_delta(const PullDeltas& d, int i) {
 
 struct StepParams {
   Geometry geo;
+  uint32_t row0, nrows;  // the launch updates rows row0 .. row0 + nrows - 1 (row = y + ny z)
   CollideParams cp;
   StoreScale ss;    // 16-bit storage scales (unused for float32)
   const void* src;  // population buffers in the handle's storage format

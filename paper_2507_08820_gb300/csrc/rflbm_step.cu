@@ -17,10 +17,12 @@ template <int kStore, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
 __global__ void __launch_bounds__(kStepBlock) step_pull(const StepParams p) {
   using S = Storage<kStore>;
   using T = typename S::T;
-  const uint32_t s = blockIdx.x * kStepBlock + threadIdx.x;
-  if (s >= p.geo.n) return;
+  // local site s of rows row0 .. row0 + nrows - 1; a z-slab's buffer holds it zlo rows up
+  const uint32_t s = p.row0 * p.geo.nx + blockIdx.x * kStepBlock + threadIdx.x;
+  if (s >= (p.row0 + p.nrows) * p.geo.nx) return;
   const PullDeltas d = pull_deltas(s, p.geo);
-  const T* __restrict__ src = static_cast<const T*>(p.src) + s;
+  const int64_t sb = s + (int64_t)p.geo.zlo * p.geo.nxy;
+  const T* __restrict__ src = static_cast<const T*>(p.src) + sb;
 
   float G[3][3][3];
 #pragma unroll
@@ -31,11 +33,11 @@ __global__ void __launch_bounds__(kStepBlock) step_pull(const StepParams p) {
   }
 
   SiteNoise noise;
-  if (kNoise) site_noise(s, p.step, p.replica, p.key0, p.key1, noise);
+  if (kNoise) site_noise(s + p.geo.site0, p.step, p.replica, p.key0, p.key1, noise);
 
   collide_site<kModel, kNoise, kGhostNeq, kPhiRho0>(G, p.cp, noise);
 
-  T* __restrict__ dst = static_cast<T*>(p.dst) + s;
+  T* __restrict__ dst = static_cast<T*>(p.dst) + sb;
 #pragma unroll
   for (int i = 0; i < kQ; ++i)
     dst[plane_of(i) * p.geo.ps] = S::store(G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1], class_of(i), p.ss);
@@ -48,9 +50,9 @@ template <int kStore, bool kOdd, int kModel, bool kNoise>
 __global__ void __launch_bounds__(kStepBlock) step_aa_gather(const StepParams p) {
   using S = Storage<kStore>;
   using T = typename S::T;
-  const uint32_t s = blockIdx.x * kStepBlock + threadIdx.x;
-  if (s >= p.geo.n) return;
-  T* const buf = static_cast<T*>(p.dst) + s;
+  const uint32_t s = p.row0 * p.geo.nx + blockIdx.x * kStepBlock + threadIdx.x;
+  if (s >= (p.row0 + p.nrows) * p.geo.nx) return;
+  T* const buf = static_cast<T*>(p.dst) + s + (int64_t)p.geo.zlo * p.geo.nxy;
   PullDeltas d{};
   if (kOdd) d = pull_deltas(s, p.geo);
 
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(kStepBlock) step_aa_gather(const StepParams p)
   }
 
   SiteNoise noise;
-  if (kNoise) site_noise(s, p.step, p.replica, p.key0, p.key1, noise);
+  if (kNoise) site_noise(s + p.geo.site0, p.step, p.replica, p.key0, p.key1, noise);
 
   collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
 
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(kStepBlock) step_aa_gather(const StepParams p)
 
 template <int kStore, bool kOdd, int kModel, bool kNoise>
 static cudaError_t launch_aa(const StepParams& p, cudaStream_t stream) {
-  const uint32_t blocks = (p.geo.n + kStepBlock - 1) / kStepBlock;
+  const uint32_t blocks = (p.nrows * p.geo.nx + kStepBlock - 1) / kStepBlock;
   step_aa_gather<kStore, kOdd, kModel, kNoise><<<blocks, kStepBlock, 0, stream>>>(p);
   return cudaGetLastError();
 }
@@ -110,7 +112,7 @@ cudaError_t launch_step_aa_gather(const StepParams& p, const StepVariant& v, boo
 
 template <int kStore, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
 static cudaError_t launch(const StepParams& p, cudaStream_t stream) {
-  const uint32_t blocks = (p.geo.n + kStepBlock - 1) / kStepBlock;
+  const uint32_t blocks = (p.nrows * p.geo.nx + kStepBlock - 1) / kStepBlock;
   step_pull<kStore, kModel, kNoise, kGhostNeq, kPhiRho0><<<blocks, kStepBlock, 0, stream>>>(p);
   return cudaGetLastError();
 }

@@ -55,12 +55,13 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
 
   const int t = threadIdx.x;
   const uint32_t nseg = p.geo.nx / kW;
-  const uint32_t row = blockIdx.x / nseg;
-  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t rb = blockIdx.x / nseg;
+  const uint32_t row = p.row0 + rb;                  // y + ny * z
+  const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
   const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
 
   grid_launch_dependents();
-  const uint32_t s = x0 + t + p.geo.nx * row;
+  const uint32_t s = x0 + t + p.geo.nx * row + p.geo.site0;  // global site (Philox counter)
   SiteNoise noise;
   if (kNoise) site_noise_part<0, kPreWaitCalls>(s, p.step, p.replica, p.rk, noise);
 
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
 
   if (t == 0) {
     mbar_arrive_expect_tx(&bar, (uint32_t)AaEvenLayout<kStore, kW>::kTileBytes + p.test_extra_tx);
-    tma_load_4d(sm, &map, (int)x0, (int)y, (int)z, 0, &bar);
+    tma_load_4d(sm, &map, (int)x0, (int)y, (int)(z + p.geo.zlo), 0, &bar);
   }
 
   if (kNoise) site_noise_part<kPreWaitCalls, 6>(s, p.step, p.replica, p.rk, noise);
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   fence_proxy_async_smem();
   __syncthreads();
   if (t == 0) {
-    tma_store_4d(&map, sm, (int)x0, (int)y, (int)z, 0);
+    tma_store_4d(&map, sm, (int)x0, (int)y, (int)(z + p.geo.zlo), 0);
     bulk_commit();
     bulk_wait_read();
   }
@@ -135,15 +136,16 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
 
   const int t = threadIdx.x;
   const uint32_t nseg = p.geo.nx / kW;
-  const uint32_t row = blockIdx.x / nseg;
-  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t rb = blockIdx.x / nseg;
+  const uint32_t row = p.row0 + rb;                  // y + ny * z
+  const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
   const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
 
   grid_launch_dependents();
   const uint32_t x = x0 + t;
-  const uint32_t s = x + p.geo.nx * row;
+  const uint32_t s = x + p.geo.nx * row;  // local site; the buffer holds it at s + zlo nx ny
   SiteNoise noise;
-  if (kNoise) site_noise_part<0, kPreWaitCalls>(s, p.step, p.replica, p.rk, noise);
+  if (kNoise) site_noise_part<0, kPreWaitCalls>(s + p.geo.site0, p.step, p.replica, p.rk, noise);
 
   if (t == 0) {
     mbar_init(&bar, 1);
@@ -161,11 +163,10 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   if (t < kGroups) {
     if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)) + p.test_extra_tx);
     const int cy = t / 3 - 1, cz = t % 3 - 1;
-    int ys = (int)y - cy, zs = (int)z - cz;
+    int ys = (int)y - cy;
     ys += ys < 0 ? (int)p.geo.ny : 0;
     ys -= ys >= (int)p.geo.ny ? (int)p.geo.ny : 0;
-    zs += zs < 0 ? (int)p.geo.nz : 0;
-    zs -= zs >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+    const int zs = zrow(p.geo, (int)z, -cz);  // buffer row (a z-slab's ghost rows at its faces)
     const int mirror = kGroups - 1 - t;
     tma_load_4d(sm + t * L::kGroup, &load_map, (int)x0 - kH, ys, zs, 3 * mirror, &bar);
     // periodic x edge: c_x = +1 (position 0) needs x = nx - 1 left of x = 0; c_x = -1
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
     }
   }
 
-  if (kNoise) site_noise_part<kPreWaitCalls, 6>(s, p.step, p.replica, p.rk, noise);
+  if (kNoise) site_noise_part<kPreWaitCalls, 6>(s + p.geo.site0, p.step, p.replica, p.rk, noise);
   const PullDeltas d = deltas_at(x, y, z, p.geo);
 
   const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
@@ -228,11 +229,10 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
     __syncthreads();
     if (t < kGroups) {
       const int cy = t / 3 - 1, cz = t % 3 - 1;
-      int yd = (int)y + cy, zd = (int)z + cz;
+      int yd = (int)y + cy;
       yd += yd < 0 ? (int)p.geo.ny : 0;
       yd -= yd >= (int)p.geo.ny ? (int)p.geo.ny : 0;
-      zd += zd < 0 ? (int)p.geo.nz : 0;
-      zd -= zd >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+      const int zd = zrow(p.geo, (int)z, cz);
       tma_store_4d(&row_map, sm + t * O::kGroup, 0, yd, zd, 3 * t);
       bulk_commit();
       bulk_wait_read();
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
 
   // population i of x goes to plane P(i) at x + c_i (coalesced: a warp writes 32
   // consecutive positions of each plane)
-  T* const dst = buf + s;
+  T* const dst = buf + s + (int64_t)p.geo.zlo * p.geo.nxy;
 #pragma unroll
   for (int i = 0; i < kQ; ++i)
     dst[plane_of(i) * p.geo.ps + push_delta(d, i)] =
@@ -264,13 +264,14 @@ __global__ void __launch_bounds__(kW / 2) step_aa_even_pair(const __grid_constan
 
   const int t = threadIdx.x;
   const uint32_t nseg = p.geo.nx / kW;
-  const uint32_t row = blockIdx.x / nseg;
-  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t rb = blockIdx.x / nseg;
+  const uint32_t row = p.row0 + rb;                  // y + ny * z
+  const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
   const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
 
   grid_launch_dependents();
   const PhiloxKey key{p.key0, p.key1};
-  PairNoise<kPairPreDrawn, PhiloxKey> noise{x0 + 2u * t + p.geo.nx * row, p.step, p.replica, key};
+  PairNoise<kPairPreDrawn, PhiloxKey> noise{x0 + 2u * t + p.geo.nx * row + p.geo.site0, p.step, p.replica, key};
   if (kNoise) noise.draw();
   if (t == 0) {
     mbar_init(&bar, 1);
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_even_pair(const __grid_constan
 
   if (t == 0) {
     mbar_arrive_expect_tx(&bar, (uint32_t)AaEvenLayout<kStore, kW>::kTileBytes + p.test_extra_tx);
-    tma_load_4d(sm, &map, (int)x0, (int)y, (int)z, 0, &bar);
+    tma_load_4d(sm, &map, (int)x0, (int)y, (int)(z + p.geo.zlo), 0, &bar);
   }
   const bool ok = mbar_wait_bounded(&bar, 0, kMaxPolls);
   if (__syncthreads_or(!ok)) {
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_even_pair(const __grid_constan
   fence_proxy_async_smem();
   __syncthreads();
   if (t == 0) {
-    tma_store_4d(&map, sm, (int)x0, (int)y, (int)z, 0);
+    tma_store_4d(&map, sm, (int)x0, (int)y, (int)(z + p.geo.zlo), 0);
     bulk_commit();
     bulk_wait_read();
   }
@@ -326,15 +327,16 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
 
   const int t = threadIdx.x;
   const uint32_t nseg = p.geo.nx / kW;
-  const uint32_t row = blockIdx.x / nseg;
-  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t rb = blockIdx.x / nseg;
+  const uint32_t row = p.row0 + rb;                  // y + ny * z
+  const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
   const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
 
   grid_launch_dependents();
   const uint32_t x = x0 + 2u * t;  // and x + 1
-  const uint32_t s = x + p.geo.nx * row;
+  const uint32_t s = x + p.geo.nx * row;  // local site; the buffer holds it at s + zlo nx ny
   const PhiloxKey key{p.key0, p.key1};
-  PairNoise<kPairPreDrawn, PhiloxKey> noise{s, p.step, p.replica, key};
+  PairNoise<kPairPreDrawn, PhiloxKey> noise{s + p.geo.site0, p.step, p.replica, key};
   if (kNoise) noise.draw();
   if (t == 0) {
     mbar_init(&bar, 1);
@@ -350,11 +352,10 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
   if (t < kGroups) {
     if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)) + p.test_extra_tx);
     const int cy = t / 3 - 1, cz = t % 3 - 1;
-    int ys = (int)y - cy, zs = (int)z - cz;
+    int ys = (int)y - cy;
     ys += ys < 0 ? (int)p.geo.ny : 0;
     ys -= ys >= (int)p.geo.ny ? (int)p.geo.ny : 0;
-    zs += zs < 0 ? (int)p.geo.nz : 0;
-    zs -= zs >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+    const int zs = zrow(p.geo, (int)z, -cz);  // buffer row (a z-slab's ghost rows at its faces)
     const int mirror = kGroups - 1 - t;
     tma_load_4d(sm + t * L::kGroup, &load_map, (int)x0 - kH, ys, zs, 3 * mirror, &bar);
     const int64_t rowoff = (int64_t)p.geo.nx * ((int64_t)ys + (int64_t)p.geo.ny * zs);
@@ -412,11 +413,10 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
     __syncthreads();
     if (t < kGroups) {
       const int cy = t / 3 - 1, cz = t % 3 - 1;
-      int yd = (int)y + cy, zd = (int)z + cz;
+      int yd = (int)y + cy;
       yd += yd < 0 ? (int)p.geo.ny : 0;
       yd -= yd >= (int)p.geo.ny ? (int)p.geo.ny : 0;
-      zd += zd < 0 ? (int)p.geo.nz : 0;
-      zd -= zd >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+      const int zd = zrow(p.geo, (int)z, cz);
       tma_store_4d(&row_map, sm + t * O::kGroup, 0, yd, zd, 3 * t);
       bulk_commit();
       bulk_wait_read();
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
   // population i of x and x + 1 goes to plane P(i) at x + c_i and x + 1 + c_i: the rows
   // (y, z) shifts are shared; along x, x + 1 never wraps from x (x is even, nx is even),
   // x - 1 wraps when x = 0, and x + 2 wraps when x + 2 = nx
-  T* const dst = buf + s;
+  T* const dst = buf + s + (int64_t)p.geo.zlo * p.geo.nxy;
   const int32_t dxb_plus = (x + 2u == p.geo.nx) ? 1 - (int32_t)p.geo.nx : 1;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
 
 template <int kStore, int kW, bool kNoise>
 cudaError_t launch_aa_pair(const TmaMaps& m, const StepParams& p, bool odd, cudaStream_t st) {
-  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.geo.ny * p.geo.nz;
+  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.nrows;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kW / 2);
@@ -469,7 +469,7 @@ cudaError_t launch_aa_pair(const TmaMaps& m, const StepParams& p, bool odd, cuda
 
 template <int kStore, int kW, int kModel, bool kNoise>
 cudaError_t launch_aa_segment(const TmaMaps& m, const StepParams& p, bool odd, cudaStream_t st) {
-  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.geo.ny * p.geo.nz;
+  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.nrows;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kW);

@@ -61,14 +61,15 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
 
   const int t = threadIdx.x;
   const uint32_t nseg = p.geo.nx / kW;
-  const uint32_t row = blockIdx.x / nseg;            // y + ny * z
-  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t rb = blockIdx.x / nseg;
+  const uint32_t row = p.row0 + rb;                  // y + ny * z
+  const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
   const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
 
   // the next step may start launching now: its CTAs draw their noise while this grid's
   // last CTAs finish; they touch global memory only after their grid_dependency_wait
   grid_launch_dependents();
-  const uint32_t s = x0 + t + p.geo.nx * row;
+  const uint32_t s = x0 + t + p.geo.nx * row + p.geo.site0;  // global site (Philox counter)
   SiteNoise noise;
   if (kNoise) site_noise_part<0, kPreWaitCalls>(s, p.step, p.replica, p.rk, noise);
 
@@ -85,11 +86,10 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   if (t < kGroups) {
     if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)) + p.test_extra_tx);
     const int cy = t / 3 - 1, cz = t % 3 - 1;
-    int ys = (int)y - cy, zs = (int)z - cz;
+    int ys = (int)y - cy;
     ys += ys < 0 ? (int)p.geo.ny : 0;
     ys -= ys >= (int)p.geo.ny ? (int)p.geo.ny : 0;
-    zs += zs < 0 ? (int)p.geo.nz : 0;
-    zs -= zs >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+    const int zs = zrow(p.geo, (int)z, -cz);  // buffer row (a z-slab's ghost rows at its faces)
     tma_load_4d(sm + t * L::kGroup, &load_map, (int)x0 - kH, ys, zs, 3 * t, &bar);
     // periodic x edge: plane c_x = +1 needs x = nx - 1 left of x = 0, plane c_x = -1
     // needs x = 0 right of x = nx - 1
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   fence_proxy_async_smem();
   __syncthreads();
   if (t == 0) {
-    tma_store_4d(&store_map, sm, (int)x0, (int)y, (int)z, 0);
+    tma_store_4d(&store_map, sm, (int)x0, (int)y, (int)(z + p.geo.zlo), 0);
     bulk_commit();
     bulk_wait_read();
   }
@@ -168,14 +168,15 @@ __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ 
 
   const int t = threadIdx.x;
   const uint32_t nseg = p.geo.nx / kW;
-  const uint32_t row = blockIdx.x / nseg;
-  const uint32_t x0 = (blockIdx.x - row * nseg) * kW;
+  const uint32_t rb = blockIdx.x / nseg;
+  const uint32_t row = p.row0 + rb;                  // y + ny * z
+  const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
   const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
 
   grid_launch_dependents();
   // (round keys computed in the rounds: from the parameter bank they measured 5 % slower here)
   const PhiloxKey key{p.key0, p.key1};
-  PairNoise<kPairPreDrawn, PhiloxKey> noise{x0 + 2u * t + p.geo.nx * row, p.step, p.replica, key};
+  PairNoise<kPairPreDrawn, PhiloxKey> noise{x0 + 2u * t + p.geo.nx * row + p.geo.site0, p.step, p.replica, key};
   if (kNoise) noise.draw();
   if (t == 0) {
     mbar_init(&bar, 1);
@@ -189,11 +190,10 @@ __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ 
   if (t < kGroups) {
     if (t == 0) mbar_arrive_expect_tx(&bar, (uint32_t)(kGroups * 3 * L::kSeg * sizeof(T)) + p.test_extra_tx);
     const int cy = t / 3 - 1, cz = t % 3 - 1;
-    int ys = (int)y - cy, zs = (int)z - cz;
+    int ys = (int)y - cy;
     ys += ys < 0 ? (int)p.geo.ny : 0;
     ys -= ys >= (int)p.geo.ny ? (int)p.geo.ny : 0;
-    zs += zs < 0 ? (int)p.geo.nz : 0;
-    zs -= zs >= (int)p.geo.nz ? (int)p.geo.nz : 0;
+    const int zs = zrow(p.geo, (int)z, -cz);  // buffer row (a z-slab's ghost rows at its faces)
     tma_load_4d(sm + t * L::kGroup, &load_map, (int)x0 - kH, ys, zs, 3 * t, &bar);
     const T* src = static_cast<const T*>(p.src);
     const int64_t rowoff = (int64_t)p.geo.nx * ((int64_t)ys + (int64_t)p.geo.ny * zs);
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ 
   fence_proxy_async_smem();
   __syncthreads();
   if (t == 0) {
-    tma_store_4d(&store_map, sm, (int)x0, (int)y, (int)z, 0);
+    tma_store_4d(&store_map, sm, (int)x0, (int)y, (int)(z + p.geo.zlo), 0);
     bulk_commit();
     bulk_wait_read();
   }
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ 
 
 template <int kStore, int kW, bool kNoise>
 cudaError_t launch_tma_pair(const TmaMaps& m, const StepParams& p, cudaStream_t st) {
-  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.geo.ny * p.geo.nz;
+  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.nrows;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kW / 2);
@@ -265,7 +265,7 @@ cudaError_t launch_tma_pair(const TmaMaps& m, const StepParams& p, cudaStream_t 
 
 template <int kStore, int kW, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
 cudaError_t launch_tma_segment(const TmaMaps& m, const StepParams& p, cudaStream_t st) {
-  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.geo.ny * p.geo.nz;
+  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.nrows;
   // programmatic stream serialisation: this launch may begin while the previous kernel
   // of the stream drains (the kernel waits for it before touching global memory)
   cudaLaunchConfig_t cfg = {};

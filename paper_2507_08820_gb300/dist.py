@@ -1,9 +1,18 @@
-"""Process-group plumbing for running independent replicas, one process per GPU.
+"""Process-group plumbing, one process per GPU: independent replicas, and the z-slab
+decomposition of one box.
 
-The Reg-FLBM step has no exchange between independent boxes, so a multi-GPU run is N
-replicas (weak scaling): rank r advances its own box with Philox replica word r, and the
-only collectives are a barrier around the timed region and a max-reduction of the
-per-rank times. torch.distributed is used for exactly that (NCCL on GPUs, gloo on CPU).
+Replicas: the Reg-FLBM step has no exchange between independent boxes, so N replicas run
+with no data-path collective (weak scaling): rank r advances its own box with Philox
+replica word r, and the only collectives are a barrier around the timed region and a
+max-reduction of the per-rank times.
+
+z-slabs (the paper's linear decomposition along z, Sec. IV): rank r holds rows
+z0 .. z0 + nz - 1 of one periodic box (`slab_bounds`); after every step each rank sends the
+face of its top row to the rank above and the face of its bottom row to the rank below, and
+receives the matching faces into its ghost rows (`exchange_faces`: grouped point-to-point
+sends and receives on a periodic ring). torch.distributed carries the bytes (NCCL on GPUs,
+gloo on CPU); which rows and populations form a face is the library's business
+(rflbm_slab_faces).
 """
 from __future__ import annotations
 
@@ -74,3 +83,43 @@ def finalize(info: RankInfo):
     import torch.distributed as dist
     if dist.is_initialized():
         dist.destroy_process_group()
+
+
+def slab_bounds(nz_global: int, world: int, rank: int):
+    """(z0, nz) of rank's z-slab when nz_global rows are split as evenly as possible over
+    world ranks (the first nz_global % world ranks take one row more)."""
+    if not 1 <= world <= nz_global:
+        raise ValueError(f"cannot split {nz_global} rows over {world} ranks")
+    base, extra = divmod(nz_global, world)
+    nz = base + (1 if rank < extra else 0)
+    z0 = rank * base + min(rank, extra)
+    return z0, nz
+
+
+def ring_neighbours(info: RankInfo):
+    """(rank above, rank below) on the periodic ring of z-slabs."""
+    return (info.rank + 1) % info.world, (info.rank - 1) % info.world
+
+
+def exchange_faces(info: RankInfo, send_up, send_down, recv_below, recv_above):
+    """One face exchange on the ring of z-slabs. Each argument is a list of equally long
+    lists of tensors (the plane rows of a face, in the library's run and plane order);
+    send_up goes to the rank above into its recv_below, send_down to the rank below into
+    its recv_above. With one rank the slab is its own neighbour (local copies). The
+    operations are posted as one group: the two sends to a peer are matched in order by
+    the peer's two receives (up before down), which also pairs them correctly when the
+    rank above and the rank below are the same peer (two ranks)."""
+    if info.world <= 1:
+        for d, s in zip(recv_below, send_up):
+            d.copy_(s)
+        for d, s in zip(recv_above, send_down):
+            d.copy_(s)
+        return
+    import torch.distributed as dist
+    up, down = ring_neighbours(info)
+    ops = [dist.P2POp(dist.isend, t, up) for t in send_up]
+    ops += [dist.P2POp(dist.isend, t, down) for t in send_down]
+    ops += [dist.P2POp(dist.irecv, t, down) for t in recv_below]
+    ops += [dist.P2POp(dist.irecv, t, up) for t in recv_above]
+    for req in dist.batch_isend_irecv(ops):
+        req.wait()

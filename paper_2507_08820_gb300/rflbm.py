@@ -51,8 +51,12 @@ class rflbm_config_t(C.Structure):
         ("model", C.c_int), ("storage", C.c_int), ("phi_rho", C.c_int),
         ("replica", C.c_uint32), ("stream", C.c_void_p),
         ("buffers", C.c_void_p * 2), ("device", C.c_int), ("kernel", C.c_int),
-        ("pattern", C.c_int),
+        ("pattern", C.c_int), ("z0", C.c_int), ("nz_global", C.c_int),
     ]
+
+
+class rflbm_face_t(C.Structure):
+    _fields_ = [("run", C.c_void_p * 3), ("plane_pitch", C.c_int64), ("row_bytes", C.c_int64)]
 
 
 class rflbm_replica_t(C.Structure):
@@ -125,6 +129,10 @@ _sig = {
     "rflbm_structure_factor": (C.c_int, [_H, C.c_int, C.c_int, _P, _P]),
     "rflbm_shell_count": (C.c_int, [_H]),
     "rflbm_testing_expect_extra_bytes": (C.c_int, [_H, C.c_uint32]),
+    "rflbm_slab_faces": (C.c_int, [_H] + [C.POINTER(rflbm_face_t)] * 4),
+    "rflbm_slab_faces_ready": (C.c_int, [_H, _P]),
+    "rflbm_slab_exchange_done": (C.c_int, [_H, _P]),
+    "rflbm_slab_exchange": (C.c_int, [_P, C.c_int]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(lib, _name)
@@ -377,6 +385,28 @@ def rflbm_site_normals(seed, step, replica, sites):
     return out
 
 
+def rflbm_slab_faces(h):
+    """(send_up, send_down, recv_below, recv_above) faces of the pending exchange, each an
+    rflbm_face_t (three runs of three plane rows, see include/rflbm.h)."""
+    f = [rflbm_face_t() for _ in range(4)]
+    _check(lib.rflbm_slab_faces(h, *[C.byref(x) for x in f]))
+    return tuple(f)
+
+
+def rflbm_slab_faces_ready(h, stream):
+    return _check(lib.rflbm_slab_faces_ready(h, stream))
+
+
+def rflbm_slab_exchange_done(h, stream):
+    return _check(lib.rflbm_slab_exchange_done(h, stream))
+
+
+def rflbm_slab_exchange(slabs):
+    """The face exchange of slabs of one box on one device, in z order."""
+    arr = (C.c_void_p * len(slabs))(*slabs)
+    return _check(lib.rflbm_slab_exchange(C.cast(arr, C.c_void_p), len(slabs)))
+
+
 RFLBM_STATS_NOALLOC_MAX_SITES = 134217728
 
 
@@ -462,13 +492,14 @@ def rflbm_batch_stats(b, r):
 
 # ------------------------------------------------------------------ convenience
 class Box:
-    """One periodic box (owns a handle). Population buffers are allocated by PyTorch
-    when `torch_buffers` is true, else by the library."""
+    """One periodic box (owns a handle), or with nz_global > 0 the z-slab of rows
+    z0 .. z0 + nz - 1 of a box of nz_global rows. Population buffers are allocated by
+    PyTorch when `torch_buffers` is true, else by the library."""
 
     def __init__(self, nx, ny, nz, tau, kT=0.0, rho0=1.0, seed=1, omega_g=1.0,
                  model=RFLBM_MODEL_REG, phi_rho=RFLBM_PHI_LOCAL_RHO, replica=0,
                  stream=None, torch_buffers=False, device=-1, kernel=RFLBM_KERNEL_AUTO,
-                 storage=RFLBM_STORE_F32, pattern=RFLBM_PATTERN_PINGPONG):
+                 storage=RFLBM_STORE_F32, pattern=RFLBM_PATTERN_PINGPONG, z0=0, nz_global=0):
         cfg = rflbm_config_default()
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
         cfg.tau, cfg.kT, cfg.rho0, cfg.seed = tau, kT, rho0, seed
@@ -477,6 +508,7 @@ class Box:
         cfg.kernel = kernel
         cfg.storage = storage
         cfg.pattern = pattern
+        cfg.z0, cfg.nz_global = z0, nz_global
         if stream is not None:
             cfg.stream = stream
         self._buffers = None

@@ -26,7 +26,7 @@ def test_reference_arm_prints_the_contract_line():
         assert key in line, key
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "MLUPS"
     assert line["value"] > 0 and line["higher_is_better"] is True
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == bench.host_cores()
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["config"]["box"] == [16, 16, 16] and "workload" in line["config"]
 
@@ -69,3 +69,11 @@ def test_workload_and_kernel_names():
     assert bench.kernel_name(2, 128, 1e-4, 0, "f32", "aa", 1, 2) == (
         "step_aa_even+step_aa_odd_pair<f32, 128, Reg, noise>", "step_aa_oddpair_f32_128")
     assert len(bench.kernel_source_hash()) == 16
+
+
+def test_mode_norms_match_the_oracle():
+    """The FDT accuracy figure divides each mode variance by rho0 kT b_k / cs2 with the
+    benchmark's own norm table; it must be Table II's (the oracle's pinned norms)."""
+    import numpy as np
+    from oracle import rflbm_oracle as o
+    assert np.allclose(bench.mode_norms(), o.norms(), rtol=0, atol=1e-15)

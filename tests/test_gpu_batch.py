@@ -9,6 +9,7 @@ slab has, with one or two slabs), site tiles elsewhere."""
 import numpy as np
 import pytest
 
+from oracle import rflbm_oracle as o
 from paper_2507_08820_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -97,4 +98,24 @@ def test_ensemble_of_64_replicas_1000_steps(R, storage):
     sizes = [rep["nx"] for rep in reps]
     for r in (int(np.argmin(sizes)), int(np.argmax(sizes))):
         assert np.array_equal(_batch_pops(R, b, reps, r), _single(R, reps[r], 1000, storage)), r
+    R.rflbm_batch_destroy(b)
+
+
+def test_replica_against_the_oracle(R):
+    """One replica of an ensemble against the FP64 oracle directly (not only through its
+    single-box run): a 16^3 box with noise, 5 steps from rest, populations within 1e-5
+    relative to max(|f_i|, w_i rho0)."""
+    reps = [dict(nx=16, ny=16, nz=16, tau=0.7, kT=1e-4, seed=12),
+            dict(nx=24, ny=8, nz=8, tau=0.9, kT=1e-3, seed=13)]
+    b = R.rflbm_batch_create(reps, storage=0, tile=192)
+    R.rflbm_batch_init_rest(b)
+    R.rflbm_batch_run(b, 5)
+    R.rflbm_batch_synchronize(b)
+    for r, rep in enumerate(reps):
+        shape = (rep["nx"], rep["ny"], rep["nz"])
+        n = int(np.prod(shape))
+        got = _batch_pops(R, b, reps, r)
+        want = o.run(o.rest_state(n), shape, rep["tau"], rep["kT"], rep["seed"], 5)
+        scale = np.maximum(np.abs(want), o.weights()[:, None])
+        assert float(np.max(np.abs(got - want) / scale)) < 1e-5, r
     R.rflbm_batch_destroy(b)
