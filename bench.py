@@ -60,16 +60,32 @@ def parse_args():
     ap.add_argument("--init", choices=["rest", "taylor-green"], default="rest",
                     help="rest start, or the Taylor-Green vortex (u0 = 0.01, k = 2 pi / edge)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--decomp", choices=["none", "slab"], default="none",
+                    help="none: every rank advances its own box (replicas); slab: the ranks hold "
+                         "z-slabs of one periodic box of edge x edge x (edge * ranks) sites and "
+                         "exchange their faces after every step (one rank: a slab periodic "
+                         "through its own faces)")
     return ap.parse_args()
 
 
 STORAGE_NAME = {"f32": "float32", "f16": "float16", "bf16": "bfloat16"}
 
 
-def workload(args):
+def workload(args, world=1):
     e = args.edge
     nbuf = 1 if args.pattern == "aa" else 2
     nbytes = nbuf * 27 * BYTES_PER_SITE[args.storage] // 54 * e ** 3
+    if getattr(args, "decomp", "none") == "slab":
+        return {"workload": f"z-slabs of a periodic {e}x{e}x{e * world} Reg-FLBM D3Q27 box, one "
+                            f"{e}^3 slab per rank, {STORAGE_NAME[args.storage]} populations, tau "
+                            f"{args.tau}, rho0 1, kT {args.kT:g}, seed 1, rest start, faces exchanged "
+                            "after every step",
+                "init": args.init, "box": [e, e, e * world], "sites": e ** 3 * world, "tau": args.tau,
+                "kT": args.kT, "storage": f"{args.storage} shifted by w_i rho0",
+                "streaming": "pull, ping-pong" if nbuf == 2 else "AA, one buffer in place",
+                "l2": f"inputs {nbytes / 1e6:.0f} MB per rank > 129 MB L2, no flush"
+                      if nbytes > 129e6 else f"inputs {nbytes / 1e6:.0f} MB per rank fit in the 129 MB L2",
+                "parallelism": "z-slabs" if world > 1 else "one z-slab, periodic through its own faces"}
     return {"workload": f"periodic {e}^3 Reg-FLBM D3Q27 thermal equilibrium, "
                         f"{STORAGE_NAME[args.storage]} populations, tau {args.tau}, rho0 1, "
                         f"kT {args.kT:g}, seed 1, "
@@ -354,14 +370,24 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-def time_steps(R, torch, box, stream, steps):
-    """CUDA-event time (ms) of `steps` launches on the box's stream."""
+def time_steps(R, torch, box, stream, steps, exchange=None):
+    """CUDA-event time (ms) of `steps` steps on the box's stream; with `exchange`, a z-slab
+    that exchanges its faces (exchange()) after every step."""
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
-    R.rflbm_step(box.h, steps)
+    advance(R, box, steps, exchange)
     end.record(stream)
     end.synchronize()
     return start.elapsed_time(end)
+
+
+def advance(R, box, steps, exchange=None):
+    if exchange is None:
+        R.rflbm_step(box.h, steps)
+        return
+    for _ in range(steps):
+        R.rflbm_step(box.h, 1)
+        exchange()
 
 
 def ensemble_arm(args):
@@ -562,9 +588,23 @@ def gb300_arm(args):
               "tma": R.RFLBM_KERNEL_TMA}[args.kernel]
     storage = {"f32": R.RFLBM_STORE_F32, "f16": R.RFLBM_STORE_F16, "bf16": R.RFLBM_STORE_BF16}
     pattern = {"pingpong": R.RFLBM_PATTERN_PINGPONG, "aa": R.RFLBM_PATTERN_AA}[args.pattern]
-    box = R.Box(e, e, e, tau=args.tau, kT=args.kT, seed=1, replica=info.rank,
-                stream=stream.cuda_stream, torch_buffers=True, device=info.local_rank,
-                kernel=kernel, storage=storage[args.storage], pattern=pattern)
+    slab = args.decomp == "slab"
+    exchange = None
+    if slab:
+        # rank r: rows r e .. (r + 1) e - 1 of one box; replica word 0 for every rank (one box)
+        z0, nz = dist.slab_bounds(e * info.world, info.world, info.rank)
+        box = R.Box(e, e, nz, tau=args.tau, kT=args.kT, seed=1, stream=stream.cuda_stream,
+                    torch_buffers=True, device=info.local_rank, kernel=kernel,
+                    storage=storage[args.storage], pattern=pattern, z0=z0, nz_global=e * info.world)
+        side = torch.cuda.Stream(device=dev)
+        if info.world == 1:
+            exchange = lambda: R.rflbm_slab_exchange([box.h])  # noqa: E731
+        else:
+            exchange = lambda: dist.exchange_slab(R, box, info, side)  # noqa: E731
+    else:
+        box = R.Box(e, e, e, tau=args.tau, kT=args.kT, seed=1, replica=info.rank,
+                    stream=stream.cuda_stream, torch_buffers=True, device=info.local_rank,
+                    kernel=kernel, storage=storage[args.storage], pattern=pattern)
     if args.init == "rest":
         R.rflbm_init_rest(box.h)
     else:
@@ -574,7 +614,7 @@ def gb300_arm(args):
     odd_pairs = pairs
     warm = args.warmup
     if args.pattern == "aa" and warm > 0:  # the odd AA steps may run the other form
-        R.rflbm_step(box.h, 1)
+        advance(R, box, 1, exchange)
         odd_pairs = R.rflbm_step_sites_per_thread(box.h)
         warm -= 1
     R.rflbm_synchronize(box.h)
@@ -583,11 +623,11 @@ def gb300_arm(args):
     sampler.start()
     time.sleep(0.3)  # let the sampler take its first reading
     # the warm-up steps run directly before the timed region, so that the GPU enters it busy
-    R.rflbm_step(box.h, warm)
+    advance(R, box, warm, exchange)
     R.rflbm_synchronize(box.h)
     dist.barrier(info, info.local_rank)
     torch.cuda.synchronize()
-    ms = time_steps(R, torch, box, stream, args.steps)
+    ms = time_steps(R, torch, box, stream, args.steps, exchange)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     dist.barrier(info, info.local_rank)
@@ -608,7 +648,7 @@ def gb300_arm(args):
         t0 = time.perf_counter()
         for _ in range(k_e2e):
             R.rflbm_set_populations_f32(box.h, host_in)
-            R.rflbm_step(box.h, 1)
+            advance(R, box, 1, exchange)
             R.rflbm_get_populations_f32(box.h, host_out)
         e2e_s = dist.max_over_ranks(info, time.perf_counter() - t0, dev)
         e2e = {"value": info.world * n * k_e2e / e2e_s / 1e6, "unit": "MLUPS",
@@ -619,7 +659,7 @@ def gb300_arm(args):
 
     variants = {}
     accuracy = None
-    if not args.no_variants and info.world == 1:
+    if not args.no_variants and info.world == 1 and not slab:
         peak_v, _ = measured_peak()
         st_main = storage[args.storage]
         k = max(10, args.steps // 4)
@@ -678,9 +718,12 @@ def gb300_arm(args):
     peak, peak_kind = measured_peak()
     kname, kstem = kernel_name(kind, path, args.kT, 0, args.storage, args.pattern, pairs, odd_pairs)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(kstem, e),
+                "frac": achieved / peak, "traffic": None if slab else profiled_traffic(kstem, e),
                 "peak_source": f"hbm_gbs of {peak_kind}", "kernel": kname,
                 "algorithmic_bytes_per_launch": BYTES_PER_SITE[args.storage] * n}
+    if slab:
+        roofline["kernel"] = f"{kname}: boundary rows, interior rows, face exchange (per step)"
+        roofline["algorithmic_bytes_per_step"] = roofline.pop("algorithmic_bytes_per_launch")
     cpu = None
     if not args.no_cpu_baseline and info.world == 1:  # the oracle baseline is an N = 1 figure
         r = oracle_sample_rate(e, args.tau, args.kT, budget_s=12.0, steps=None)
@@ -689,7 +732,7 @@ def gb300_arm(args):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": info.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "storage_dtype": args.storage, "data": "synthetic", "config": workload(args),
+        "storage_dtype": args.storage, "data": "synthetic", "config": workload(args, info.world),
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -12,13 +12,17 @@
 // same way, whichever form it uses.
 //
 // Work per site (all FP32):
-//  1. the ten moments of order <= 2 by three sum-factorised sweeps (Eqs. 3-5):
+//  1. Reg-FLBM: the ten moments of order <= 2 by three sum-factorised sweeps (Eqs. 3-5):
 //     delta rho = rho - rho0, j = rho u, and the second Hermite moment
-//     a^(2)_ab = sum_i f_i (c_ia c_ib - delta_ab/3);
+//     a^(2)_ab = sum_i f_i (c_ia c_ib - delta_ab/3). BGK-FLBM: all 27 Hermite moments
+//     m_k = sum_i e_ki g_i (Eq. 5) by three sweeps of nine 1-D lines (4 operations each),
+//     since its relaxation keeps (1 - omega) of every non-conserved moment;
 //  2. the post-collision moments, divided by their norms b_k, in a tile M[p][q][r] of
-//     Hermite exponents: the equilibrium coefficients rho u_x^p u_y^q u_z^r (Eq. 21),
-//     the relaxed stress non-equilibrium a^(2) - rho u u (Eq. 20 with Eq. 15) for
-//     k = 4..9, the ghost non-equilibrium of Eq. 22 when omega_g != 1, and
+//     Hermite exponents: the equilibrium coefficients rho u_x^p u_y^q u_z^r (Eq. 21);
+//     Reg: the relaxed stress non-equilibrium a^(2) - rho u u (Eq. 20 with Eq. 15) for
+//     k = 4..9 and the ghost non-equilibrium of Eq. 22 when omega_g != 1; BGK:
+//     omega a_0,k + (1 - omega) m_k for every k >= 4, the density and momentum kept
+//     (Eq. 12 projected on the complete Hermite basis of the lattice); and
 //     phi_k r_k (Eqs. 9-10) for k = 4..26;
 //  3. the back transform f_i = w_i sum_k b_k^-1 e_ki m_k (Eq. 11) by three
 //     sum-factorised sweeps (4 operations per line of three) and the weights.
@@ -33,6 +37,9 @@ namespace rflbm_dev {
 
 enum : int { kModelReg = 0, kModelBgk = 1 };
 
+// The noise amplitude of Eq. 10 for mode k, relative to sqrt(rho), factors into a rate part
+// sqrt(kT omega (2 - omega)) shared by the modes of one relaxation rate and the mode part
+// sqrt(1 / (cs2 b_k)) = sqrt(3 / b_k), a constant of the lattice (mode_amp).
 struct CollideParams {
   float rho0;
   float omega;       // omega_h = 1/tau (the single rate of the BGK model)
@@ -40,8 +47,18 @@ struct CollideParams {
   float neq_off;     // (1 - omega_h) / b for the off-diagonal stress modes (b = 1/9)
   float ghost_keep;  // 1 - omega_g (ghost non-equilibrium kept by the Eq. 22 recursion)
   float sqrt_rho0;   // sqrt(rho0), used when Eq. 10 takes the reference density
-  float amp[23];     // sqrt(kT omega_k (2 - omega_k) / (cs2 b_k)) for k = 4..26
+  float amp_h;       // sqrt(kT omega_h (2 - omega_h)): the rate part for k = 4..9
+  float amp_g;       // sqrt(kT omega_g (2 - omega_g)) for k = 10..26 (BGK: omega_h)
 };
+
+// sqrt(3 / b_k) of mode k >= 1: with b = beta_p beta_q beta_r and beta = (1, 1/3, 2/9), every
+// h_1 factor of the mode contributes sqrt(3) and every h_2 factor 3 / sqrt(2).
+__host__ __device__ constexpr double mode_amp(int k) {
+  double a = 1.7320508075688772;  // sqrt(3)
+  const int e[3] = {p_of(k), q_of(k), r_of(k)};
+  for (int d = 0; d < 3; ++d) a *= e[d] == 1 ? 1.7320508075688772 : (e[d] == 2 ? 2.1213203435596424 : 1.0);
+  return a;
+}
 
 // e - 1 clamped at 0 (an exponent after one derivative; only used where e >= 1).
 __host__ __device__ constexpr int lo(int e) { return e > 0 ? e - 1 : 0; }
@@ -55,15 +72,6 @@ __device__ __forceinline__ void line_inverse(float L0, float L1, float L2, float
   om = a - L1;
   op = a + L1;
 }
-
-// Supplies the pre-collision value of tile entry (a, b, c) to the BGK update at the end of
-// the collision. By default the tile itself, which keeps its 27 values live in registers
-// through the whole collision; kernels that still hold the inputs in shared memory pass a
-// reader instead, and the registers are free in between.
-struct KeepTile {
-  template <class V>
-  __device__ __forceinline__ V operator()(int, int, int, V g) const { return g; }
-};
 
 // ---- lane-wise arithmetic
 __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
@@ -108,16 +116,28 @@ __device__ __forceinline__ void line_inverse_v(V L0, V L1, V L2, V& om, V& o0, V
   op = vadd(a, L1);
 }
 
-// Noise source for one site per thread: the normals drawn beforehand (SiteNoise), call j
-// giving the (radius, cos, sin) triples of Box-Muller pairs 2j and 2j + 1.
+// One line of the forward 1-D transform: from the values at c = -1, 0, +1 the projections on
+// h_0 = 1, h_1 = c and h_2 = c^2 - 1/3.
+template <class V>
+__device__ __forceinline__ void line_forward_v(V gm, V g0, V gp, V& H0, V& H1, V& H2) {
+  const V s = vadd(gp, gm);
+  H1 = vsub(gp, gm);
+  H0 = vadd(s, g0);
+  H2 = kfma(-1.0f / 3.0f, H0, s);
+}
+
+// Noise sources of the collision: noise(j, n0, n1) gives the normals of the two Box-Muller
+// pairs of Philox call j, n0[h] = r cos and n1[h] = r sin of pair h (the normals r_k of modes
+// k = 4j + 2h + 4 and 4j + 2h + 5).
+
+// One site per thread, the normals drawn beforehand (SiteNoise).
 struct DrawnNoise {
   const SiteNoise& n;
-  __device__ __forceinline__ void operator()(int j, float (&r)[2], float (&c)[2], float (&s)[2]) const {
+  __device__ __forceinline__ void operator()(int j, float (&n0)[2], float (&n1)[2]) const {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      r[h] = n.r[2 * j + h];
-      c[h] = n.c[2 * j + h];
-      s[h] = n.s[2 * j + h];
+      n0[h] = n.n[4 * j + 2 * h];
+      n1[h] = n.n[4 * j + 2 * h + 1];
     }
   }
 };
@@ -125,9 +145,9 @@ struct DrawnNoise {
 // Philox calls the two-site kernels draw before they wait for the previous step.
 constexpr int kPairPreDrawn = 2;
 
-// Noise source for two sites per thread (sites site0 and site0 + 1): Philox calls j < kPre
-// drawn beforehand by draw() (raw words, while the previous step drains), the later calls
-// when the collision needs them. Key: PhiloxKey or PhiloxRoundKeys.
+// Two sites per thread (sites site0 and site0 + 1): Philox calls j < kPre drawn beforehand
+// by draw() (raw words, while the previous step drains), the later calls when the collision
+// needs them. Key: PhiloxKey or PhiloxRoundKeys.
 template <int kPre, class Key>
 struct PairNoise {
   uint32_t site0, step, replica;
@@ -143,7 +163,7 @@ struct PairNoise {
       w[j][1] = call(site0 + 1u, j);
     }
   }
-  __device__ __forceinline__ void operator()(int j, float2 (&r)[2], float2 (&c)[2], float2 (&s)[2]) const {
+  __device__ __forceinline__ void operator()(int j, float2 (&n0)[2], float2 (&n1)[2]) const {
     uint4 a, b;
     if (j < kPre) {
       a = w[j < kPre ? j : 0][0];
@@ -152,10 +172,18 @@ struct PairNoise {
       a = call(site0, j);
       b = call(site0 + 1u, j);
     }
+    // the radius times cosine and sine of both sites as packed products (rounded as the
+    // scalar products of box_muller_normals)
+    float2 r[2], c[2], s[2];
     box_muller(a.x, a.y, r[0].x, c[0].x, s[0].x);
     box_muller(b.x, b.y, r[0].y, c[0].y, s[0].y);
     box_muller(a.z, a.w, r[1].x, c[1].x, s[1].x);
     box_muller(b.z, b.w, r[1].y, c[1].y, s[1].y);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      n0[h] = __fmul2_rn(r[h], c[h]);
+      n1[h] = __fmul2_rn(r[h], s[h]);
+    }
   }
 };
 
@@ -167,11 +195,124 @@ struct LatticeWeight {
   }
 };
 
-template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0, class V, class Noise,
-          class Reload, class OutWeight>
+// Adds phi_k r_k (Eqs. 9-10) to the scaled moments M of k = 4..26: M_k += sqrt(3 / b_k)
+// sqrt(kT omega_k (2 - omega_k) rho) r_k, the factor of each mode formed once per site (modes
+// of equal norm and rate share it).
+template <bool kNoise, bool kPhiRho0, class V, class Noise>
+__device__ __forceinline__ void inject_noise(V (&M)[3][3][3], V rho, const CollideParams& cp, const Noise& noise) {
+  if (kNoise) {
+    const V srho = kPhiRho0 ? splat<V>(cp.sqrt_rho0) : vsqrt(rho);
+    const V sh = kmul(cp.amp_h, srho), sg = kmul(cp.amp_g, srho);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      V n0[2], n1[2];
+      noise(j, n0, n1);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        // pair m = 2j + h gives r_k of modes k = 2m + 4 (cosine) and 2m + 5 (sine, unused
+        // for m = 11); a pair never mixes stress (k < 10) and ghost modes
+        const int k0 = 4 * j + 2 * h + 4, k1 = k0 + 1;
+        const V s = k0 < 10 ? sh : sg;
+        V& M0 = M[p_of(k0)][q_of(k0)][r_of(k0)];
+        M0 = vfma(kmul(float(mode_amp(k0)), s), n0[h], M0);
+        if (k1 < kQ) {
+          const int k1c = k1 < kQ ? k1 : 4;
+          V& M1 = M[p_of(k1c)][q_of(k1c)][r_of(k1c)];
+          M1 = vfma(kmul(float(mode_amp(k1c)), s), n1[h], M1);
+        }
+      }
+    }
+  }
+}
+
+// The back transform (Eq. 11; sweep z, then y, then x) of the scaled moments M into the
+// tile G, times the output weights.
+template <class V, class OutWeight>
+__device__ __forceinline__ void back_transform(V (&M)[3][3][3], V (&G)[3][3][3], const OutWeight& outw) {
+  V Z[3][3][3];  // [p][q][c]
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      line_inverse_v(M[p][q][0], M[p][q][1], M[p][q][2], Z[p][q][0], Z[p][q][1], Z[p][q][2]);
+  V Y[3][3][3];  // [p][b][c]
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      line_inverse_v(Z[p][0][c], Z[p][1][c], Z[p][2][c], Y[p][0][c], Y[p][1][c], Y[p][2][c]);
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      V o[3];
+      line_inverse_v(Y[0][b][c], Y[1][b][c], Y[2][b][c], o[0], o[1], o[2]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) G[a][b][c] = vmul(splat<V>(outw(a, b, c)), o[a]);
+    }
+}
+
+// BGK-FLBM (Eq. 12) in the moment space of the 27 Hermite modes, which span the lattice's
+// population space: every non-conserved scaled moment becomes
+// omega a_0,k / b_k + (1 - omega) m_k / b_k (+ noise), density and momentum are kept, and
+// the back transform gives f* = f^(0) + (1 - omega)(f - f^(0)) + the noise.
+template <bool kNoise, bool kPhiRho0, class V, class Noise, class OutWeight>
+__device__ __forceinline__ void collide_tile_bgk(V (&G)[3][3][3], const CollideParams& cp, const Noise& noise,
+                                                 const OutWeight& outw) {
+  // ---- 1. all 27 Hermite moments H[p][q][r] = sum g h_p(c_x) h_q(c_y) h_r(c_z): sweep x,
+  // then y, then z (the rest state drops out of every moment but H[0][0][0] = drho)
+  V X[3][3][3];  // [p][b][c]
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) line_forward_v(G[0][b][c], G[1][b][c], G[2][b][c], X[0][b][c], X[1][b][c], X[2][b][c]);
+  V Y[3][3][3];  // [p][q][c]
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) line_forward_v(X[p][0][c], X[p][1][c], X[p][2][c], Y[p][0][c], Y[p][1][c], Y[p][2][c]);
+  V M[3][3][3];  // [p][q][r]
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) line_forward_v(Y[p][q][0], Y[p][q][1], Y[p][q][2], M[p][q][0], M[p][q][1], M[p][q][2]);
+  const V drho = M[0][0][0], jx = M[1][0][0], jy = M[0][1][0], jz = M[0][0][1];
+
+  // ---- 2. relaxation towards the equilibrium coefficients rho u_x^p u_y^q u_z^r (Eq. 21)
+  const V rho = vadd(splat<V>(cp.rho0), drho);
+  const V inv_rho = vrcp(rho);
+  const V ux = vmul(jx, inv_rho), uy = vmul(jy, inv_rho), uz = vmul(jz, inv_rho);
+  // omega U[p] = omega u^p / beta_p and (1 - omega) / b for each mode
+  const float om = cp.omega;
+  const V Uy[3] = {splat<V>(1.0f), kmul(3.0f, uy), vmul(kmul(4.5f, uy), uy)};
+  const V Uz[3] = {splat<V>(1.0f), kmul(3.0f, uz), vmul(kmul(4.5f, uz), uz)};
+  const V RX[3] = {kmul(om, rho), kmul(3.0f * om, jx), vmul(kmul(4.5f * om, jx), ux)};
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        if (p + q + r < 2) continue;  // density and momentum are kept
+        const V yz = q == 0 ? Uz[r] : (r == 0 ? Uy[q] : vmul(Uy[q], Uz[r]));
+        const V eq = (q == 0 && r == 0) ? RX[p] : vmul(RX[p], yz);
+        M[p][q][r] = kfma((1.0f - om) * float(1.0 / bnorm(p, q, r)), M[p][q][r], eq);
+      }
+  // scaled conserved moments m / b: drho, 3 j
+  M[1][0][0] = kmul(3.0f, jx);
+  M[0][1][0] = kmul(3.0f, jy);
+  M[0][0][1] = kmul(3.0f, jz);
+  inject_noise<kNoise, kPhiRho0>(M, rho, cp, noise);
+  back_transform(M, G, outw);
+}
+
+template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0, class V, class Noise, class OutWeight>
 __device__ __forceinline__ void collide_tile(V (&G)[3][3][3], const CollideParams& cp,
-                                          const Noise& noise, const Reload& reload,
-                                          const OutWeight& outw) {
+                                          const Noise& noise, const OutWeight& outw) {
+  if (kModel == kModelBgk) {
+    collide_tile_bgk<kNoise, kPhiRho0>(G, cp, noise, outw);
+    return;
+  }
   // ---- 1. moments of order <= 2 (sweep x, then y, then z)
   V X0[3][3], X1[3][3], X2[3][3];
 #pragma unroll
@@ -217,10 +358,8 @@ __device__ __forceinline__ void collide_tile(V (&G)[3][3][3], const CollideParam
   const V Uy[3] = {splat<V>(1.0f), kmul(3.0f, uy), vmul(kmul(4.5f, uy), uy)};
   const V Uz[3] = {splat<V>(1.0f), kmul(3.0f, uz), vmul(kmul(4.5f, uz), uz)};
   const float om = cp.omega;
-  const bool bgk = kModel == kModelBgk;
-  // RX[p] = rho U_x[p] (BGK: times omega, which scales every equilibrium moment)
-  const V RX[3] = {bgk ? kmul(om, rho) : rho, kmul(bgk ? 3.0f * om : 3.0f, jx),
-                   vmul(kmul(bgk ? 4.5f * om : 4.5f, jx), ux)};
+  // RX[p] = rho U_x[p]
+  const V RX[3] = {rho, kmul(3.0f, jx), vmul(kmul(4.5f, jx), ux)};
   V M[3][3][3];
 #pragma unroll
   for (int p = 0; p < 3; ++p)
@@ -233,7 +372,7 @@ __device__ __forceinline__ void collide_tile(V (&G)[3][3][3], const CollideParam
       }
 
   const V vom = splat<V>(om);
-  if (kModel == kModelReg) {
+  {
     // conserved modes are kept exactly
     M[0][0][0] = drho;
     M[0][1][0] = kmul(3.0f, jy);
@@ -274,80 +413,17 @@ __device__ __forceinline__ void collide_tile(V (&G)[3][3][3], const CollideParam
             M[p][q][r] = kfma(cp.ghost_keep * float(1.0 / bnorm(p, q, r)), t, M[p][q][r]);
           }
     }
-  } else {
-    // BGK: omega f^(0) here (omega is in RX), (1 - omega) f added after the back
-    // transform; the shifted density mode is omega drho
-    M[0][0][0] = vmul(vom, drho);
-    M[0][1][0] = vmul(vom, kmul(3.0f, jy));
-    M[0][0][1] = vmul(vom, kmul(3.0f, jz));
   }
-  if (kNoise) {
-    // Box-Muller pair m gives the normals r_k of modes k = 2m + 4 (cosine) and 2m + 5 (sine)
-    const V srho = kPhiRho0 ? splat<V>(cp.sqrt_rho0) : vsqrt(rho);
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      V nr[2], nc[2], ns[2];
-      noise(j, nr, nc, ns);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = 2 * j + h;
-        const int k0 = 2 * m + 4, k1 = 2 * m + 5;
-        V& M0 = M[p_of(k0)][q_of(k0)][r_of(k0)];
-        const V rr = vmul(nr[h], srho);
-        if (k1 < kQ && same_amplitude(k0, k1)) {
-          V& M1 = M[p_of(k1)][q_of(k1)][r_of(k1)];
-          const V a = kmul(cp.amp[k0 - 4], rr);
-          M0 = vfma(a, nc[h], M0);
-          M1 = vfma(a, ns[h], M1);
-        } else {
-          M0 = kfma(cp.amp[k0 - 4], vmul(rr, nc[h]), M0);
-          if (k1 < kQ) {
-            const int k1c = k1 < kQ ? k1 : 4;  // (k1 = 27 does not exist: pair 11's sine is unused)
-            V& M1 = M[p_of(k1c)][q_of(k1c)][r_of(k1c)];
-            M1 = kfma(cp.amp[k1c - 4], vmul(rr, ns[h]), M1);
-          }
-        }
-      }
-    }
-  }
-
-  // ---- 3. back transform (sweep z, then y, then x) and the lattice weights
-  V Z[3][3][3];  // [p][q][c]
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      line_inverse_v(M[p][q][0], M[p][q][1], M[p][q][2], Z[p][q][0], Z[p][q][1], Z[p][q][2]);
-  V Y[3][3][3];  // [p][b][c]
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      line_inverse_v(Z[p][0][c], Z[p][1][c], Z[p][2][c], Y[p][0][c], Y[p][1][c], Y[p][2][c]);
-#pragma unroll
-  for (int b = 0; b < 3; ++b)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      V o[3];
-      line_inverse_v(Y[0][b][c], Y[1][b][c], Y[2][b][c], o[0], o[1], o[2]);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const V wt = splat<V>(outw(a, b, c));
-        if (kModel == kModelBgk) {
-          G[a][b][c] = vfma(splat<V>(1.0f - om), reload(a, b, c, G[a][b][c]), vmul(wt, o[a]));
-        } else {
-          G[a][b][c] = vmul(wt, o[a]);
-        }
-      }
-    }
+  inject_noise<kNoise, kPhiRho0>(M, rho, cp, noise);
+  back_transform(M, G, outw);
 }
 
 // The collision of one site per thread with its normals drawn beforehand and the lattice
 // weights (the storage scale is applied by the caller).
-template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0, class Reload = KeepTile>
+template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
 __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideParams& cp,
-                                             const SiteNoise& noise, const Reload& reload = Reload()) {
-  collide_tile<kModel, kNoise, kGhostNeq, kPhiRho0>(G, cp, DrawnNoise{noise}, reload, LatticeWeight());
+                                             const SiteNoise& noise) {
+  collide_tile<kModel, kNoise, kGhostNeq, kPhiRho0>(G, cp, DrawnNoise{noise}, LatticeWeight());
 }
 
 }  // namespace rflbm_dev

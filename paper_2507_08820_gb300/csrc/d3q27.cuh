@@ -72,12 +72,6 @@ __host__ __device__ constexpr int r_of(int k) {
   constexpr int t[kQ] = {0, 0, 0, 1, 0, 0, 2, 0, 1, 1, 0, 1, 0, 2, 2, 1, 1, 0, 2, 2, 2, 1, 1, 2, 1, 2, 2};
   return t[k];
 }
-// Modes k and l relax at the same rate and have the same norm: equal noise amplitudes.
-__host__ __device__ constexpr bool same_amplitude(int k, int l) {
-  return bnorm(p_of(k), q_of(k), r_of(k)) == bnorm(p_of(l), q_of(l), r_of(l)) &&
-         ((k < 10) == (l < 10));
-}
-
 // Table II index k of the mode with Hermite exponents (p, q, r).
 __host__ __device__ constexpr int mode_of(int p, int q, int r) {
   constexpr int t[kQ] = {0, 3, 6, 2, 9, 14, 5, 15, 19, 1, 8, 13, 7, 16, 20,

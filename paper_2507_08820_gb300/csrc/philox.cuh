@@ -117,11 +117,19 @@ __device__ __forceinline__ void box_muller(uint32_t x0, uint32_t x1, float& r, f
   s = -st;
 }
 
-// The 24 normals of one site at one step as 12 (radius, cos, sin) triples, pair m of
-// call j at index 2*j + m (normals n[4j + 2m] = r c, n[4j + 2m + 1] = r s).
+// The 24 normals of one site at one step: Box-Muller pair m of call j (m = 2j, 2j + 1)
+// gives n[2m] = r cos and n[2m + 1] = r sin, so n[4j .. 4j + 3] come from call j.
 struct SiteNoise {
-  float r[12], c[12], s[12];
+  float n[24];
 };
+
+// The two normals of one Box-Muller pair.
+__device__ __forceinline__ void box_muller_normals(uint32_t x0, uint32_t x1, float& n0, float& n1) {
+  float r, c, s;
+  box_muller(x0, x1, r, c, s);
+  n0 = __fmul_rn(r, c);
+  n1 = __fmul_rn(r, s);
+}
 
 // Calls j0 <= j < j1 of site_noise (the draws can be split around other work).
 template <int j0, int j1>
@@ -130,8 +138,8 @@ __device__ __forceinline__ void site_noise_part(uint32_t site, uint32_t step, ui
 #pragma unroll
   for (int j = j0; j < j1; ++j) {
     const uint4 w = philox4x32_10(make_uint4(site, step, (uint32_t)j, replica), k0, k1);
-    box_muller(w.x, w.y, out.r[2 * j], out.c[2 * j], out.s[2 * j]);
-    box_muller(w.z, w.w, out.r[2 * j + 1], out.c[2 * j + 1], out.s[2 * j + 1]);
+    box_muller_normals(w.x, w.y, out.n[4 * j], out.n[4 * j + 1]);
+    box_muller_normals(w.z, w.w, out.n[4 * j + 2], out.n[4 * j + 3]);
   }
 }
 
@@ -142,26 +150,17 @@ __device__ __forceinline__ void site_noise_part(uint32_t site, uint32_t step, ui
 #pragma unroll
   for (int j = j0; j < j1; ++j) {
     const uint4 w = philox4x32_10(make_uint4(site, step, (uint32_t)j, replica), rk);
-    box_muller(w.x, w.y, out.r[2 * j], out.c[2 * j], out.s[2 * j]);
-    box_muller(w.z, w.w, out.r[2 * j + 1], out.c[2 * j + 1], out.s[2 * j + 1]);
+    box_muller_normals(w.x, w.y, out.n[4 * j], out.n[4 * j + 1]);
+    box_muller_normals(w.z, w.w, out.n[4 * j + 2], out.n[4 * j + 3]);
   }
 }
 
 __device__ __forceinline__ void site_noise(uint32_t site, uint32_t step, uint32_t replica,
                                            uint32_t k0, uint32_t k1, SiteNoise& out) {
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    const uint4 w = philox4x32_10(make_uint4(site, step, (uint32_t)j, replica), k0, k1);
-    box_muller(w.x, w.y, out.r[2 * j], out.c[2 * j], out.s[2 * j]);
-    box_muller(w.z, w.w, out.r[2 * j + 1], out.c[2 * j + 1], out.s[2 * j + 1]);
-  }
+  site_noise_part<0, 6>(site, step, replica, k0, k1, out);
 }
 
-// Normal n[m] (m = 0..23) of a SiteNoise, optionally scaled by a per-site factor.
-__device__ __forceinline__ float normal_at(const SiteNoise& n, int m, float scale = 1.0f) {
-  const int pair = m >> 1;
-  const float rr = n.r[pair] * scale;
-  return (m & 1) ? rr * n.s[pair] : rr * n.c[pair];
-}
+// Normal n[m] (m = 0..23) of a SiteNoise.
+__device__ __forceinline__ float normal_at(const SiteNoise& n, int m) { return n.n[m]; }
 
 }  // namespace rflbm_dev

@@ -169,16 +169,11 @@ void fill_collide_params(rflbm* h) {
   cp.neq_off = (float)((1.0 - om) / bnorm(1, 1, 0));
   cp.ghost_keep = (float)(1.0 - og);
   cp.sqrt_rho0 = (float)std::sqrt(c.rho0);
-  const double cs2 = 1.0 / 3.0;
-  for (int p = 0; p < 3; ++p)
-    for (int q = 0; q < 3; ++q)
-      for (int r = 0; r < 3; ++r) {
-        if (p + q + r < 2) continue;
-        const int k = mode_of(p, q, r);
-        // the BGK model relaxes every mode at omega (Eq. 12); Reg splits hydro/ghost
-        const double ok = (c.model == RFLBM_MODEL_BGK || k < 10) ? om : og;
-        cp.amp[k - 4] = (float)std::sqrt(c.kT * ok * (2.0 - ok) / (cs2 * bnorm(p, q, r)));
-      }
+  // Eq. 10: phi_k = sqrt(rho kT omega_k (2 - omega_k) / (cs2 b_k)); the BGK model relaxes
+  // every mode at omega (Eq. 12), Reg splits stress (omega_h) and ghost (omega_g) modes
+  const double og_noise = c.model == RFLBM_MODEL_BGK ? om : og;
+  cp.amp_h = (float)std::sqrt(c.kT * om * (2.0 - om));
+  cp.amp_g = (float)std::sqrt(c.kT * og_noise * (2.0 - og_noise));
   h->variant.model = c.model == RFLBM_MODEL_BGK ? kModelBgk : kModelReg;
   h->variant.noise = c.kT > 0.0;
   h->variant.ghost_neq = (c.model == RFLBM_MODEL_REG) && (og != 1.0);

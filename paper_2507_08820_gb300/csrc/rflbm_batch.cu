@@ -33,20 +33,29 @@
 
 namespace rflbm_dev {
 
+// One replica as the step kernels see it. The kernels take the descriptors of up to
+// kGroupReps replicas in their launch parameters (the constant bank): a CTA reads its
+// replica's fields there, with no per-CTA copy, and the compiler may reload any of them
+// instead of holding it in a register.
 struct ReplicaDev {
   Geometry geo;
   CollideParams cp;
   StoreScale ss;
   void* buf[2];
-  uint32_t key0, key1;
-  int noise;          // kT > 0
-  int cur;            // buffer holding the state at the start of a run
+  const CUtensorMap* maps;  // rows tiles, per buffer b: [2 b] loads (nx, rows, 1, 3), [2 b + 1] stores (nx, rows, 1, 27)
   int64_t tile_begin;  // first global tile index of this replica
   int64_t ntiles;      // tiles per step
+  uint32_t key0, key1;
   uint32_t rows;       // rows per tile (rows tiles), 0: sites tiles
   uint32_t yblocks;    // row blocks per slab: ceil(ny / rows)
-  const CUtensorMap* maps;  // rows tiles, per buffer b: [2 b] loads (nx, rows, 1, 3), [2 b + 1] stores (nx, rows, 1, 27)
+  int noise;           // kT > 0
 };
+
+constexpr int kGroupReps = 64;  // replicas whose descriptors one launch carries
+struct ReplicaTable {
+  ReplicaDev r[kGroupReps];
+};
+static_assert(sizeof(ReplicaTable) <= 16 * 1024, "the replica table stays well inside the launch parameters");
 
 // Dynamic shared memory of a rows tile: 9 groups of 3 planes x kTile sites (each group
 // rounded to 128 bytes), which then holds the 27-plane output tile.
@@ -63,38 +72,32 @@ constexpr int kBatchGroups = 9;  // source rows (c_y, c_z) of a site
 
 // One step of the tiles [tile0, tile0 + gridDim.x) of the tile table, all of one kind
 // (rows tiles when kRows, else sites tiles).
-// Rows tiles are held to 56 registers (65536 / (kTile 56) resident CTAs per SM): the
-// replica's collision parameters come from shared memory, not from the constant bank.
-// (At tile 192, 64 registers (5 CTAs per SM, 8 B of spill) measured 76.1 % and 80 (4 CTAs,
-// no spill) 65.4 %, against 79.2 % here with 40 B of spill.)
+// Rows tiles are held to 56 registers (65536 / (kTile 56) resident CTAs per SM), which they
+// fit without spilling: the replica's parameters are read from the launch parameters and
+// the noise is held as 24 normals.
 template <int kStore, int kTile, bool kRows>
 __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
-    k_batch_step(const ReplicaDev* __restrict__ reps, const int* __restrict__ tile_rep, int64_t tile0,
-                 const unsigned long long* step0_ptr, uint32_t k, int* err) {
+    k_batch_step(const __grid_constant__ ReplicaTable tab, const int* __restrict__ tile_rep, int64_t tile0,
+                 const unsigned long long* run, uint32_t k, int* err) {
   using S = Storage<kStore>;
   using T = typename S::T;
   constexpr int kGroup = (int)(batch_group_bytes(kTile, sizeof(T)) / sizeof(T));  // elements
   constexpr int rn = kTile;  // sites of a rows tile (R nx)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
-  __shared__ __align__(16) ReplicaDev rep;  // this tile's replica
   T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
   const int tid = threadIdx.x;
   const int64_t j = tile0 + blockIdx.x;
-  const int r = __ldg(tile_rep + j);
-  {
-    const int* from = reinterpret_cast<const int*>(reps + r);
-    int* to = reinterpret_cast<int*>(&rep);
-    for (int w = tid; w < (int)(sizeof(ReplicaDev) / sizeof(int)); w += kTile) to[w] = __ldg(from + w);
-  }
+  const ReplicaDev& rep = tab.r[__ldg(tile_rep + j)];  // this tile's replica
   if (kRows && tid == 0) {
     mbar_init(&bar, 1);
     mbar_init_fence();
   }
-  __syncthreads();
+  if (kRows) __syncthreads();
   grid_launch_dependents();
-  const uint32_t step = (uint32_t)*step0_ptr + k;
-  const int parity = (rep.cur + (int)(k & 1u)) & 1;
+  // run[0]: the first step of this run, run[1]: the buffer holding its state
+  const uint32_t step = (uint32_t)__ldg(run) + k;
+  const int parity = (int)((__ldg(run + 1) + k) & 1u);
   const T* src = static_cast<const T*>(rep.buf[parity]);
   T* dst = static_cast<T*>(rep.buf[parity ^ 1]);
   const uint32_t li = (uint32_t)(j - rep.tile_begin);  // tile index within the replica
@@ -132,10 +135,10 @@ __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
   const uint32_t row = fastdiv((uint32_t)tid, rep.geo.div_nx);
   const uint32_t x = (uint32_t)tid - row * nx;
   const bool active = row < nrows;
-  // the noise is drawn while the previous step drains (calls 0 and 1) and while the copies
-  // are in flight (calls 2 to 5), as in the single-box kernel
-  SiteNoise noise;
+  // the normals of calls 0 and 1 while the previous step drains, of calls 2 to 5 while the
+  // copies are in flight
   const uint32_t site = x + nx * ((y0 + row) + ny * z);
+  SiteNoise noise;
   if (rep.noise && active) site_noise_part<0, kBatchPreWaitCalls>(site, step, 0u, rep.key0, rep.key1, noise);
 
   grid_dependency_wait();  // the previous step's writes (our source) are complete
@@ -216,8 +219,8 @@ __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
 // collision of the single-box two-site kernels, the storage scale folded into the weights.
 template <int kStore, int kTile>
 __global__ void __launch_bounds__(kTile / 2)
-    k_batch_rows_pair(const ReplicaDev* __restrict__ reps, const int* __restrict__ tile_rep,
-                      const unsigned long long* step0_ptr, uint32_t k, int* err) {
+    k_batch_rows_pair(const __grid_constant__ ReplicaTable tab, const int* __restrict__ tile_rep, int64_t tile0,
+                      const unsigned long long* run, uint32_t k, int* err) {
   using S = Storage<kStore>;
   using T = typename S::T;
   constexpr int kGroup = (int)(batch_group_bytes(kTile, sizeof(T)) / sizeof(T));
@@ -225,24 +228,18 @@ __global__ void __launch_bounds__(kTile / 2)
   constexpr int kThreads = kTile / 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
-  __shared__ __align__(16) ReplicaDev rep;
   T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
   const int tid = threadIdx.x;
-  const int64_t j = blockIdx.x;
-  const int r = __ldg(tile_rep + j);
-  {
-    const int* from = reinterpret_cast<const int*>(reps + r);
-    int* to = reinterpret_cast<int*>(&rep);
-    for (int w = tid; w < (int)(sizeof(ReplicaDev) / sizeof(int)); w += kThreads) to[w] = __ldg(from + w);
-  }
+  const int64_t j = tile0 + blockIdx.x;
+  const ReplicaDev& rep = tab.r[__ldg(tile_rep + j)];
   if (tid == 0) {
     mbar_init(&bar, 1);
     mbar_init_fence();
   }
   __syncthreads();
   grid_launch_dependents();
-  const uint32_t step = (uint32_t)*step0_ptr + k;
-  const int parity = (rep.cur + (int)(k & 1u)) & 1;
+  const uint32_t step = (uint32_t)__ldg(run) + k;
+  const int parity = (int)((__ldg(run + 1) + k) & 1u);
   const T* src = static_cast<const T*>(rep.buf[parity]);
   const uint32_t li = (uint32_t)(j - rep.tile_begin);
 
@@ -317,9 +314,9 @@ __global__ void __launch_bounds__(kTile / 2)
           G[a][b][c] = v;
         }
     if (rep.noise)
-      collide_tile<kModelReg, true, false, false>(G, rep.cp, noise, KeepTile(), ScaledWeight<kStore>{rep.ss});
+      collide_tile<kModelReg, true, false, false>(G, rep.cp, noise, ScaledWeight<kStore>{rep.ss});
     else
-      collide_tile<kModelReg, false, false, false>(G, rep.cp, noise, KeepTile(), ScaledWeight<kStore>{rep.ss});
+      collide_tile<kModelReg, false, false, false>(G, rep.cp, noise, ScaledWeight<kStore>{rep.ss});
   }
   __syncthreads();
   if (active) {
@@ -351,11 +348,18 @@ static cudaError_t set_smem_t() {
   return cudaFuncSetAttribute(k_batch_step<kStore, kTile, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// nsteps steps over all tiles: per step one launch of the rows tiles [0, rows_tiles) and
-// one of the sites tiles [rows_tiles, tiles), chained by programmatic dependent launch.
+// One launch group: the descriptors of up to kGroupReps replicas and the global tile ranges
+// of their rows tiles and of their sites tiles.
+struct BatchLaunch {
+  ReplicaTable tab;
+  int64_t rows_begin, rows_end, sites_begin, sites_end;
+};
+
+// nsteps steps over all tiles: per step and launch group one launch of its rows tiles and
+// one of its sites tiles, chained by programmatic dependent launch.
 template <int kStore, int kTile>
-static cudaError_t launch_batch_t(const ReplicaDev* reps, const int* tile_rep, int64_t tiles, int64_t rows_tiles,
-                                  int64_t nsteps, const unsigned long long* step0, int* err, cudaStream_t st) {
+static cudaError_t launch_batch_t(const BatchLaunch* groups, int ngroups, const int* tile_rep, int64_t nsteps,
+                                  const unsigned long long* run, int* err, cudaStream_t st) {
   if (cudaError_t e = set_smem_t<kStore, kTile>()) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kTile);
@@ -366,26 +370,30 @@ static cudaError_t launch_batch_t(const ReplicaDev* reps, const int* tile_rep, i
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   for (int64_t k = 0; k < nsteps; ++k) {
-    if (rows_tiles > 0) {
-      cfg.gridDim = dim3((unsigned)rows_tiles);
-      cfg.dynamicSmemBytes = batch_smem_bytes(kTile, storage_bytes(kStore));
-      cudaError_t e;
-      if constexpr (batch_rows_pairs<kStore>()) {
-        cfg.blockDim = dim3(kTile / 2);
-        e = cudaLaunchKernelEx(&cfg, k_batch_rows_pair<kStore, kTile>, reps, tile_rep, step0, (uint32_t)k, err);
-        cfg.blockDim = dim3(kTile);
-      } else {
-        e = cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, true>, reps, tile_rep, (int64_t)0, step0,
-                               (uint32_t)k, err);
+    for (int g = 0; g < ngroups; ++g) {
+      const BatchLaunch& L = groups[g];
+      if (L.rows_end > L.rows_begin) {
+        cfg.gridDim = dim3((unsigned)(L.rows_end - L.rows_begin));
+        cfg.dynamicSmemBytes = batch_smem_bytes(kTile, storage_bytes(kStore));
+        cudaError_t e;
+        if constexpr (batch_rows_pairs<kStore>()) {
+          cfg.blockDim = dim3(kTile / 2);
+          e = cudaLaunchKernelEx(&cfg, k_batch_rows_pair<kStore, kTile>, L.tab, tile_rep, L.rows_begin, run,
+                                 (uint32_t)k, err);
+          cfg.blockDim = dim3(kTile);
+        } else {
+          e = cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, true>, L.tab, tile_rep, L.rows_begin, run,
+                                 (uint32_t)k, err);
+        }
+        if (e != cudaSuccess) return e;
       }
-      if (e != cudaSuccess) return e;
-    }
-    if (tiles > rows_tiles) {
-      cfg.gridDim = dim3((unsigned)(tiles - rows_tiles));
-      cfg.dynamicSmemBytes = 0;
-      const cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, false>, reps, tile_rep, rows_tiles,
-                                               step0, (uint32_t)k, err);
-      if (e != cudaSuccess) return e;
+      if (L.sites_end > L.sites_begin) {
+        cfg.gridDim = dim3((unsigned)(L.sites_end - L.sites_begin));
+        cfg.dynamicSmemBytes = 0;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, false>, L.tab, tile_rep,
+                                                 L.sites_begin, run, (uint32_t)k, err);
+        if (e != cudaSuccess) return e;
+      }
     }
   }
   return cudaSuccess;
@@ -437,11 +445,10 @@ static int batch_occupancy(int storage, int tile) {
   return 1;
 }
 
-static cudaError_t launch_batch(int storage, int tile, const ReplicaDev* reps, const int* tile_rep,
-                                int64_t tiles, int64_t rows_tiles, int64_t nsteps,
-                                const unsigned long long* step0, int* err, cudaStream_t st) {
+static cudaError_t launch_batch(int storage, int tile, const BatchLaunch* groups, int ngroups, const int* tile_rep,
+                                int64_t nsteps, const unsigned long long* run, int* err, cudaStream_t st) {
   RFLBM_BATCH_DISPATCH(storage, tile,
-                       return (launch_batch_t<S, T>(reps, tile_rep, tiles, rows_tiles, nsteps, step0, err, st)));
+                       return (launch_batch_t<S, T>(groups, ngroups, tile_rep, nsteps, run, err, st)));
   return cudaErrorInvalidValue;
 }
 
@@ -458,14 +465,15 @@ struct rflbm_batch {
   cudaStream_t stream = nullptr;
   std::vector<rflbm_replica_t> cfg;
   std::vector<ReplicaDev> host;
-  ReplicaDev* dev_reps = nullptr;
-  int* tile_rep = nullptr;
+  std::vector<BatchLaunch> groups;  // launch groups of kGroupReps replicas
+  int cur = 0;                      // buffer holding every replica's current state
+  int* tile_rep = nullptr;          // per global tile: its replica's index within its group
   CUtensorMap* maps = nullptr;  // 4 per replica (rows tiles), device memory
   int64_t tiles = 0;
   int64_t rows_tiles = 0;  // tiles [0, rows_tiles) are rows tiles, the rest sites tiles
   int tile = 256;
   int ctas_per_sm = 1;
-  unsigned long long* step0 = nullptr;     // first step index of the current run (device)
+  unsigned long long* run = nullptr;  // device: first step of the current run, its buffer
   int* err = nullptr;
   double* partials = nullptr;
   int stat_blocks = 0;
@@ -500,11 +508,6 @@ int bcuda(cudaError_t e, const char* what) {
 
 int64_t pstride(int64_t n) { return (n + 63) / 64 * 64; }
 
-int upload_reps(rflbm_batch* b) {
-  BCUDA(cudaMemcpyAsync(b->dev_reps, b->host.data(), sizeof(ReplicaDev) * b->n, cudaMemcpyHostToDevice, b->stream),
-        "uploading replica descriptors");
-  return RFLBM_OK;
-}
 
 // Builds the per-replica descriptors, their tensor maps and the tile map for tile size
 // `tile` (CTA threads). A replica takes rows tiles when its row is a whole number of
@@ -534,21 +537,31 @@ int layout_tiles(rflbm_batch* b, int tile) {
     }
     d.ntiles = d.rows ? (int64_t)g.nz * d.yblocks : ((int64_t)g.n + tile - 1) / tile;
   }
-  // rows tiles first, then sites tiles (one launch each per step)
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int r = 0; r < b->n; ++r) {
-      ReplicaDev& d = b->host[r];
-      if ((d.rows != 0) != (pass == 0)) continue;
-      d.tile_begin = tiles;
-      tiles += d.ntiles;
+  // per launch group of kGroupReps replicas: its rows tiles, then its sites tiles
+  const int ngroups = (b->n + kGroupReps - 1) / kGroupReps;
+  b->groups.assign((size_t)ngroups, BatchLaunch{});
+  b->rows_tiles = 0;
+  for (int g = 0; g < ngroups; ++g) {
+    BatchLaunch& L = b->groups[(size_t)g];
+    const int r0 = g * kGroupReps, r1 = std::min(b->n, r0 + kGroupReps);
+    for (int pass = 0; pass < 2; ++pass) {
+      (pass == 0 ? L.rows_begin : L.sites_begin) = tiles;
+      for (int r = r0; r < r1; ++r) {
+        ReplicaDev& d = b->host[r];
+        if ((d.rows != 0) != (pass == 0)) continue;
+        d.tile_begin = tiles;
+        tiles += d.ntiles;
+      }
+      (pass == 0 ? L.rows_end : L.sites_end) = tiles;
     }
-    if (pass == 0) b->rows_tiles = tiles;
+    b->rows_tiles += L.rows_end - L.rows_begin;
   }
   BCUDA(cudaMemcpy(b->maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice),
         "uploading tensor maps");
   std::vector<int> map((size_t)tiles);
   for (int r = 0; r < b->n; ++r)
-    for (int64_t j = 0; j < b->host[r].ntiles; ++j) map[(size_t)(b->host[r].tile_begin + j)] = r;
+    for (int64_t j = 0; j < b->host[r].ntiles; ++j) map[(size_t)(b->host[r].tile_begin + j)] = r % kGroupReps;
+  for (int r = 0; r < b->n; ++r) b->groups[(size_t)(r / kGroupReps)].tab.r[r % kGroupReps] = b->host[r];
   cudaFree(b->tile_rep);
   b->tile_rep = nullptr;
   BCUDA(cudaMalloc(&b->tile_rep, sizeof(int) * (size_t)tiles), "allocating the tile map");
@@ -565,12 +578,12 @@ int layout_tiles(rflbm_batch* b, int tile) {
     b->graph = nullptr;
   }
   b->graph_steps = -1;
-  return upload_reps(b);
+  return RFLBM_OK;
 }
 
 // The launch sequence of one run: one step kernel over all tiles per step.
 int enqueue_run(rflbm_batch* b, int64_t nsteps, cudaStream_t st) {
-  BCUDA(launch_batch(b->storage, b->tile, b->dev_reps, b->tile_rep, b->tiles, b->rows_tiles, nsteps, b->step0,
+  BCUDA(launch_batch(b->storage, b->tile, b->groups.data(), (int)b->groups.size(), b->tile_rep, nsteps, b->run,
                      b->err, st),
         "launching the batched step kernel");
   return RFLBM_OK;
@@ -590,8 +603,8 @@ int bsync(rflbm_batch* b, const char* what) {
 // Runs n steps through a CUDA graph of the launch sequence (captured once per n; the
 // starting step is read by the kernel from device memory, written before each launch).
 int run_graph(rflbm_batch* b, int64_t n) {
-  const unsigned long long s0 = (unsigned long long)b->step;
-  BCUDA(cudaMemcpyAsync(b->step0, &s0, sizeof(s0), cudaMemcpyHostToDevice, b->stream), "setting the step index");
+  const unsigned long long r0[2] = {(unsigned long long)b->step, (unsigned long long)b->cur};
+  BCUDA(cudaMemcpyAsync(b->run, r0, sizeof(r0), cudaMemcpyHostToDevice, b->stream), "setting the step index");
   if (!b->exec || b->graph_steps != n) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -668,21 +681,15 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
     g.div_nx = make_fastdiv(g.nx);
     g.div_nxy = make_fastdiv(g.nxy);
     // collision and noise parameters: the single-box handle's (Reg-FLBM, omega_g = 1)
-    const double om = 1.0 / c.tau, cs2 = 1.0 / 3.0;
+    const double om = 1.0 / c.tau;
     d.cp.rho0 = (float)rho0;
     d.cp.omega = (float)om;
     d.cp.neq_diag = (float)((1.0 - om) / bnorm(2, 0, 0));
     d.cp.neq_off = (float)((1.0 - om) / bnorm(1, 1, 0));
     d.cp.ghost_keep = 0.0f;
     d.cp.sqrt_rho0 = (float)std::sqrt(rho0);
-    for (int p = 0; p < 3; ++p)
-      for (int q = 0; q < 3; ++q)
-        for (int s = 0; s < 3; ++s) {
-          if (p + q + s < 2) continue;
-          const int k = mode_of(p, q, s);
-          const double ok = k < 10 ? om : 1.0;
-          d.cp.amp[k - 4] = (float)std::sqrt(c.kT * ok * (2.0 - ok) / (cs2 * bnorm(p, q, s)));
-        }
+    d.cp.amp_h = (float)std::sqrt(c.kT * om * (2.0 - om));  // Eq. 10 rate parts (omega_g = 1)
+    d.cp.amp_g = (float)std::sqrt(c.kT);
     const double wc[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
     for (int k = 0; k < 4; ++k) {
       if (b->storage == kStoreF32) {
@@ -696,7 +703,6 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
     d.key0 = (uint32_t)(c.seed & 0xffffffffu);
     d.key1 = (uint32_t)(c.seed >> 32);
     d.noise = c.kT > 0.0;
-    d.cur = 0;
     for (int k = 0; k < 2 && rc == RFLBM_OK; ++k) {
       cudaError_t e = cudaMalloc(&d.buf[k], (size_t)g.ps * kQ * elem);
       if (e == cudaSuccess) e = cudaMemset(d.buf[k], 0, (size_t)g.ps * kQ * elem);
@@ -704,9 +710,8 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
     }
   }
   if (rc == RFLBM_OK) {
-    cudaError_t e = cudaMalloc((void**)&b->dev_reps, sizeof(ReplicaDev) * n);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->step0, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(b->step0, 0, sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc((void**)&b->run, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(b->run, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(int));
     if (e != cudaSuccess) rc = bcuda(e, "allocating batch descriptors");
@@ -759,10 +764,9 @@ void rflbm_batch_destroy(rflbm_batch_t* b) {
     cudaFree(d.buf[0]);
     cudaFree(d.buf[1]);
   }
-  cudaFree(b->dev_reps);
   cudaFree(b->tile_rep);
   cudaFree(b->maps);
-  cudaFree(b->step0);
+  cudaFree(b->run);
   cudaFree(b->err);
   cudaFree(b->partials);
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -794,14 +798,12 @@ int rflbm_batch_replica_dims(const rflbm_batch_t* b, int r, int* nx, int* ny, in
 
 int rflbm_batch_init_rest(rflbm_batch_t* b) {
   if (!b) return bfail(RFLBM_EINVAL, "batch handle is NULL");
-  for (auto& d : b->host) {
-    d.cur = 0;
+  for (auto& d : b->host)
     BCUDA(cudaMemsetAsync(d.buf[0], 0, (size_t)d.geo.ps * kQ * storage_bytes(b->storage), b->stream),
           "clearing replica populations");
-  }
+  b->cur = 0;
   b->step = 0;
   b->initialised = true;
-  if (int e = upload_reps(b)) return e;
   return bsync(b, "rflbm_batch_init_rest");
 }
 
@@ -812,10 +814,7 @@ int rflbm_batch_run(rflbm_batch_t* b, int64_t n) {
   if (n == 0) return RFLBM_OK;
   if (int e = run_graph(b, n)) return e;
   b->step += n;
-  if (n & 1) {
-    for (auto& d : b->host) d.cur ^= 1;
-    if (int e = upload_reps(b)) return e;
-  }
+  if (n & 1) b->cur ^= 1;
   return RFLBM_OK;
 }
 
@@ -831,7 +830,7 @@ int rflbm_batch_get_populations(rflbm_batch_t* b, int r, double* f) {
   double* dev = nullptr;
   const size_t bytes = sizeof(double) * kQ * (size_t)d.geo.n;
   BCUDA(cudaMalloc((void**)&dev, bytes), "allocating the export buffer");
-  cudaError_t e = launch_get_populations_f64(d.geo, d.cp.rho0, d.ss, b->storage, d.buf[d.cur], dev, b->stream);
+  cudaError_t e = launch_get_populations_f64(d.geo, d.cp.rho0, d.ss, b->storage, d.buf[b->cur], dev, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(f, dev, bytes, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   cudaFree(dev);
@@ -845,7 +844,7 @@ int rflbm_batch_stats(rflbm_batch_t* b, int r, rflbm_stats_t* out) {
   const ReplicaDev& d = b->host[r];
   const int blocks = std::max(1, (int)std::min<int64_t>(b->stat_blocks, ((int64_t)d.geo.n + 255) / 256));
   double* res = b->partials + (size_t)b->stat_blocks * kStatOutFields;
-  BCUDA(launch_stats(d.geo, d.cp.rho0, d.ss, b->storage, d.buf[d.cur], b->partials, blocks, res, b->stream),
+  BCUDA(launch_stats(d.geo, d.cp.rho0, d.ss, b->storage, d.buf[b->cur], b->partials, blocks, res, b->stream),
         "launching replica stats");
   double host[kStatOutFields];
   BCUDA(cudaMemcpyAsync(host, res, sizeof(host), cudaMemcpyDeviceToHost, b->stream), "copying replica stats");

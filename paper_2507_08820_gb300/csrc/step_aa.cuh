@@ -91,11 +91,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   for (int i = 0; i < kQ; ++i)
     G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = S::load(sm[plane_of(i) * kW + t], class_of(i), p.ss);
 
-  // BGK re-reads its inputs from the tile at the end instead of keeping them in registers
-  const auto reload = [&](int a, int b, int c, float) {
-    return S::load(sm[(9 * b + 3 * c + a) * kW + t], class_at(a, b, c), p.ss);
-  };
-  collide_site<kModel, kNoise, false, false>(G, p.cp, noise, reload);
+  collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
 
   __syncthreads();  // all inputs are read: the tile can take the outputs
 #pragma unroll
@@ -204,11 +200,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
         S::load(mine[gi * L::kGroup + (1 - cx_of(i)) * L::kSeg - cx_of(i)], class_of(i), p.ss);
   }
 
-  // BGK re-reads its inputs from the tile at the end instead of keeping them in registers
-  const auto reload = [&](int a, int b, int c, float) {
-    return S::load(mine[(3 * b + c) * L::kGroup + (2 - a) * L::kSeg + (1 - a)], class_at(a, b, c), p.ss);
-  };
-  collide_site<kModel, kNoise, false, false>(G, p.cp, noise, reload);
+  collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
 
   if (kFullRow) {
     // the segment is the whole row: population i of x goes to position (x + c_x) mod nx of
@@ -298,7 +290,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_even_pair(const __grid_constan
     if (S::kScaled) v = kmul(p.ss.inv_scale[class_of(i)], v);
     G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = v;
   }
-  collide_tile<kModelReg, kNoise, false, false>(G, p.cp, noise, KeepTile(), ScaledWeight<kStore>{p.ss});
+  collide_tile<kModelReg, kNoise, false, false>(G, p.cp, noise, ScaledWeight<kStore>{p.ss});
 
   __syncthreads();  // all inputs are read: the tile can take the outputs
 #pragma unroll
@@ -390,7 +382,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
     if (S::kScaled) v = kmul(p.ss.inv_scale[class_of(i)], v);
     G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = v;
   }
-  collide_tile<kModelReg, kNoise, false, false>(G, p.cp, noise, KeepTile(), ScaledWeight<kStore>{p.ss});
+  collide_tile<kModelReg, kNoise, false, false>(G, p.cp, noise, ScaledWeight<kStore>{p.ss});
 
   if (kFullRow) {
     using O = AaRowOut<kStore, kW>;

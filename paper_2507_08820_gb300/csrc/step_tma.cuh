@@ -70,6 +70,8 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   // last CTAs finish; they touch global memory only after their grid_dependency_wait
   grid_launch_dependents();
   const uint32_t s = x0 + t + p.geo.nx * row + p.geo.site0;  // global site (Philox counter)
+  // the normals of calls 0 and 1 before the dependency wait, of calls 2 to 5 while the
+  // copies are in flight
   SiteNoise noise;
   if (kNoise) site_noise_part<0, kPreWaitCalls>(s, p.step, p.replica, p.rk, noise);
 
@@ -126,11 +128,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
         S::load(mine[gi * L::kGroup + (cx_of(i) + 1) * L::kSeg - cx_of(i)], class_of(i), p.ss);
   }
 
-  // BGK re-reads its inputs from the tile at the end instead of keeping them in registers
-  const auto reload = [&](int a, int b, int c, float) {
-    return S::load(mine[(3 * b + c) * L::kGroup + a * L::kSeg - (a - 1)], class_at(a, b, c), p.ss);
-  };
-  collide_site<kModel, kNoise, kGhostNeq, kPhiRho0>(G, p.cp, noise, reload);
+  collide_site<kModel, kNoise, kGhostNeq, kPhiRho0>(G, p.cp, noise);
 
   __syncthreads();  // every thread has read its inputs: the tile can hold the outputs
   T* out = sm + t;  // dense [plane][kW] output tile at the (128-byte aligned) start
@@ -230,7 +228,7 @@ __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ 
     G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = v;
   }
 
-  collide_tile<kModelReg, kNoise, false, false>(G, p.cp, noise, KeepTile(),
+  collide_tile<kModelReg, kNoise, false, false>(G, p.cp, noise,
                                                     ScaledWeight<kStore>{p.ss});
 
   __syncthreads();

@@ -123,3 +123,33 @@ def exchange_faces(info: RankInfo, send_up, send_down, recv_below, recv_above):
     ops += [dist.P2POp(dist.irecv, t, up) for t in recv_above]
     for req in dist.batch_isend_irecv(ops):
         req.wait()
+
+
+def face_rows(buffers, face):
+    """The 9 plane rows of a face (an rflbm_face_t: three runs of three plane rows) as uint8
+    views of the torch tensors that hold the slab's population buffers."""
+    rows = []
+    for r in range(3):
+        for p in range(3):
+            addr = face.run[r] + p * face.plane_pitch
+            for t in buffers:
+                off = addr - t.data_ptr()
+                if 0 <= off and off + face.row_bytes <= t.numel():
+                    rows.append(t[off:off + face.row_bytes])
+                    break
+            else:
+                raise ValueError("face row outside the slab's buffers")
+    return rows
+
+
+def exchange_slab(R, box, info: RankInfo, stream):
+    """The face exchange after a step of this rank's z-slab (a Box created with
+    torch_buffers=True): the copy stream waits for the slab's boundary rows, the faces
+    travel on it (exchange_faces), and the slab's next step waits for the stream."""
+    import torch
+    send_up, send_down, recv_below, recv_above = R.rflbm_slab_faces(box.h)
+    R.rflbm_slab_faces_ready(box.h, stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        exchange_faces(info, face_rows(box._buffers, send_up), face_rows(box._buffers, send_down),
+                       face_rows(box._buffers, recv_below), face_rows(box._buffers, recv_above))
+    R.rflbm_slab_exchange_done(box.h, stream.cuda_stream)

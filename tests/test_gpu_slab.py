@@ -222,3 +222,25 @@ def test_slab_protocol_errors(R):
     assert R.rflbm_launches_per_step(R.Box(32, 4, 5, tau=0.8, z0=0, nz_global=5).h) == 3
     for h in (a, b, c, whole):
         h.close()
+
+
+@pytest.mark.parametrize("pattern", [0, 1])
+def test_rank_exchange_of_one_slab(R, pattern):
+    """The rank-side exchange of the distributed path (dist.exchange_slab) with one rank:
+    the slab is its own neighbour, so it must reproduce the periodic box."""
+    import torch
+    from paper_2507_08820_gb300 import dist
+    shape = (64, 4, 6)
+    f0 = _state(shape, seed=13)
+    whole = R.Box(*shape, tau=0.8, kT=1e-4, seed=5, pattern=pattern)
+    R.rflbm_set_populations(whole.h, f0)
+    (slab,) = _split(shape, (6,), f0, R, tau=0.8, kT=1e-4, seed=5, pattern=pattern, torch_buffers=True)
+    info = dist.RankInfo(0, 1, 0)
+    side = torch.cuda.Stream()
+    for _ in range(3):
+        R.rflbm_step(slab.h, 1)
+        dist.exchange_slab(R, slab, info, side)
+    R.rflbm_step(whole.h, 3)
+    assert np.array_equal(slab.populations(), whole.populations())
+    whole.close()
+    slab.close()
