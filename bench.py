@@ -50,9 +50,10 @@ def parse_args():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--kernel", choices=["auto", "gather", "tma"], default="auto")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
-    ap.add_argument("--workload", choices=["box", "ensemble"], default="box",
-                    help="one periodic box (default), or the 64-replica ensemble of uneven "
-                         "sizes advanced together (--storage applies)")
+    ap.add_argument("--workload", choices=["box", "ensemble", "backtransform"], default="box",
+                    help="one periodic box (default), the 64-replica ensemble of uneven sizes "
+                         "advanced together (--storage applies), or the back transform of Eq. 11 "
+                         "alone as float32 FMAs and as tensor-core MMA (a design measurement)")
     ap.add_argument("--tile", type=int, choices=[0, 128, 192, 256, 512], default=0,
                     help="ensemble tile size (0: chosen by the library's autotuner)")
     ap.add_argument("--pattern", choices=["pingpong", "aa"], default="pingpong",
@@ -748,12 +749,33 @@ def gb300_arm(args):
     return 0
 
 
+def backtransform_arm(args):
+    """The back transform of Eq. 11 on its own: float32 FMAs (as in the step kernels) against
+    tcgen05 MMA over tiles of 128 sites with split-bfloat16 moments. Each site transforms
+    `reps` sets of moments held in registers, so no population crosses DRAM."""
+    from paper_2507_08820_gb300 import build
+    build.build()
+    from paper_2507_08820_gb300 import rflbm as R
+    tiles, reps = 152 * 32, 64
+    out = {"metric": "Eq. 11 back transforms per second, float32 FMA vs tcgen05 MMA", "unit": "G site transforms/s",
+           "workload": f"{tiles} tiles of 128 sites x {reps} transforms each, moments in registers",
+           "higher_is_better": True}
+    for name, method in (("fma", 0), ("mma", 1)):
+        R.rflbm_testing_backtransform_time(method, tiles, reps)
+        ms = min(R.rflbm_testing_backtransform_time(method, tiles, reps) for _ in range(3))
+        out[name] = {"ms": ms, "value": tiles * 128 * reps / (ms * 1e-3) / 1e9}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "ensemble":
         return ensemble_arm(args)
+    if args.workload == "backtransform":
+        return backtransform_arm(args)
     return gb300_arm(args)
 
 

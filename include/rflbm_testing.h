@@ -24,6 +24,23 @@ extern "C" {
  * re-initialise it. */
 int rflbm_testing_expect_extra_bytes(rflbm_t* h, uint32_t bytes);
 
+/* Measurement of a design choice, not a production path: the back transform of Eq. 11,
+ * f_i = w_i sum_k e_ki m_k / b_k (Table II modes, scaled moments M_k = m_k / b_k as input),
+ * on its own, computed either as the step kernels compute it (method 0: sum-factorised
+ * float32 FMAs, one thread per site) or on the tensor cores (method 1: one tcgen05 MMA tile of
+ * 128 sites x 32 populations x 32 modes per CTA, split-bfloat16 moments, float32 accumulator
+ * in tensor memory; about 16 significant bits of M survive the split).
+ * rflbm_testing_backtransform: m holds 27 planes of n scaled moments (host memory, element
+ *   [k n + s], k = 9 p + 3 q + r for the exponents (p, q, r) of the mode), f receives 27
+ *   planes of n populations (host, element [i n + s], i = 9 (c_x + 1) + 3 (c_y + 1) + c_z + 1).
+ *   n must be a positive multiple of 128. Synchronous; allocates device memory.
+ * rflbm_testing_backtransform_time: *ms receives the time of one launch over `tiles` tiles of
+ *   128 sites, each site transforming `reps` sets of synthetic moments held in registers
+ *   (one untimed launch first). Synchronous; allocates device memory.
+ * A bounded wait for the MMA that expires returns RFLBM_ETIMEOUT. */
+int rflbm_testing_backtransform(int method, const float* m, int64_t n, float* f);
+int rflbm_testing_backtransform_time(int method, int64_t tiles, int reps, float* ms);
+
 #ifdef __cplusplus
 }
 #endif

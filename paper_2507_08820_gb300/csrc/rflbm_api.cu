@@ -549,10 +549,14 @@ int rflbm_init_field(rflbm_t* h, const double* rho, const double* u, int on_devi
 
 namespace {
 
-// Launches rows row0 .. row0 + nrows - 1 (row = y + ny z) of the handle's next step.
-cudaError_t launch_rows(rflbm* h, StepParams& p, uint32_t row0, uint32_t nrows) {
+// Launches nrows rows of the handle's next step (row = y + ny z): row0 .. row0 + split - 1,
+// then from row0 + split + gap on.
+cudaError_t launch_rows(rflbm* h, StepParams& p, uint32_t row0, uint32_t nrows, uint32_t split = ~0u,
+                        uint32_t gap = 0) {
   p.row0 = row0;
   p.nrows = nrows;
+  p.row_split = split < nrows ? split : nrows;
+  p.row_gap = gap;
   if (h->aa) {
     p.src = p.dst = h->buf[0];
     const bool odd = h->phase != 0;
@@ -571,17 +575,12 @@ cudaError_t launch_rows(rflbm* h, StepParams& p, uint32_t row0, uint32_t nrows) 
   return launch_step_gather(p, h->variant, h->stream);
 }
 
-// One step of a z-slab: its two boundary rows first (they write the faces its neighbours
-// need), the faces-ready event, then its interior rows, which run while the faces move.
+// One step of a z-slab: its two boundary slabs of rows first, in one launch (they write the
+// faces its neighbours need), the faces-ready event, then its interior rows, which run while
+// the faces move.
 cudaError_t slab_step(rflbm* h, StepParams& p) {
   const uint32_t ny = h->geo.ny, nz = h->geo.nz;
-  cudaError_t e;
-  if (nz <= 2) {
-    e = launch_rows(h, p, 0, ny * nz);
-  } else {
-    e = launch_rows(h, p, 0, ny);
-    if (e == cudaSuccess) e = launch_rows(h, p, (nz - 1) * ny, ny);
-  }
+  cudaError_t e = nz <= 2 ? launch_rows(h, p, 0, ny * nz) : launch_rows(h, p, 0, 2 * ny, ny, (nz - 2) * ny);
   if (e == cudaSuccess) e = cudaEventRecord(h->faces_ready, h->stream);
   if (e == cudaSuccess && nz > 2) e = launch_rows(h, p, ny, (nz - 2) * ny);
   return e;
@@ -921,7 +920,7 @@ int rflbm_get_dims(const rflbm_t* h, int* nx, int* ny, int* nz) {
 int rflbm_launches_per_step(const rflbm_t* h) {
   if (int e = check_handle(h)) return e;
   if (!h->slab) return 1;
-  return h->geo.nz <= 2 ? 1 : 3;  // a z-slab: boundary rows (one or two launches), interior
+  return h->geo.nz <= 2 ? 1 : 2;  // a z-slab: boundary rows, interior rows
 }
 
 int rflbm_step_path(const rflbm_t* h, int* width) {

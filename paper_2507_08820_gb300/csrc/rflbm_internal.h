@@ -140,7 +140,9 @@ __device__ __forceinline__ int32_t push_delta(const PullDeltas& d, int i) {
 
 struct StepParams {
   Geometry geo;
-  uint32_t row0, nrows;  // the launch updates rows row0 .. row0 + nrows - 1 (row = y + ny z)
+  // The launch updates nrows rows (row = y + ny z): rows row0 .. row0 + row_split - 1, then
+  // from row0 + row_split + row_gap on (row_gap 0: one contiguous range).
+  uint32_t row0, nrows, row_split, row_gap;
   CollideParams cp;
   StoreScale ss;    // 16-bit storage scales (unused for float32)
   const void* src;  // population buffers in the handle's storage format

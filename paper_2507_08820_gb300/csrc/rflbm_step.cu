@@ -17,9 +17,10 @@ template <int kStore, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
 __global__ void __launch_bounds__(kStepBlock) step_pull(const StepParams p) {
   using S = Storage<kStore>;
   using T = typename S::T;
-  // local site s of rows row0 .. row0 + nrows - 1; a z-slab's buffer holds it zlo rows up
-  const uint32_t s = p.row0 * p.geo.nx + blockIdx.x * kStepBlock + threadIdx.x;
-  if (s >= (p.row0 + p.nrows) * p.geo.nx) return;
+  // local site s of the launched rows (see StepParams); a z-slab's buffer holds it zlo rows up
+  const uint32_t q = blockIdx.x * kStepBlock + threadIdx.x;
+  if (q >= p.nrows * p.geo.nx) return;
+  const uint32_t s = p.row0 * p.geo.nx + q + (q >= p.row_split * p.geo.nx ? p.row_gap * p.geo.nx : 0u);
   const PullDeltas d = pull_deltas(s, p.geo);
   const int64_t sb = s + (int64_t)p.geo.zlo * p.geo.nxy;
   const T* __restrict__ src = static_cast<const T*>(p.src) + sb;
@@ -50,8 +51,9 @@ template <int kStore, bool kOdd, int kModel, bool kNoise>
 __global__ void __launch_bounds__(kStepBlock) step_aa_gather(const StepParams p) {
   using S = Storage<kStore>;
   using T = typename S::T;
-  const uint32_t s = p.row0 * p.geo.nx + blockIdx.x * kStepBlock + threadIdx.x;
-  if (s >= (p.row0 + p.nrows) * p.geo.nx) return;
+  const uint32_t q = blockIdx.x * kStepBlock + threadIdx.x;
+  if (q >= p.nrows * p.geo.nx) return;
+  const uint32_t s = p.row0 * p.geo.nx + q + (q >= p.row_split * p.geo.nx ? p.row_gap * p.geo.nx : 0u);
   T* const buf = static_cast<T*>(p.dst) + s + (int64_t)p.geo.zlo * p.geo.nxy;
   PullDeltas d{};
   if (kOdd) d = pull_deltas(s, p.geo);

@@ -1,0 +1,232 @@
+// The back transform of Eq. 11 on its own, f_i = w_i sum_k e_ki m_k / b_k over tiles of 128
+// sites, in two forms: the step kernels' sum-factorised float32 FMAs (back_transform of
+// collide.cuh), and fifth-generation tensor-core MMA. A measurement of that design choice;
+// the step kernels use the FMA form.
+//
+// MMA form: D[site][i] = sum_k A[site][k] B[i][k] on one tcgen05 kind::f16 MMA tile of
+// M = 128 sites x N = 32 populations (27 used), K = 32 modes (27 used), with the float32
+// accumulator in tensor memory. B[i][k] = e'_ki = h'_p(c_x) h'_q(c_y) h'_r(c_z) with
+// h' = (1, c, 3c^2 - 1): small integers, exact in bfloat16. A[site][k] = M_k / 3^(n_k), n_k the
+// number of second-order factors of mode k, so that A B = sum_k e_ki M_k; each thread writes
+// its site's row of A split into a bfloat16 high part and a bfloat16 remainder (two MMAs per
+// K chunk accumulate both), which keeps about 16 significant bits of M. The threads then read
+// their rows back from tensor memory and apply the weights w_i.
+//
+// Both operands sit in shared memory in the canonical K-major layout without swizzling:
+// element (row, k) at byte (row % 8) 16 + (row / 8) 512 + (k % 8) 2 + (k / 8) 128, i.e. core
+// matrices of 8 rows x 16 bytes, 128 bytes apart along K and 512 bytes apart along the rows.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/rflbm_testing.h"
+#include "rflbm_internal.h"
+#include "tcgen05.cuh"
+
+namespace rflbm_dev {
+namespace {
+
+constexpr int kBtTile = 128;  // sites per CTA: the MMA's M
+constexpr int kBtK = 32;      // modes, padded: the MMA's K (two K = 16 instructions)
+constexpr int kBtN = 32;      // populations, padded: the MMA's N
+constexpr uint32_t kBtPolls = 1u << 22;
+
+// element offset of (row, k) in a canonical K-major operand of 32 columns
+__host__ __device__ constexpr int canon(int row, int k) { return (row % 8) * 8 + (row / 8) * 256 + (k % 8) + (k / 8) * 64; }
+// scaled 1-D Hermite value h'_p(c) = 1, c, 3c^2 - 1
+__host__ __device__ constexpr int hs(int p, int c) { return p == 0 ? 1 : (p == 1 ? c : 3 * c * c - 1); }
+// second-order factors of mode k = 9p + 3q + r
+__host__ __device__ constexpr int n2_of(int k) { return (k / 9 == 2) + ((k / 3) % 3 == 2) + (k % 3 == 2); }
+
+// The moments of a site: loaded (27 planes of n values), or synthetic values for timing.
+template <bool kSynth>
+__device__ __forceinline__ void site_moments_in(const float* m, int64_t n, int64_t site, float (&M)[27]) {
+#pragma unroll
+  for (int k = 0; k < 27; ++k)
+    M[k] = kSynth ? 1e-3f * (float)(((uint32_t)site * 2654435761u + 40503u * (uint32_t)k) >> 20) - 2.0f
+                  : m[(int64_t)k * n + site];
+}
+
+// ---- FMA form: the step kernels' back transform, per thread and site
+template <bool kSynth>
+__global__ void __launch_bounds__(kBtTile) k_bt_fma(const float* __restrict__ m, int64_t n, int reps,
+                                                    float* __restrict__ out) {
+  const int64_t site = (int64_t)blockIdx.x * kBtTile + threadIdx.x;
+  float Mv[27];
+  site_moments_in<kSynth>(m, n, site, Mv);
+  float acc[27];
+#pragma unroll
+  for (int i = 0; i < 27; ++i) acc[i] = 0.0f;
+  for (int rep = 0; rep < reps; ++rep) {
+    float M[3][3][3], G[3][3][3];
+#pragma unroll
+    for (int k = 0; k < 27; ++k) M[k / 9][(k / 3) % 3][k % 3] = kSynth ? Mv[k] + 1e-4f * (float)rep : Mv[k];
+    back_transform(M, G, LatticeWeight());
+#pragma unroll
+    for (int i = 0; i < 27; ++i) acc[i] += G[i / 9][(i / 3) % 3][i % 3];
+  }
+#pragma unroll
+  for (int i = 0; i < 27; ++i) out[(int64_t)i * n + site] = acc[i];
+}
+
+// ---- MMA form
+template <bool kSynth>
+__global__ void __launch_bounds__(kBtTile) k_bt_mma(const float* __restrict__ m, int64_t n, int reps,
+                                                    float* __restrict__ out, int* err) {
+  __shared__ __align__(1024) __nv_bfloat16 sA[2][kBtTile * kBtK];  // high parts, remainders
+  __shared__ __align__(1024) __nv_bfloat16 sB[kBtN * kBtK];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int64_t site = (int64_t)blockIdx.x * kBtTile + t;
+
+  for (int e = t; e < kBtN * kBtK; e += kBtTile) {
+    const int i = e / kBtK, k = e % kBtK;
+    const int v = (i < 27 && k < 27) ? hs(k / 9, i / 9 - 1) * hs((k / 3) % 3, (i / 3) % 3 - 1) * hs(k % 3, i % 3 - 1) : 0;
+    sB[canon(i, k)] = __float2bfloat16((float)v);
+  }
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 32);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  float Mv[27];
+  site_moments_in<kSynth>(m, n, site, Mv);
+  float acc[27];
+#pragma unroll
+  for (int i = 0; i < 27; ++i) acc[i] = 0.0f;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int rep = 0; rep < reps && ok; ++rep) {
+    // this site's row of A: M_k / 3^n_k as a bfloat16 high part and remainder, 8 modes per
+    // 16-byte store
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __align__(16) __nv_bfloat162 hi[4], lo[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        float v[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int k = 8 * j + 2 * h + e;
+          const float scale = n2_of(k) == 0 ? 1.0f : (n2_of(k) == 1 ? 1.0f / 3.0f : (n2_of(k) == 2 ? 1.0f / 9.0f : 1.0f / 27.0f));
+          v[e] = k < 27 ? (kSynth ? Mv[k] + 1e-4f * (float)rep : Mv[k]) * scale : 0.0f;
+        }
+        hi[h] = __floats2bfloat162_rn(v[0], v[1]);
+        const float2 back = __bfloat1622float2(hi[h]);
+        lo[h] = __floats2bfloat162_rn(v[0] - back.x, v[1] - back.y);
+      }
+      *reinterpret_cast<uint4*>(&sA[0][canon(t, 8 * j)]) = *reinterpret_cast<const uint4*>(hi);
+      *reinterpret_cast<uint4*>(&sA[1][canon(t, 8 * j)]) = *reinterpret_cast<const uint4*>(lo);
+    }
+    fence_proxy_async_smem();  // the rows become visible to the tensor core's reads
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after_sync();
+      constexpr uint32_t idesc = idesc_bf16_f32(kBtTile, kBtN);
+#pragma unroll
+      for (int part = 0; part < 2; ++part)
+#pragma unroll
+        for (int s = 0; s < 2; ++s)  // K = 16 per instruction: two core matrices along K
+          tc_mma_bf16(tmem, smem_desc_noswizzle(smem_addr(&sA[part][0]) + 256u * s, 128u, 512u),
+                      smem_desc_noswizzle(smem_addr(&sB[0]) + 256u * s, 128u, 512u), idesc, (part | s) != 0);
+      tc_commit(&bar);
+    }
+    ok = mbar_wait_bounded(&bar, phase, kBtPolls);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) atomicOr(err, 1);
+      mbar_wait_bounded(&bar, phase ^ 1u, kBtPolls);  // the MMA in flight completes first
+      ok = false;
+      break;
+    }
+    tc_fence_after_sync();
+    float D[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), D);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) acc[i] = fmaf((float)(w1d(i / 9) * w1d((i / 3) % 3) * w1d(i % 3)), D[i], acc[i]);
+    tc_fence_before_sync();
+    __syncthreads();  // every row is read before the next MMA overwrites the accumulator
+  }
+  if (ok) {
+#pragma unroll
+    for (int i = 0; i < 27; ++i) out[(int64_t)i * n + site] = acc[i];
+  }
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 32);
+}
+
+int bt_fail(int code, const char* msg, cudaError_t e = cudaSuccess) {
+  return record_error(code, msg, e == cudaSuccess ? nullptr : cudaGetErrorString(e));
+}
+
+}  // namespace
+}  // namespace rflbm_dev
+
+using namespace rflbm_dev;
+
+extern "C" int rflbm_testing_backtransform(int method, const float* m, int64_t n, float* f) {
+  if ((method != 0 && method != 1) || !m || !f || n < kBtTile || n % kBtTile)
+    return bt_fail(RFLBM_EINVAL, "rflbm_testing_backtransform: method 0 or 1, n a positive multiple of 128");
+  float *dm = nullptr, *df = nullptr;
+  int* derr = nullptr;
+  const size_t bytes = sizeof(float) * 27 * (size_t)n;
+  cudaError_t e = cudaMalloc(&dm, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&df, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&derr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(dm, m, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const unsigned blocks = (unsigned)(n / kBtTile);
+    if (method == 0) k_bt_fma<false><<<blocks, kBtTile>>>(dm, n, 1, df);
+    else k_bt_mma<false><<<blocks, kBtTile>>>(dm, n, 1, df, derr);
+    e = cudaGetLastError();
+  }
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(f, df, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&err, derr, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(dm);
+  cudaFree(df);
+  cudaFree(derr);
+  if (e != cudaSuccess) return bt_fail(RFLBM_ECUDA, "rflbm_testing_backtransform", e);
+  if (err) return bt_fail(RFLBM_ETIMEOUT, "rflbm_testing_backtransform: a bounded wait for the MMA expired");
+  return RFLBM_OK;
+}
+
+extern "C" int rflbm_testing_backtransform_time(int method, int64_t tiles, int reps, float* ms) {
+  if ((method != 0 && method != 1) || tiles < 1 || reps < 1 || !ms)
+    return bt_fail(RFLBM_EINVAL, "rflbm_testing_backtransform_time: invalid arguments");
+  const int64_t n = tiles * kBtTile;
+  float* dout = nullptr;
+  int* derr = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&dout, sizeof(float) * 27 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&derr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {  // warm-up, then timed
+    if (pass == 1) e = cudaEventRecord(e0);
+    if (method == 0) k_bt_fma<true><<<(unsigned)tiles, kBtTile>>>(nullptr, n, reps, dout);
+    else k_bt_mma<true><<<(unsigned)tiles, kBtTile>>>(nullptr, n, reps, dout, derr);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (pass == 1 && e == cudaSuccess) e = cudaEventRecord(e1);
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&err, derr, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(dout);
+  cudaFree(derr);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return bt_fail(RFLBM_ECUDA, "rflbm_testing_backtransform_time", e);
+  if (err) return bt_fail(RFLBM_ETIMEOUT, "rflbm_testing_backtransform_time: a bounded wait for the MMA expired");
+  return RFLBM_OK;
+}

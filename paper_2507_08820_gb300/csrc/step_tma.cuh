@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   const int t = threadIdx.x;
   const uint32_t nseg = p.geo.nx / kW;
   const uint32_t rb = blockIdx.x / nseg;
-  const uint32_t row = p.row0 + rb;                  // y + ny * z
+  const uint32_t row = p.row0 + rb + (rb >= p.row_split ? p.row_gap : 0u);  // y + ny * z
   const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
   const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
 
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ 
   const int t = threadIdx.x;
   const uint32_t nseg = p.geo.nx / kW;
   const uint32_t rb = blockIdx.x / nseg;
-  const uint32_t row = p.row0 + rb;                  // y + ny * z
+  const uint32_t row = p.row0 + rb + (rb >= p.row_split ? p.row_gap : 0u);  // y + ny * z
   const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
   const uint32_t z = row / p.geo.ny, y = row - z * p.geo.ny;
 

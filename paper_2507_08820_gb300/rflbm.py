@@ -129,6 +129,8 @@ _sig = {
     "rflbm_structure_factor": (C.c_int, [_H, C.c_int, C.c_int, _P, _P]),
     "rflbm_shell_count": (C.c_int, [_H]),
     "rflbm_testing_expect_extra_bytes": (C.c_int, [_H, C.c_uint32]),
+    "rflbm_testing_backtransform": (C.c_int, [C.c_int, _P, C.c_int64, _P]),
+    "rflbm_testing_backtransform_time": (C.c_int, [C.c_int, C.c_int64, C.c_int, C.POINTER(C.c_float)]),
     "rflbm_slab_faces": (C.c_int, [_H] + [C.POINTER(rflbm_face_t)] * 4),
     "rflbm_slab_faces_ready": (C.c_int, [_H, _P]),
     "rflbm_slab_exchange_done": (C.c_int, [_H, _P]),
@@ -335,6 +337,24 @@ def rflbm_testing_expect_extra_bytes(h, nbytes):
     arrive, so their bounded waits run out and the next synchronising call raises
     RFLBM_ETIMEOUT; 0 restores normal operation."""
     return _check(lib.rflbm_testing_expect_extra_bytes(h, int(nbytes)))
+
+
+def rflbm_testing_backtransform(method, m):
+    """Testing (include/rflbm_testing.h): the back transform of Eq. 11 alone; m: (27, n)
+    float32 scaled moments in exponent order, n a multiple of 128. Returns (27, n) populations.
+    method 0: float32 FMAs as in the step kernels, 1: tcgen05 MMA with split-bfloat16 moments."""
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    f = np.empty_like(m)
+    _check(lib.rflbm_testing_backtransform(int(method), m.ctypes.data, m.shape[1], f.ctypes.data))
+    return f
+
+
+def rflbm_testing_backtransform_time(method, tiles, reps):
+    """Testing: milliseconds of one launch over `tiles` tiles of 128 sites, `reps` synthetic
+    transforms per site."""
+    ms = C.c_float()
+    _check(lib.rflbm_testing_backtransform_time(int(method), int(tiles), int(reps), C.byref(ms)))
+    return ms.value
 
 
 def rflbm_step_path(h):
