@@ -752,7 +752,8 @@ def gb300_arm(args):
 def backtransform_arm(args):
     """The back transform of Eq. 11 on its own: float32 FMAs (as in the step kernels) against
     tcgen05 MMA over tiles of 128 sites with split-bfloat16 moments. Each site transforms
-    `reps` sets of moments held in registers, so no population crosses DRAM."""
+    `reps` sets of moments held in registers, so no population crosses DRAM. Also the noise
+    draw of a step on its own (24 normals per site), the bound of the 16-bit steps."""
     from paper_2507_08820_gb300 import build
     build.build()
     from paper_2507_08820_gb300 import rflbm as R
@@ -764,6 +765,15 @@ def backtransform_arm(args):
         R.rflbm_testing_backtransform_time(method, tiles, reps)
         ms = min(R.rflbm_testing_backtransform_time(method, tiles, reps) for _ in range(3))
         out[name] = {"ms": ms, "value": tiles * 128 * reps / (ms * 1e-3) / 1e9}
+    # the noise draw of a step alone, against the sites per second of the 16-bit roofline
+    nsites = 1 << 27
+    R.rflbm_testing_noise_time(nsites)
+    ms = min(R.rflbm_testing_noise_time(nsites) for _ in range(3))
+    peak, kind = measured_peak()
+    rate = nsites / (ms * 1e-3)
+    out["noise_draw_alone"] = {"ms": ms, "sites": nsites, "value": rate / 1e9, "unit": "G sites/s",
+                               "fraction_of_16bit_roofline": rate * 108 / 1e9 / peak,
+                               "peak": f"hbm_gbs of {kind}"}
     print(json.dumps(out))
     return 0
 

@@ -41,6 +41,12 @@ int rflbm_testing_expect_extra_bytes(rflbm_t* h, uint32_t bytes);
 int rflbm_testing_backtransform(int method, const float* m, int64_t n, float* f);
 int rflbm_testing_backtransform_time(int method, int64_t tiles, int reps, float* ms);
 
+/* Measurement of the noise draw of a step alone (the r_k of Eq. 9 by the generator stated in
+ * rflbm.h: 6 Philox4x32-10 calls and 12 Box-Muller pairs per site), two sites per thread as in
+ * the 16-bit step kernels, with nothing else done: *ms receives the time of one launch over
+ * nsites sites (2 <= nsites < 2^31; one untimed launch first). Synchronous. */
+int rflbm_testing_noise_time(int64_t nsites, float* ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,5 +1,6 @@
-// The back transform of Eq. 11 on its own, f_i = w_i sum_k e_ki m_k / b_k over tiles of 128
-// sites, in two forms: the step kernels' sum-factorised float32 FMAs (back_transform of
+// Measurements of design choices (not production paths). The noise draw of a step on its own
+// (rflbm_testing_noise_time). The back transform of Eq. 11 on its own, f_i = w_i sum_k e_ki m_k / b_k
+// over tiles of 128 sites, in two forms: the step kernels' sum-factorised float32 FMAs (back_transform of
 // collide.cuh), and fifth-generation tensor-core MMA. A measurement of that design choice;
 // the step kernels use the FMA form.
 //
@@ -18,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "../../include/rflbm_testing.h"
@@ -162,6 +164,22 @@ __global__ void __launch_bounds__(kBtTile) k_bt_mma(const float* __restrict__ m,
   if (warp == 0) tmem_dealloc(tmem, 32);
 }
 
+// ---- the noise draw alone: the 24 normals of every site at one step (6 Philox4x32-10 calls
+// and 12 Box-Muller pairs, site_noise), two sites per thread as in the 16-bit step kernels,
+// folded into one sum per thread so that nothing but the draw costs time
+__global__ void __launch_bounds__(128) k_noise_only(uint32_t nsites, uint32_t step, float* __restrict__ out) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  float acc = 0.0f;
+  for (uint32_t s = 2 * tid; s + 1 < nsites; s += 2 * gridDim.x * blockDim.x) {
+    SiteNoise a, b;
+    site_noise(s, step, 0u, 1u, 0u, a);
+    site_noise(s + 1, step, 0u, 1u, 0u, b);
+#pragma unroll
+    for (int m = 0; m < 23; ++m) acc = fmaf(a.n[m], b.n[m], acc);
+  }
+  out[tid] = acc;
+}
+
 int bt_fail(int code, const char* msg, cudaError_t e = cudaSuccess) {
   return record_error(code, msg, e == cudaSuccess ? nullptr : cudaGetErrorString(e));
 }
@@ -228,5 +246,31 @@ extern "C" int rflbm_testing_backtransform_time(int method, int64_t tiles, int r
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return bt_fail(RFLBM_ECUDA, "rflbm_testing_backtransform_time", e);
   if (err) return bt_fail(RFLBM_ETIMEOUT, "rflbm_testing_backtransform_time: a bounded wait for the MMA expired");
+  return RFLBM_OK;
+}
+
+extern "C" int rflbm_testing_noise_time(int64_t nsites, float* ms) {
+  if (nsites < 2 || nsites >= (int64_t(1) << 31) || !ms)
+    return bt_fail(RFLBM_EINVAL, "rflbm_testing_noise_time: 2 <= nsites < 2^31");
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const unsigned blocks = (unsigned)std::max(1, sms * 16);
+  float* dout = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&dout, sizeof(float) * blocks * 128);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {  // warm-up, then timed
+    if (pass == 1) e = cudaEventRecord(e0);
+    k_noise_only<<<blocks, 128>>>((uint32_t)nsites, 7u, dout);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (pass == 1 && e == cudaSuccess) e = cudaEventRecord(e1);
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaFree(dout);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return bt_fail(RFLBM_ECUDA, "rflbm_testing_noise_time", e);
   return RFLBM_OK;
 }

@@ -131,6 +131,7 @@ _sig = {
     "rflbm_testing_expect_extra_bytes": (C.c_int, [_H, C.c_uint32]),
     "rflbm_testing_backtransform": (C.c_int, [C.c_int, _P, C.c_int64, _P]),
     "rflbm_testing_backtransform_time": (C.c_int, [C.c_int, C.c_int64, C.c_int, C.POINTER(C.c_float)]),
+    "rflbm_testing_noise_time": (C.c_int, [C.c_int64, C.POINTER(C.c_float)]),
     "rflbm_slab_faces": (C.c_int, [_H] + [C.POINTER(rflbm_face_t)] * 4),
     "rflbm_slab_faces_ready": (C.c_int, [_H, _P]),
     "rflbm_slab_exchange_done": (C.c_int, [_H, _P]),
@@ -354,6 +355,13 @@ def rflbm_testing_backtransform_time(method, tiles, reps):
     transforms per site."""
     ms = C.c_float()
     _check(lib.rflbm_testing_backtransform_time(int(method), int(tiles), int(reps), C.byref(ms)))
+    return ms.value
+
+
+def rflbm_testing_noise_time(nsites):
+    """Testing: milliseconds of one launch drawing the 24 normals of nsites sites."""
+    ms = C.c_float()
+    _check(lib.rflbm_testing_noise_time(int(nsites), C.byref(ms)))
     return ms.value
 
 

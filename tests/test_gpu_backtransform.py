@@ -52,3 +52,7 @@ def test_mma_back_transform_matches_the_fma_form(R):
 def test_both_forms_time(R):
     for method in (0, 1):
         assert R.rflbm_testing_backtransform_time(method, 152 * 4, 4) > 0.0
+
+
+def test_noise_draw_alone_times(R):
+    assert R.rflbm_testing_noise_time(1 << 20) > 0.0
