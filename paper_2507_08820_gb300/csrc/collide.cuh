@@ -12,20 +12,18 @@
 // same way, whichever form it uses.
 //
 // Work per site (all FP32):
-//  1. Reg-FLBM: the ten moments of order <= 2 by three sum-factorised sweeps (Eqs. 3-5):
+//  1. the ten moments of order <= 2 by three sum-factorised sweeps (Eqs. 3-5):
 //     delta rho = rho - rho0, j = rho u, and the second Hermite moment
-//     a^(2)_ab = sum_i f_i (c_ia c_ib - delta_ab/3). BGK-FLBM: all 27 Hermite moments
-//     m_k = sum_i e_ki g_i (Eq. 5) by three sweeps of nine 1-D lines (4 operations each),
-//     since its relaxation keeps (1 - omega) of every non-conserved moment;
+//     a^(2)_ab = sum_i f_i (c_ia c_ib - delta_ab/3);
 //  2. the post-collision moments, divided by their norms b_k, in a tile M[p][q][r] of
 //     Hermite exponents: the equilibrium coefficients rho u_x^p u_y^q u_z^r (Eq. 21);
 //     Reg: the relaxed stress non-equilibrium a^(2) - rho u u (Eq. 20 with Eq. 15) for
-//     k = 4..9 and the ghost non-equilibrium of Eq. 22 when omega_g != 1; BGK:
-//     omega a_0,k + (1 - omega) m_k for every k >= 4, the density and momentum kept
-//     (Eq. 12 projected on the complete Hermite basis of the lattice); and
-//     phi_k r_k (Eqs. 9-10) for k = 4..26;
+//     k = 4..9 and the ghost non-equilibrium of Eq. 22 when omega_g != 1; BGK: omega times
+//     the equilibrium coefficients; and phi_k r_k (Eqs. 9-10) for k = 4..26;
 //  3. the back transform f_i = w_i sum_k b_k^-1 e_ki m_k (Eq. 11) by three
-//     sum-factorised sweeps (4 operations per line of three) and the weights.
+//     sum-factorised sweeps (4 operations per line of three) and the weights; BGK adds
+//     (1 - omega) f (Eq. 12), re-read from shared memory by the kernels that stage their
+//     inputs there.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -114,16 +112,6 @@ __device__ __forceinline__ void line_inverse_v(V L0, V L1, V L2, V& om, V& o0, V
   o0 = kfma(-1.0f / 3.0f, L2, L0);
   om = vsub(a, L1);
   op = vadd(a, L1);
-}
-
-// One line of the forward 1-D transform: from the values at c = -1, 0, +1 the projections on
-// h_0 = 1, h_1 = c and h_2 = c^2 - 1/3.
-template <class V>
-__device__ __forceinline__ void line_forward_v(V gm, V g0, V gp, V& H0, V& H1, V& H2) {
-  const V s = vadd(gp, gm);
-  H1 = vsub(gp, gm);
-  H0 = vadd(s, g0);
-  H2 = kfma(-1.0f / 3.0f, H0, s);
 }
 
 // Noise sources of the collision: noise(j, n0, n1) gives the normals of the two Box-Muller
@@ -252,68 +240,12 @@ __device__ __forceinline__ void back_transform(V (&M)[3][3][3], V (&G)[3][3][3],
     }
 }
 
-// BGK-FLBM (Eq. 12) in the moment space of the 27 Hermite modes, which span the lattice's
-// population space: every non-conserved scaled moment becomes
-// omega a_0,k / b_k + (1 - omega) m_k / b_k (+ noise), density and momentum are kept, and
-// the back transform gives f* = f^(0) + (1 - omega)(f - f^(0)) + the noise.
-template <bool kNoise, bool kPhiRho0, class V, class Noise, class OutWeight>
-__device__ __forceinline__ void collide_tile_bgk(V (&G)[3][3][3], const CollideParams& cp, const Noise& noise,
-                                                 const OutWeight& outw) {
-  // ---- 1. all 27 Hermite moments H[p][q][r] = sum g h_p(c_x) h_q(c_y) h_r(c_z): sweep x,
-  // then y, then z (the rest state drops out of every moment but H[0][0][0] = drho)
-  V X[3][3][3];  // [p][b][c]
-#pragma unroll
-  for (int b = 0; b < 3; ++b)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) line_forward_v(G[0][b][c], G[1][b][c], G[2][b][c], X[0][b][c], X[1][b][c], X[2][b][c]);
-  V Y[3][3][3];  // [p][q][c]
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) line_forward_v(X[p][0][c], X[p][1][c], X[p][2][c], Y[p][0][c], Y[p][1][c], Y[p][2][c]);
-  V M[3][3][3];  // [p][q][r]
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) line_forward_v(Y[p][q][0], Y[p][q][1], Y[p][q][2], M[p][q][0], M[p][q][1], M[p][q][2]);
-  const V drho = M[0][0][0], jx = M[1][0][0], jy = M[0][1][0], jz = M[0][0][1];
-
-  // ---- 2. relaxation towards the equilibrium coefficients rho u_x^p u_y^q u_z^r (Eq. 21)
-  const V rho = vadd(splat<V>(cp.rho0), drho);
-  const V inv_rho = vrcp(rho);
-  const V ux = vmul(jx, inv_rho), uy = vmul(jy, inv_rho), uz = vmul(jz, inv_rho);
-  // omega U[p] = omega u^p / beta_p and (1 - omega) / b for each mode
-  const float om = cp.omega;
-  const V Uy[3] = {splat<V>(1.0f), kmul(3.0f, uy), vmul(kmul(4.5f, uy), uy)};
-  const V Uz[3] = {splat<V>(1.0f), kmul(3.0f, uz), vmul(kmul(4.5f, uz), uz)};
-  const V RX[3] = {kmul(om, rho), kmul(3.0f * om, jx), vmul(kmul(4.5f * om, jx), ux)};
-#pragma unroll
-  for (int p = 0; p < 3; ++p)
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        if (p + q + r < 2) continue;  // density and momentum are kept
-        const V yz = q == 0 ? Uz[r] : (r == 0 ? Uy[q] : vmul(Uy[q], Uz[r]));
-        const V eq = (q == 0 && r == 0) ? RX[p] : vmul(RX[p], yz);
-        M[p][q][r] = kfma((1.0f - om) * float(1.0 / bnorm(p, q, r)), M[p][q][r], eq);
-      }
-  // scaled conserved moments m / b: drho, 3 j
-  M[1][0][0] = kmul(3.0f, jx);
-  M[0][1][0] = kmul(3.0f, jy);
-  M[0][0][1] = kmul(3.0f, jz);
-  inject_noise<kNoise, kPhiRho0>(M, rho, cp, noise);
-  back_transform(M, G, outw);
-}
-
-template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0, class V, class Noise, class OutWeight>
-__device__ __forceinline__ void collide_tile(V (&G)[3][3][3], const CollideParams& cp,
-                                          const Noise& noise, const OutWeight& outw) {
-  if (kModel == kModelBgk) {
-    collide_tile_bgk<kNoise, kPhiRho0>(G, cp, noise, outw);
-    return;
-  }
-  // ---- 1. moments of order <= 2 (sweep x, then y, then z)
+// The moments of order <= 2 of the shifted populations by three sum-factorised sweeps
+// (sweep x, then y, then z): delta rho, j = rho u, the off-diagonal second moments
+// sum g c_a c_b and the diagonal second Hermite moments a^(2)_aa.
+template <class V>
+__device__ __forceinline__ void moments_order2(const V (&G)[3][3][3], V& drho, V& jx, V& jy, V& jz, V& sxy, V& sxz,
+                                               V& syz, V& axx, V& ayy, V& azz) {
   V X0[3][3], X1[3][3], X2[3][3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
@@ -335,20 +267,98 @@ __device__ __forceinline__ void collide_tile(V (&G)[3][3][3], const CollideParam
     T20[c] = vadd(vadd(X2[2][c], X2[0][c]), X2[1][c]);
   }
   const V s002 = vadd(T00[2], T00[0]);
-  const V drho = vadd(s002, T00[1]);
-  const V jz = vsub(T00[2], T00[0]);
-  const V jy = vadd(vadd(T01[0], T01[1]), T01[2]);
-  const V syz = vsub(T01[2], T01[0]);
+  drho = vadd(s002, T00[1]);
+  jz = vsub(T00[2], T00[0]);
+  jy = vadd(vadd(T01[0], T01[1]), T01[2]);
+  syz = vsub(T01[2], T01[0]);
   const V syy = vadd(vadd(T02[0], T02[1]), T02[2]);
-  const V jx = vadd(vadd(T10[0], T10[1]), T10[2]);
-  const V sxz = vsub(T10[2], T10[0]);
-  const V sxy = vadd(vadd(T11[0], T11[1]), T11[2]);
+  jx = vadd(vadd(T10[0], T10[1]), T10[2]);
+  sxz = vsub(T10[2], T10[0]);
+  sxy = vadd(vadd(T11[0], T11[1]), T11[2]);
   const V sxx = vadd(vadd(T20[0], T20[1]), T20[2]);
   const V szz = s002;
   // second Hermite moment of f: sum g (c c) - (drho / 3) delta (the rest state drops out)
-  const V axx = kfma(-1.0f / 3.0f, drho, sxx);
-  const V ayy = kfma(-1.0f / 3.0f, drho, syy);
-  const V azz = kfma(-1.0f / 3.0f, drho, szz);
+  axx = kfma(-1.0f / 3.0f, drho, sxx);
+  ayy = kfma(-1.0f / 3.0f, drho, syy);
+  azz = kfma(-1.0f / 3.0f, drho, szz);
+
+}
+
+// Supplies the pre-collision value g of tile entry (a, b, c) to BGK-FLBM's (1 - omega) f
+// term at the end of the collision. By default the tile itself, which keeps its 27 values in
+// registers through the whole collision; kernels that still hold their inputs in shared
+// memory pass a reader instead, and the registers are free in between.
+struct KeepTile {
+  template <class V>
+  __device__ __forceinline__ V operator()(int, int, int, V g) const { return g; }
+};
+
+// BGK-FLBM (Eq. 12): f* = f^(0) + (1 - omega)(f - f^(0)) + noise, as the back transform of
+// omega a_0 + noise (the shifted density mode is omega drho) plus (1 - omega) f.
+template <bool kNoise, bool kPhiRho0, class V, class Noise, class OutWeight, class Reload>
+__device__ __forceinline__ void collide_tile_bgk(V (&G)[3][3][3], const CollideParams& cp, const Noise& noise,
+                                                 const OutWeight& outw, const Reload& reload) {
+  V drho, jx, jy, jz, sxy, sxz, syz, axx, ayy, azz;
+  moments_order2(G, drho, jx, jy, jz, sxy, sxz, syz, axx, ayy, azz);
+  const V rho = vadd(splat<V>(cp.rho0), drho);
+  const V inv_rho = vrcp(rho);
+  const V ux = vmul(jx, inv_rho), uy = vmul(jy, inv_rho), uz = vmul(jz, inv_rho);
+  const float om = cp.omega;
+  const V Uy[3] = {splat<V>(1.0f), kmul(3.0f, uy), vmul(kmul(4.5f, uy), uy)};
+  const V Uz[3] = {splat<V>(1.0f), kmul(3.0f, uz), vmul(kmul(4.5f, uz), uz)};
+  // omega times the equilibrium moments; the shifted density mode is omega drho
+  const V RX[3] = {kmul(om, rho), kmul(3.0f * om, jx), vmul(kmul(4.5f * om, jx), ux)};
+  V M[3][3][3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const V yz = q == 0 ? Uz[r] : (r == 0 ? Uy[q] : vmul(Uy[q], Uz[r]));
+        M[p][q][r] = (q == 0 && r == 0) ? RX[p] : vmul(RX[p], yz);
+      }
+  M[0][0][0] = kmul(om, drho);
+  M[0][1][0] = kmul(3.0f * om, jy);
+  M[0][0][1] = kmul(3.0f * om, jz);
+  inject_noise<kNoise, kPhiRho0>(M, rho, cp, noise);
+  // the back transform of Eq. 11 (as back_transform), each output combined with (1 - omega) g
+  V Z[3][3][3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      line_inverse_v(M[p][q][0], M[p][q][1], M[p][q][2], Z[p][q][0], Z[p][q][1], Z[p][q][2]);
+  V Y[3][3][3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      line_inverse_v(Z[p][0][c], Z[p][1][c], Z[p][2][c], Y[p][0][c], Y[p][1][c], Y[p][2][c]);
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      V o[3];
+      line_inverse_v(Y[0][b][c], Y[1][b][c], Y[2][b][c], o[0], o[1], o[2]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        G[a][b][c] = vfma(splat<V>(1.0f - om), reload(a, b, c, G[a][b][c]), vmul(splat<V>(outw(a, b, c)), o[a]));
+    }
+}
+
+template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0, class V, class Noise, class OutWeight,
+          class Reload = KeepTile>
+__device__ __forceinline__ void collide_tile(V (&G)[3][3][3], const CollideParams& cp,
+                                          const Noise& noise, const OutWeight& outw,
+                                          const Reload& reload = Reload()) {
+  if (kModel == kModelBgk) {
+    collide_tile_bgk<kNoise, kPhiRho0>(G, cp, noise, outw, reload);
+    return;
+  }
+  // ---- 1. moments of order <= 2
+  V drho, jx, jy, jz, sxy, sxz, syz, axx, ayy, azz;
+  moments_order2(G, drho, jx, jy, jz, sxy, sxz, syz, axx, ayy, azz);
 
   // ---- 2. density, velocity and the scaled post-collision moments
   const V rho = vadd(splat<V>(cp.rho0), drho);
@@ -420,10 +430,10 @@ __device__ __forceinline__ void collide_tile(V (&G)[3][3][3], const CollideParam
 
 // The collision of one site per thread with its normals drawn beforehand and the lattice
 // weights (the storage scale is applied by the caller).
-template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
+template <int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0, class Reload = KeepTile>
 __device__ __forceinline__ void collide_site(float (&G)[3][3][3], const CollideParams& cp,
-                                             const SiteNoise& noise) {
-  collide_tile<kModel, kNoise, kGhostNeq, kPhiRho0>(G, cp, DrawnNoise{noise}, LatticeWeight());
+                                             const SiteNoise& noise, const Reload& reload = Reload()) {
+  collide_tile<kModel, kNoise, kGhostNeq, kPhiRho0>(G, cp, DrawnNoise{noise}, LatticeWeight(), reload);
 }
 
 }  // namespace rflbm_dev

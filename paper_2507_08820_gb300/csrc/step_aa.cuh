@@ -91,7 +91,14 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   for (int i = 0; i < kQ; ++i)
     G[cx_of(i) + 1][cy_of(i) + 1][cz_of(i) + 1] = S::load(sm[plane_of(i) * kW + t], class_of(i), p.ss);
 
-  collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
+  if (kModel == kModelBgk) {
+    const auto reload = [&](int a, int b, int c, float) {
+      return S::load(sm[(9 * b + 3 * c + a) * kW + t], class_at(a, b, c), p.ss);
+    };
+    collide_site<kModel, kNoise, false, false>(G, p.cp, noise, reload);
+  } else {
+    collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
+  }
 
   __syncthreads();  // all inputs are read: the tile can take the outputs
 #pragma unroll
@@ -200,7 +207,14 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
         S::load(mine[gi * L::kGroup + (1 - cx_of(i)) * L::kSeg - cx_of(i)], class_of(i), p.ss);
   }
 
-  collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
+  if (kModel == kModelBgk) {
+    const auto reload = [&](int a, int b, int c, float) {
+      return S::load(mine[(3 * b + c) * L::kGroup + (2 - a) * L::kSeg + (1 - a)], class_at(a, b, c), p.ss);
+    };
+    collide_site<kModel, kNoise, false, false>(G, p.cp, noise, reload);
+  } else {
+    collide_site<kModel, kNoise, false, false>(G, p.cp, noise);
+  }
 
   if (kFullRow) {
     // the segment is the whole row: population i of x goes to position (x + c_x) mod nx of

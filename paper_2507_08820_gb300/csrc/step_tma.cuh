@@ -128,7 +128,15 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
         S::load(mine[gi * L::kGroup + (cx_of(i) + 1) * L::kSeg - cx_of(i)], class_of(i), p.ss);
   }
 
-  collide_site<kModel, kNoise, kGhostNeq, kPhiRho0>(G, p.cp, noise);
+  if (kModel == kModelBgk) {
+    // BGK re-reads its inputs from the tile at the end instead of keeping them in registers
+    const auto reload = [&](int a, int b, int c, float) {
+      return S::load(mine[(3 * b + c) * L::kGroup + a * L::kSeg - (a - 1)], class_at(a, b, c), p.ss);
+    };
+    collide_site<kModel, kNoise, kGhostNeq, kPhiRho0>(G, p.cp, noise, reload);
+  } else {
+    collide_site<kModel, kNoise, kGhostNeq, kPhiRho0>(G, p.cp, noise);
+  }
 
   __syncthreads();  // every thread has read its inputs: the tile can hold the outputs
   T* out = sm + t;  // dense [plane][kW] output tile at the (128-byte aligned) start
