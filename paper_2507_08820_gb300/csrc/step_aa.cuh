@@ -28,8 +28,10 @@
 //    slower: tensor stores of each segment's aligned interior with plain stores at its
 //    edges, and the segments of a row as one thread-block cluster handing the edge values
 //    to their neighbours through distributed shared memory.)
-// Both forms use programmatic dependent launch and bounded mbarrier waits like the
-// ping-pong kernel: global memory is touched only after griddepcontrol.wait, so an in-place
+// Reg-FLBM forms are held to 9 CTAs of 128 threads per SM (56 registers; 8 CTAs at the 60
+// registers the compiler would take measured 93.0 % against 94.0 % of the copy bandwidth at
+// 128^3), BGK forms to 8. Both forms use programmatic dependent launch and bounded mbarrier
+// waits like the ping-pong kernel: global memory is touched only after griddepcontrol.wait, so an in-place
 // step never overlaps the previous one.
 #pragma once
 
@@ -45,7 +47,7 @@ struct AaEvenLayout {
 };
 
 template <int kStore, int kW, int kModel, bool kNoise>
-__global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_aa_even(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 1152 / kW) step_aa_even(const __grid_constant__ CUtensorMap map,
                                                    const StepParams p) {
   using S = Storage<kStore>;
   using T = typename S::T;
@@ -126,7 +128,7 @@ struct AaRowOut {
 };
 
 template <int kStore, int kW, int kModel, bool kNoise, bool kFullRow>
-__global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_aa_odd(const __grid_constant__ CUtensorMap load_map,
+__global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 1152 / kW) step_aa_odd(const __grid_constant__ CUtensorMap load_map,
                                                   const __grid_constant__ CUtensorMap row_map,
                                                   const StepParams p) {
   using S = Storage<kStore>;
