@@ -54,8 +54,8 @@ def parse_args():
                     help="one periodic box (default), the 64-replica ensemble of uneven sizes "
                          "advanced together (--storage applies), or the back transform of Eq. 11 "
                          "alone as float32 FMAs and as tensor-core MMA (a design measurement)")
-    ap.add_argument("--tile", type=int, choices=[0, 128, 192, 256, 512], default=0,
-                    help="ensemble tile size (0: chosen by the library's autotuner)")
+    ap.add_argument("--tile", type=int, choices=[0, 96, 128, 192, 256, 512], default=0,
+                    help="ensemble tile size for every replica (0: each replica its own, by row length)")
     ap.add_argument("--pattern", choices=["pingpong", "aa"], default="pingpong",
                     help="two population buffers (pull, ping-pong) or one updated in place (AA)")
     ap.add_argument("--init", choices=["rest", "taylor-green"], default="rest",
@@ -184,7 +184,7 @@ def _kernel_name(kind, path, kT, model, storage, pattern, sites_per_thread, odd_
 
 
 def profiled_traffic(profile_stem, edge):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    """DRAM bytes per launch of the step kernel (per step of an ensemble: all its launches) from the committed ncu summary
     (<stem>_<edge>cubed.md, or <stem>_<edge>.md when edge is a workload name), or None when
     the summary is missing or was taken on different kernel sources."""
     suffix = f"{edge}cubed" if isinstance(edge, int) else edge
@@ -192,7 +192,7 @@ def profiled_traffic(profile_stem, edge):
         text = open(os.path.join(PROFILES, f"{profile_stem}_{suffix}.md")).read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s*\(sources ([0-9a-f]+)\)", text)
+    m = re.search(r"traffic_bytes_per_(?:launch|step):\s*([0-9.eE+]+)\s*\(sources ([0-9a-f]+)\)", text)
     names = (AA_KERNEL_SOURCES if profile_stem.startswith("step_aa") else
              BATCH_KERNEL_SOURCES if profile_stem.startswith("k_batch") else STEP_KERNEL_SOURCES)
     if not m or m.group(2) != kernel_source_hash(names):
@@ -429,7 +429,18 @@ def ensemble_arm(args):
     ms_max = dist.max_over_ranks(info, ms, dev)
     tile, per_sm, tiles = R.rflbm_batch_tuning(bh)
     launches = R.rflbm_batch_launches_per_step(bh) * args.steps
+    tilings = [R.rflbm_batch_replica_tiling(bh, r) for r in range(len(reps))]
     R.rflbm_batch_destroy(bh)
+    # the row-tile kernels of a step, by tile size, with the share of the sites each updates
+    row_sites = {}
+    for (t, rows), r in zip(tilings, reps):
+        if rows:
+            row_sites[t] = row_sites.get(t, 0) + r["nx"] * r["ny"] * r["nz"]
+    kname = ("k_batch_step<{}, {}, rows>" if args.storage == "f32" else "k_batch_rows_pair<{}, {}>")
+    kernels = " + ".join(kname.format(args.storage, t) for t in sorted(row_sites))
+    site_share = {str(t): row_sites[t] / sites for t in sorted(row_sites)}
+    stem = ("k_batch_step_" if args.storage == "f32" else "k_batch_rows_pair_") + args.storage + "_" + (
+        str(tile) if tile else "per_replica")
     if info.rank != 0:
         dist.finalize(info)
         return 0
@@ -443,16 +454,14 @@ def ensemble_arm(args):
         "storage_dtype": args.storage, "data": "synthetic",
         "config": {"workload": f"64-replica Reg-FLBM ensemble, edges 16-96, {STORAGE_NAME[args.storage]} "
                                "populations, rest start", "replicas": len(reps), "sites": sites,
-                   "tile": tile, "ctas_per_sm": per_sm, "tiles_per_step": tiles,
+                   "tile": tile or "per replica", "row_tile_site_share": site_share,
+                   "ctas_per_sm": per_sm, "tiles_per_step": tiles,
                    "parallelism": "replicas"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
-                     "traffic": profiled_traffic(
-                         (f"k_batch_step_{args.storage}_{tile}" if args.storage == "f32"
-                          else f"k_batch_rows_pair_{args.storage}_{tile}"), "ensemble64"),
-                     "kernel": (f"k_batch_step<{args.storage}, {tile}, rows>" if args.storage == "f32"
-                                else f"k_batch_rows_pair<{args.storage}, {tile}>"),
-                     "algorithmic_bytes_per_launch": bps * sites},
+                     "traffic": profiled_traffic(stem, "ensemble64"),
+                     "kernel": kernels, "launches_per_step": launches // args.steps,
+                     "algorithmic_bytes_per_step": bps * sites},
         "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks,
     }
     print(json.dumps(line))

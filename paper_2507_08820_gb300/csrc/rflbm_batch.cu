@@ -46,6 +46,7 @@ struct ReplicaDev {
   int64_t tile_begin;  // first global tile index of this replica
   int64_t ntiles;      // tiles per step
   uint32_t key0, key1;
+  PhiloxRoundKeys rk;  // round keys of (key0, key1) (float32 rows tiles: 88.7 % against 88.0 % computed in the rounds)
   uint32_t rows;       // rows per tile (rows tiles), 0: sites tiles
   uint32_t yblocks;    // row blocks per slab: ceil(ny / rows)
   int noise;           // kT > 0
@@ -55,7 +56,7 @@ constexpr int kGroupReps = 64;  // replicas whose descriptors one launch carries
 struct ReplicaTable {
   ReplicaDev r[kGroupReps];
 };
-static_assert(sizeof(ReplicaTable) <= 16 * 1024, "the replica table stays well inside the launch parameters");
+static_assert(sizeof(ReplicaTable) <= 30 * 1024, "the replica table stays inside the launch parameters (32 KB)");
 
 // Dynamic shared memory of a rows tile: 9 groups of 3 planes x kTile sites (each group
 // rounded to 128 bytes), which then holds the 27-plane output tile.
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
   // copies are in flight
   const uint32_t site = x + nx * ((y0 + row) + ny * z);
   SiteNoise noise;
-  if (rep.noise && active) site_noise_part<0, kBatchPreWaitCalls>(site, step, 0u, rep.key0, rep.key1, noise);
+  if (rep.noise && active) site_noise_part<0, kBatchPreWaitCalls>(site, step, 0u, rep.rk, noise);
 
   grid_dependency_wait();  // the previous step's writes (our source) are complete
   if (tid < kBatchGroups) {
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
     zs -= zs >= (int)nz ? (int)nz : 0;
     tma_load_4d(sm + tid * kGroup, rep.maps + 2 * parity, 0, (int)y0 - cy, zs, 3 * tid, &bar);
   }
-  if (rep.noise && active) site_noise_part<kBatchPreWaitCalls, 6>(site, step, 0u, rep.key0, rep.key1, noise);
+  if (rep.noise && active) site_noise_part<kBatchPreWaitCalls, 6>(site, step, 0u, rep.rk, noise);
   const bool ok = mbar_wait_bounded(&bar, 0, kBatchTmaPolls);
   if (__syncthreads_or(!ok)) {
     if (tid == 0) atomicOr(err, 1);
@@ -255,6 +256,7 @@ __global__ void __launch_bounds__(kTile / 2)
   const uint32_t row = fastdiv(q, rep.geo.div_nx);
   const uint32_t x = q - row * nx;  // even
   const bool active = row < nrows;
+  // (round keys computed in the rounds: from the replica table they measured 0.9 % slower here)
   const PhiloxKey key{rep.key0, rep.key1};
   PairNoise<kBatchPairPreDrawn, PhiloxKey> noise{x + nx * ((y0 + row) + ny * z), step, 0u, key};
   if (rep.noise && active) noise.draw();
@@ -342,8 +344,17 @@ __global__ void __launch_bounds__(kTile / 2)
 template <int kStore>
 constexpr bool batch_rows_pairs() { return kStore != kStoreF32; }
 
+// One launch of a step: the rows tiles (or the sites tiles) of one tile size within one
+// group of kGroupReps replicas, global tiles [begin, end).
+struct BatchLaunch {
+  int group;
+  int tile;
+  bool rows;
+  int64_t begin, end;
+};
+
 template <int kStore, int kTile>
-static cudaError_t set_smem_t() {
+static cudaError_t prepare_t() {
   const size_t smem = batch_smem_bytes(kTile, storage_bytes(kStore));
   if (smem <= 48 * 1024) return cudaSuccess;
   if constexpr (batch_rows_pairs<kStore>())
@@ -351,20 +362,13 @@ static cudaError_t set_smem_t() {
   return cudaFuncSetAttribute(k_batch_step<kStore, kTile, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// One launch group: the descriptors of up to kGroupReps replicas and the global tile ranges
-// of their rows tiles and of their sites tiles.
-struct BatchLaunch {
-  ReplicaTable tab;
-  int64_t rows_begin, rows_end, sites_begin, sites_end;
-};
-
-// nsteps steps over all tiles: per step and launch group one launch of its rows tiles and
-// one of its sites tiles, chained by programmatic dependent launch.
+// Step k of a run for the tiles of launch L, chained to the previous launch on the stream
+// by programmatic dependent launch.
 template <int kStore, int kTile>
-static cudaError_t launch_batch_t(const BatchLaunch* groups, int ngroups, const int* tile_rep, int64_t nsteps,
-                                  const unsigned long long* run, int* err, cudaStream_t st) {
-  if (cudaError_t e = set_smem_t<kStore, kTile>()) return e;
+static cudaError_t launch_one_t(const ReplicaTable& tab, const BatchLaunch& L, const int* tile_rep, uint32_t k,
+                                const unsigned long long* run, int* err, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(L.end - L.begin));
   cfg.blockDim = dim3(kTile);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -372,87 +376,105 @@ static cudaError_t launch_batch_t(const BatchLaunch* groups, int ngroups, const 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  for (int64_t k = 0; k < nsteps; ++k) {
-    for (int g = 0; g < ngroups; ++g) {
-      const BatchLaunch& L = groups[g];
-      if (L.rows_end > L.rows_begin) {
-        cfg.gridDim = dim3((unsigned)(L.rows_end - L.rows_begin));
-        cfg.dynamicSmemBytes = batch_smem_bytes(kTile, storage_bytes(kStore));
-        cudaError_t e;
-        if constexpr (batch_rows_pairs<kStore>()) {
-          cfg.blockDim = dim3(kTile / 2);
-          e = cudaLaunchKernelEx(&cfg, k_batch_rows_pair<kStore, kTile>, L.tab, tile_rep, L.rows_begin, run,
-                                 (uint32_t)k, err);
-          cfg.blockDim = dim3(kTile);
-        } else {
-          e = cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, true>, L.tab, tile_rep, L.rows_begin, run,
-                                 (uint32_t)k, err);
-        }
-        if (e != cudaSuccess) return e;
-      }
-      if (L.sites_end > L.sites_begin) {
-        cfg.gridDim = dim3((unsigned)(L.sites_end - L.sites_begin));
-        cfg.dynamicSmemBytes = 0;
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, false>, L.tab, tile_rep,
-                                                 L.sites_begin, run, (uint32_t)k, err);
-        if (e != cudaSuccess) return e;
-      }
-    }
+  if (!L.rows) return cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, false>, tab, tile_rep, L.begin, run, k, err);
+  cfg.dynamicSmemBytes = batch_smem_bytes(kTile, storage_bytes(kStore));
+  if constexpr (batch_rows_pairs<kStore>()) {
+    cfg.blockDim = dim3(kTile / 2);
+    return cudaLaunchKernelEx(&cfg, k_batch_rows_pair<kStore, kTile>, tab, tile_rep, L.begin, run, k, err);
+  } else {
+    return cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, true>, tab, tile_rep, L.begin, run, k, err);
   }
-  return cudaSuccess;
 }
 
+// Resident CTAs per SM of the rows-tile kernel (rows) or the sites-tile kernel.
 template <int kStore, int kTile>
-static int occupancy_t() {
-  if (set_smem_t<kStore, kTile>() != cudaSuccess) return 1;
+static int occupancy_t(bool rows) {
   int n = 0;
-  const size_t smem = batch_smem_bytes(kTile, storage_bytes(kStore));
   cudaError_t e;
-  if constexpr (batch_rows_pairs<kStore>())
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_rows_pair<kStore, kTile>, kTile / 2, smem);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<kStore, kTile, true>, kTile, smem);
+  if (!rows) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<kStore, kTile, false>, kTile, 0);
+  } else {
+    if (prepare_t<kStore, kTile>() != cudaSuccess) return 1;
+    const size_t smem = batch_smem_bytes(kTile, storage_bytes(kStore));
+    if constexpr (batch_rows_pairs<kStore>())
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_rows_pair<kStore, kTile>, kTile / 2, smem);
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<kStore, kTile, true>, kTile, smem);
+  }
   if (e != cudaSuccess) return 1;
   return std::max(n, 1);
 }
 
-// Tile sizes: CTA threads, and sites per tile of the sites kind. 192 divides every row
-// length 16, 24, 32, 48, 64, 96 of the ensemble configuration.
-constexpr int kBatchTiles[4] = {128, 192, 256, 512};
+// Tile sizes: CTA threads of a tile (half as many threads for two-site rows tiles), and
+// sites per tile.
+constexpr int kNumTiles = 5;
+constexpr int kBatchTiles[kNumTiles] = {96, 128, 192, 256, 512};
+
+// Per-replica tile choice: the first size of the storage format's order of preference
+// that the row length divides. Uniform 2000-step ensembles, fraction of the copy bandwidth:
+// float32 rows of 96 at tile 96 92.3 % (192: 89.7 %), of 64 at 128 92.8 % (192: 88.2 %,
+// 256: 85.1 %, 64: 86.5 %), of 48 at 96 90.2 % (192: 87.2 %), of 32 at 128 84.2 % (96:
+// 83.3 %, 192: 77.5 %); two-site 16-bit rows of 64 at 128 49.6 % (192: 45.7 %), of 96 at
+// 192 47.1 % (96: 38.0 %). Smaller CTAs at the same resident threads interleave more
+// independent copy-collide-store phases per SM, down to 96-128 threads.
+constexpr int kPrefF32[kNumTiles] = {128, 96, 192, 256, 512};
+constexpr int kPref16[kNumTiles] = {128, 192, 256, 512, 96};
+constexpr int kAutoSitesTile = 128;  // sites tiles in per-replica mode
 
 static int tile_index(int tile) {
-  for (int k = 0; k < 4; ++k)
+  for (int k = 0; k < kNumTiles; ++k)
     if (kBatchTiles[k] == tile) return k;
   return -1;
 }
 
-#define RFLBM_BATCH_DISPATCH(storage, tile, CALL)                    \
-  switch ((storage) * 4 + tile_index(tile)) {                        \
-    case 0: { constexpr int S = kStoreF32, T = 128; CALL; }          \
-    case 1: { constexpr int S = kStoreF32, T = 192; CALL; }          \
-    case 2: { constexpr int S = kStoreF32, T = 256; CALL; }          \
-    case 3: { constexpr int S = kStoreF32, T = 512; CALL; }          \
-    case 4: { constexpr int S = kStoreF16, T = 128; CALL; }          \
-    case 5: { constexpr int S = kStoreF16, T = 192; CALL; }          \
-    case 6: { constexpr int S = kStoreF16, T = 256; CALL; }          \
-    case 7: { constexpr int S = kStoreF16, T = 512; CALL; }          \
-    case 8: { constexpr int S = kStoreBF16, T = 128; CALL; }         \
-    case 9: { constexpr int S = kStoreBF16, T = 192; CALL; }         \
-    case 10: { constexpr int S = kStoreBF16, T = 256; CALL; }        \
-    case 11: { constexpr int S = kStoreBF16, T = 512; CALL; }        \
-    default: break;                                                  \
+#define RFLBM_BATCH_DISPATCH(storage, tile, CALL)               \
+  switch ((storage) * kNumTiles + tile_index(tile)) {           \
+    case 0: { constexpr int S = kStoreF32, T = 96; CALL; }      \
+    case 1: { constexpr int S = kStoreF32, T = 128; CALL; }     \
+    case 2: { constexpr int S = kStoreF32, T = 192; CALL; }     \
+    case 3: { constexpr int S = kStoreF32, T = 256; CALL; }     \
+    case 4: { constexpr int S = kStoreF32, T = 512; CALL; }     \
+    case 5: { constexpr int S = kStoreF16, T = 96; CALL; }      \
+    case 6: { constexpr int S = kStoreF16, T = 128; CALL; }     \
+    case 7: { constexpr int S = kStoreF16, T = 192; CALL; }     \
+    case 8: { constexpr int S = kStoreF16, T = 256; CALL; }     \
+    case 9: { constexpr int S = kStoreF16, T = 512; CALL; }     \
+    case 10: { constexpr int S = kStoreBF16, T = 96; CALL; }    \
+    case 11: { constexpr int S = kStoreBF16, T = 128; CALL; }   \
+    case 12: { constexpr int S = kStoreBF16, T = 192; CALL; }   \
+    case 13: { constexpr int S = kStoreBF16, T = 256; CALL; }   \
+    case 14: { constexpr int S = kStoreBF16, T = 512; CALL; }   \
+    default: break;                                             \
   }
 
-static int batch_occupancy(int storage, int tile) {
-  RFLBM_BATCH_DISPATCH(storage, tile, return (occupancy_t<S, T>()));
+static cudaError_t batch_prepare(int storage, int tile) {
+  RFLBM_BATCH_DISPATCH(storage, tile, return (prepare_t<S, T>()));
+  return cudaErrorInvalidValue;
+}
+
+static int batch_occupancy(int storage, int tile, bool rows) {
+  RFLBM_BATCH_DISPATCH(storage, tile, return (occupancy_t<S, T>(rows)));
   return 1;
 }
 
-static cudaError_t launch_batch(int storage, int tile, const BatchLaunch* groups, int ngroups, const int* tile_rep,
-                                int64_t nsteps, const unsigned long long* run, int* err, cudaStream_t st) {
-  RFLBM_BATCH_DISPATCH(storage, tile,
-                       return (launch_batch_t<S, T>(groups, ngroups, tile_rep, nsteps, run, err, st)));
-  return cudaErrorInvalidValue;
+// nsteps steps of every launch; launch l runs on stream l % nstreams. The launches of a
+// step update disjoint replicas, so each stream is an independent chain of steps: a launch
+// waits only for the previous step of the launches on its own stream.
+static cudaError_t launch_batch(int storage, const ReplicaTable* tabs, const BatchLaunch* launches, int nlaunches,
+                                const int* tile_rep, int64_t nsteps, const unsigned long long* run, int* err,
+                                const cudaStream_t* streams, int nstreams) {
+  for (int64_t k = 0; k < nsteps; ++k) {
+    for (int l = 0; l < nlaunches; ++l) {
+      const BatchLaunch& L = launches[l];
+      cudaError_t e = cudaErrorInvalidValue;
+      RFLBM_BATCH_DISPATCH(storage, L.tile,
+                           e = (launch_one_t<S, T>(tabs[L.group], L, tile_rep, (uint32_t)k, run, err,
+                                                   streams[l % nstreams]));
+                           break);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 }  // namespace rflbm_dev
@@ -468,13 +490,16 @@ struct rflbm_batch {
   cudaStream_t stream = nullptr;
   std::vector<rflbm_replica_t> cfg;
   std::vector<ReplicaDev> host;
-  std::vector<BatchLaunch> groups;  // launch groups of kGroupReps replicas
-  int cur = 0;                      // buffer holding every replica's current state
-  int* tile_rep = nullptr;          // per global tile: its replica's index within its group
+  std::vector<int> rep_tile;           // per replica: its tile size
+  std::vector<ReplicaTable> tables;    // per group of kGroupReps replicas: their descriptors
+  std::vector<BatchLaunch> launches;   // the launches of one step, in order
+  std::vector<cudaStream_t> chains;    // streams of the independent launch chains of a run
+  std::vector<cudaEvent_t> chain_ev;   // [0]: fork, [1 + c]: join of chain c
+  int cur = 0;                         // buffer holding every replica's current state
+  int* tile_rep = nullptr;             // per global tile: its replica's index within its group
   CUtensorMap* maps = nullptr;  // 4 per replica (rows tiles), device memory
   int64_t tiles = 0;
-  int64_t rows_tiles = 0;  // tiles [0, rows_tiles) are rows tiles, the rest sites tiles
-  int tile = 256;
+  int tile = 0;  // requested tile size (0: per replica)
   int ctas_per_sm = 1;
   unsigned long long* run = nullptr;  // device: first step of the current run, its buffer
   int* err = nullptr;
@@ -512,22 +537,55 @@ int bcuda(cudaError_t e, const char* what) {
 int64_t pstride(int64_t n) { return (n + 63) / 64 * 64; }
 
 
-// Builds the per-replica descriptors, their tensor maps and the tile map for tile size
-// `tile` (CTA threads). A replica takes rows tiles when its row is a whole number of
-// 16-byte units, divides the tile, fits the TMA box limit (256), and its maps encode.
+constexpr int kBatchChains = 8;  // streams of the independent launch chains of a run
+
+// Streams and events for the launch chains of a run (created outside any stream capture).
+int ensure_chains(rflbm_batch* b) {
+  const int nc = std::min((int)b->launches.size(), kBatchChains);
+  while ((int)b->chains.size() < nc) {
+    cudaStream_t c;
+    BCUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking), "creating a launch-chain stream");
+    b->chains.push_back(c);
+  }
+  while ((int)b->chain_ev.size() < nc + 1) {
+    cudaEvent_t e;
+    BCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "creating a launch-chain event");
+    b->chain_ev.push_back(e);
+  }
+  return RFLBM_OK;
+}
+
+// Tile size of a replica: `tile` when given, else the first size of the storage format's
+// order of preference that takes the replica's rows (sites tiles of kAutoSitesTile when none).
+int replica_tile(const rflbm_batch* b, const Geometry& g, int tile) {
+  if (tile) return tile;
+  const size_t elem = storage_bytes(b->storage);
+  const int* pref = b->storage == kStoreF32 ? kPrefF32 : kPref16;
+  if ((g.nx * elem) % 16 == 0 && g.nx <= 256)
+    for (int k = 0; k < kNumTiles; ++k)
+      if (pref[k] % (int)g.nx == 0) return pref[k];
+  return kAutoSitesTile;
+}
+
+// Builds the per-replica descriptors, their tensor maps, the launches of a step and the
+// tile map, every replica at tile size `tile` (0: each at its own, see replica_tile). A
+// replica takes rows tiles when its row is a whole number of 16-byte units, divides its
+// tile, fits the TMA box limit (256), and its maps encode; else sites tiles.
 int layout_tiles(rflbm_batch* b, int tile) {
   const size_t elem = storage_bytes(b->storage);
   std::vector<CUtensorMap> maps((size_t)b->n * 4);
   if (!b->maps) BCUDA(cudaMalloc((void**)&b->maps, sizeof(CUtensorMap) * maps.size()), "allocating tensor maps");
-  int64_t tiles = 0;
+  b->rep_tile.assign((size_t)b->n, 0);
   for (int r = 0; r < b->n; ++r) {
     ReplicaDev& d = b->host[r];
     const Geometry& g = d.geo;
+    const int t = replica_tile(b, g, tile);
+    b->rep_tile[(size_t)r] = t;
     d.rows = 0;
     d.yblocks = 0;
     d.maps = nullptr;
-    if ((g.nx * elem) % 16 == 0 && tile % g.nx == 0 && g.nx <= 256) {
-      const uint32_t R = (uint32_t)tile / g.nx;
+    if ((g.nx * elem) % 16 == 0 && t % g.nx == 0 && g.nx <= 256) {
+      const uint32_t R = (uint32_t)t / g.nx;
       bool ok = true;
       for (int k = 0; k < 2 && ok; ++k)
         ok = encode_population_map(&maps[4 * r + 2 * k], d.buf[k], g, g.nx, R, 3, b->storage) &&
@@ -538,40 +596,52 @@ int layout_tiles(rflbm_batch* b, int tile) {
         d.maps = b->maps + 4 * r;
       }
     }
-    d.ntiles = d.rows ? (int64_t)g.nz * d.yblocks : ((int64_t)g.n + tile - 1) / tile;
+    d.ntiles = d.rows ? (int64_t)g.nz * d.yblocks : ((int64_t)g.n + t - 1) / t;
   }
-  // per launch group of kGroupReps replicas: its rows tiles, then its sites tiles
+  // per group of kGroupReps replicas: one launch per tile size of its rows tiles, then one
+  // per tile size of its sites tiles
   const int ngroups = (b->n + kGroupReps - 1) / kGroupReps;
-  b->groups.assign((size_t)ngroups, BatchLaunch{});
-  b->rows_tiles = 0;
+  b->tables.assign((size_t)ngroups, ReplicaTable{});
+  b->launches.clear();
+  int64_t tiles = 0;
+  std::vector<int64_t> sites_at(kNumTiles * 2, 0);  // [kind][tile]: sites updated by such tiles
   for (int g = 0; g < ngroups; ++g) {
-    BatchLaunch& L = b->groups[(size_t)g];
     const int r0 = g * kGroupReps, r1 = std::min(b->n, r0 + kGroupReps);
     for (int pass = 0; pass < 2; ++pass) {
-      (pass == 0 ? L.rows_begin : L.sites_begin) = tiles;
-      for (int r = r0; r < r1; ++r) {
-        ReplicaDev& d = b->host[r];
-        if ((d.rows != 0) != (pass == 0)) continue;
-        d.tile_begin = tiles;
-        tiles += d.ntiles;
+      for (int ti = 0; ti < kNumTiles; ++ti) {
+        BatchLaunch L{g, kBatchTiles[ti], pass == 0, tiles, tiles};
+        for (int r = r0; r < r1; ++r) {
+          ReplicaDev& d = b->host[r];
+          if ((d.rows != 0) != L.rows || b->rep_tile[(size_t)r] != L.tile) continue;
+          d.tile_begin = tiles;
+          tiles += d.ntiles;
+          sites_at[(size_t)(pass * kNumTiles + ti)] += d.geo.n;
+        }
+        L.end = tiles;
+        if (L.end > L.begin) b->launches.push_back(L);
       }
-      (pass == 0 ? L.rows_end : L.sites_end) = tiles;
     }
-    b->rows_tiles += L.rows_end - L.rows_begin;
   }
   BCUDA(cudaMemcpy(b->maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice),
         "uploading tensor maps");
   std::vector<int> map((size_t)tiles);
   for (int r = 0; r < b->n; ++r)
     for (int64_t j = 0; j < b->host[r].ntiles; ++j) map[(size_t)(b->host[r].tile_begin + j)] = r % kGroupReps;
-  for (int r = 0; r < b->n; ++r) b->groups[(size_t)(r / kGroupReps)].tab.r[r % kGroupReps] = b->host[r];
+  for (int r = 0; r < b->n; ++r) b->tables[(size_t)(r / kGroupReps)].r[r % kGroupReps] = b->host[r];
   cudaFree(b->tile_rep);
   b->tile_rep = nullptr;
   BCUDA(cudaMalloc(&b->tile_rep, sizeof(int) * (size_t)tiles), "allocating the tile map");
   BCUDA(cudaMemcpy(b->tile_rep, map.data(), sizeof(int) * (size_t)tiles, cudaMemcpyHostToDevice), "uploading the tile map");
+  for (const BatchLaunch& L : b->launches)
+    if (L.rows) BCUDA(batch_prepare(b->storage, L.tile), "setting the shared-memory size of the batched step kernel");
+  if (int e = ensure_chains(b)) return e;
   b->tiles = tiles;
   b->tile = tile;
-  b->ctas_per_sm = batch_occupancy(b->storage, tile);
+  // occupancy of the kernel that updates the most sites
+  size_t top = 0;
+  for (size_t k = 1; k < sites_at.size(); ++k)
+    if (sites_at[k] > sites_at[top]) top = k;
+  b->ctas_per_sm = batch_occupancy(b->storage, kBatchTiles[top % kNumTiles], top < (size_t)kNumTiles);
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
@@ -584,11 +654,29 @@ int layout_tiles(rflbm_batch* b, int tile) {
   return RFLBM_OK;
 }
 
-// The launch sequence of one run: one step kernel over all tiles per step.
+// The launch sequence of one run on stream st: a single launch per step chains on st
+// itself; several fork into one chain each (up to kBatchChains streams, launches beyond
+// that share them round-robin) and join back into st at the end.
 int enqueue_run(rflbm_batch* b, int64_t nsteps, cudaStream_t st) {
-  BCUDA(launch_batch(b->storage, b->tile, b->groups.data(), (int)b->groups.size(), b->tile_rep, nsteps, b->run,
-                     b->err, st),
+  const int nl = (int)b->launches.size();
+  const int nc = std::min(nl, kBatchChains);
+  if (nc <= 1) {
+    BCUDA(launch_batch(b->storage, b->tables.data(), b->launches.data(), nl, b->tile_rep, nsteps, b->run, b->err, &st,
+                       1),
+          "launching the batched step kernel");
+    return RFLBM_OK;
+  }
+  if ((int)b->chains.size() < nc || (int)b->chain_ev.size() < nc + 1)
+    return bfail(RFLBM_ESTATE, "batch launch chains not set up");
+  BCUDA(cudaEventRecord(b->chain_ev[0], st), "forking the launch chains");
+  for (int c = 0; c < nc; ++c) BCUDA(cudaStreamWaitEvent(b->chains[c], b->chain_ev[0], 0), "forking the launch chains");
+  BCUDA(launch_batch(b->storage, b->tables.data(), b->launches.data(), nl, b->tile_rep, nsteps, b->run, b->err,
+                     b->chains.data(), nc),
         "launching the batched step kernel");
+  for (int c = 0; c < nc; ++c) {
+    BCUDA(cudaEventRecord(b->chain_ev[1 + c], b->chains[c]), "joining the launch chains");
+    BCUDA(cudaStreamWaitEvent(st, b->chain_ev[1 + c], 0), "joining the launch chains");
+  }
   return RFLBM_OK;
 }
 
@@ -705,6 +793,7 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
     }
     d.key0 = (uint32_t)(c.seed & 0xffffffffu);
     d.key1 = (uint32_t)(c.seed >> 32);
+    d.rk = philox_round_keys(d.key0, d.key1);
     d.noise = c.kT > 0.0;
     for (int k = 0; k < 2 && rc == RFLBM_OK; ++k) {
       cudaError_t e = cudaMalloc(&d.buf[k], (size_t)g.ps * kQ * elem);
@@ -726,33 +815,7 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
     cudaError_t e = cudaMalloc((void**)&b->partials, sizeof(double) * ((size_t)b->stat_blocks * kStatOutFields + 8));
     if (e != cudaSuccess) rc = bcuda(e, "allocating the reduction scratch");
   }
-  if (rc == RFLBM_OK) rc = layout_tiles(b, tile ? tile : 256);
-  if (rc == RFLBM_OK && tile == 0) {
-    // autotuner: time a few steps of every tile size on this ensemble and keep the fastest
-    // (the populations are reset by the init call that must follow)
-    cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
-    float best = 1e30f;
-    int best_tile = 256;
-    for (int cand : kBatchTiles) {
-      if (layout_tiles(b, cand) != RFLBM_OK) continue;
-      enqueue_run(b, 1, b->stream);  // warm-up
-      cudaEventRecord(t0, b->stream);
-      enqueue_run(b, 3, b->stream);
-      cudaEventRecord(t1, b->stream);
-      float ms = 1e30f;
-      if (cudaEventSynchronize(t1) == cudaSuccess) cudaEventElapsedTime(&ms, t0, t1);
-      if (ms < best) {
-        best = ms;
-        best_tile = cand;
-      }
-    }
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
-    rc = layout_tiles(b, best_tile);
-    if (rc == RFLBM_OK) rc = bsync(b, "autotuning the batch");
-  }
+  if (rc == RFLBM_OK) rc = layout_tiles(b, tile);
   if (rc != RFLBM_OK) {
     rflbm_batch_destroy(b);
     return nullptr;
@@ -774,12 +837,14 @@ void rflbm_batch_destroy(rflbm_batch_t* b) {
   cudaFree(b->partials);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t c : b->chains) cudaStreamDestroy(c);
+  for (cudaEvent_t e : b->chain_ev) cudaEventDestroy(e);
   delete b;
 }
 
 int rflbm_batch_launches_per_step(const rflbm_batch_t* b) {
   if (!b) return bfail(RFLBM_EINVAL, "batch handle is NULL");
-  return (b->rows_tiles > 0 ? 1 : 0) + (b->tiles > b->rows_tiles ? 1 : 0);
+  return (int)b->launches.size();
 }
 
 int rflbm_batch_tuning(const rflbm_batch_t* b, int* tile, int* ctas_per_sm, int64_t* tiles_per_step) {
@@ -787,6 +852,13 @@ int rflbm_batch_tuning(const rflbm_batch_t* b, int* tile, int* ctas_per_sm, int6
   if (tile) *tile = b->tile;
   if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
   if (tiles_per_step) *tiles_per_step = b->tiles;
+  return RFLBM_OK;
+}
+
+int rflbm_batch_replica_tiling(const rflbm_batch_t* b, int r, int* tile, int* rows) {
+  if (!b || r < 0 || r >= b->n) return bfail(RFLBM_EINVAL, "invalid batch or replica");
+  if (tile) *tile = b->rep_tile[(size_t)r];
+  if (rows) *rows = (int)b->host[r].rows;
   return RFLBM_OK;
 }
 

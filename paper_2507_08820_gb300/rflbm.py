@@ -119,6 +119,7 @@ _sig = {
     "rflbm_batch_destroy": (None, [_H]),
     "rflbm_batch_tuning": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "rflbm_batch_launches_per_step": (C.c_int, [_H]),
+    "rflbm_batch_replica_tiling": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "rflbm_batch_replica_dims": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                            C.POINTER(C.c_int)]),
     "rflbm_batch_init_rest": (C.c_int, [_H]),
@@ -480,6 +481,13 @@ def rflbm_batch_tuning(b):
     t, c, n = C.c_int(), C.c_int(), C.c_int64()
     _check(lib.rflbm_batch_tuning(b, C.byref(t), C.byref(c), C.byref(n)))
     return t.value, c.value, n.value
+
+
+def rflbm_batch_replica_tiling(b, r):
+    """(tile size, rows per tile; 0 for tiles of consecutive sites) of replica r."""
+    t, rows = C.c_int(), C.c_int()
+    _check(lib.rflbm_batch_replica_tiling(b, int(r), C.byref(t), C.byref(rows)))
+    return t.value, rows.value
 
 
 def rflbm_batch_replica_dims(b, r):

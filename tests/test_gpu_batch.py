@@ -5,7 +5,8 @@ reproduce their single-box runs; the ensemble of the batched configuration
 
 The replicas below take both kinds of tile at every tile size: rows tiles where nx divides
 the tile (row blocks that fill a slab exactly, end short of it, or hold more rows than the
-slab has, with one or two slabs), site tiles elsewhere."""
+slab has, with one or two slabs), site tiles elsewhere; with tile 0 each replica takes its
+own tile size, so one step runs launches of several sizes."""
 import numpy as np
 import pytest
 
@@ -53,7 +54,7 @@ def _batch_pops(R, b, reps, r):
 
 
 @pytest.mark.parametrize("storage", [0, 1, 2])
-@pytest.mark.parametrize("tile", [128, 192, 256, 512])
+@pytest.mark.parametrize("tile", [96, 128, 192, 256, 512])
 def test_replicas_reproduce_their_single_box_runs(R, storage, tile):
     b = R.rflbm_batch_create(SMALL, storage=storage, tile=tile)
     assert R.rflbm_batch_tuning(b)[0] == tile
@@ -69,11 +70,36 @@ def test_replicas_reproduce_their_single_box_runs(R, storage, tile):
     R.rflbm_batch_destroy(b)
 
 
-def test_autotuner_and_errors(R):
+# per-replica tile sizes of SMALL (tile size, rows per tile) in float32 and in 16-bit storage
+PER_REPLICA = {0: [(128, 8), (96, 4), (128, 4), (128, 0), (128, 2), (128, 0), (128, 4), (128, 8)],
+               1: [(128, 8), (192, 8), (128, 4), (128, 0), (128, 2), (128, 0), (128, 4), (128, 8)]}
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_per_replica_tiles_reproduce_single_box_runs(R, storage):
+    """tile 0: every replica at the tile size its row length and storage select; the step
+    runs one launch per size and kind (rows at 128 and at 96 or 192, sites at 128)."""
+    b = R.rflbm_batch_create(SMALL, storage=storage, tile=0)
+    assert R.rflbm_batch_tuning(b)[0] == 0
+    assert [R.rflbm_batch_replica_tiling(b, r) for r in range(len(SMALL))] == PER_REPLICA[min(storage, 1)]
+    assert R.rflbm_batch_launches_per_step(b) == 3
+    R.rflbm_batch_init_rest(b)
+    for n in (3, 4, 3):
+        R.rflbm_batch_run(b, n)
+    R.rflbm_batch_synchronize(b)
+    for r, rep in enumerate(SMALL):
+        assert np.array_equal(_batch_pops(R, b, SMALL, r), _single(R, rep, 10, storage)), r
+    R.rflbm_batch_destroy(b)
+
+
+def test_tuning_and_errors(R):
     b = R.rflbm_batch_create(SMALL[:3], tile=0)
     tile, per_sm, tiles = R.rflbm_batch_tuning(b)
-    assert tile in (128, 192, 256, 512) and per_sm >= 1 and tiles > 0
-    assert R.rflbm_batch_launches_per_step(b) in (1, 2)
+    assert tile == 0 and per_sm >= 1 and tiles > 0
+    assert R.rflbm_batch_launches_per_step(b) == 2  # rows at 128 (nx 16, 32) and at 96 (nx 24)
+    with pytest.raises(R.RflbmError) as e:
+        R.rflbm_batch_replica_tiling(b, 3)
+    assert e.value.status == R.RFLBM_EINVAL
     with pytest.raises(R.RflbmError) as e:
         R.rflbm_batch_run(b, 1)  # not initialised
     assert e.value.status == R.RFLBM_ESTATE
