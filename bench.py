@@ -412,6 +412,7 @@ def ensemble_arm(args):
     bh = R.rflbm_batch_create(reps, storage=storage, tile=args.tile)
     R.rflbm_batch_init_rest(bh)
     R.rflbm_batch_run(bh, args.warmup)
+    R.rflbm_batch_prepare(bh, args.steps)  # the timed call's graph is built before the timed region
     R.rflbm_batch_synchronize(bh)
     sampler = ClockSampler(device_uuid(torch))
     dist.barrier(info, info.local_rank)
@@ -704,8 +705,9 @@ def gb300_arm(args):
             bh = R.rflbm_batch_create(reps, storage=st_b, tile=0)
             R.rflbm_batch_init_rest(bh)
             R.rflbm_batch_run(bh, 20)
+            k = max(200, args.steps // 20)
+            R.rflbm_batch_prepare(bh, k)
             R.rflbm_batch_synchronize(bh)
-            k = max(20, args.steps // 20)
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(torch.cuda.default_stream())
             R.rflbm_batch_run(bh, k)
@@ -714,7 +716,7 @@ def gb300_arm(args):
             sites_s = sites * k / (ev0.elapsed_time(ev1) * 1e-3)
             tile, per_sm, _ = R.rflbm_batch_tuning(bh)
             variants[name] = {"value": sites_s / 1e6, "unit": "MLUPS", "steps": k,
-                              "replicas": len(reps), "sites": sites, "tile": tile,
+                              "replicas": len(reps), "sites": sites, "tile": tile or "per replica",
                               "roofline_frac": bps * sites_s / 1e9 / peak_v, "bytes_per_site": bps}
             R.rflbm_batch_destroy(bh)
     box.close()

@@ -326,8 +326,13 @@ int rflbm_batch_launches_per_step(const rflbm_batch_t* b);
 int rflbm_batch_replica_dims(const rflbm_batch_t* b, int r, int* nx, int* ny, int* nz);
 /* Every replica at rest, step 0. */
 int rflbm_batch_init_rest(rflbm_batch_t* b);
-/* n steps of every replica (asynchronous on the default stream). */
+/* n steps of every replica (asynchronous on the default stream). The n steps replay one
+ * CUDA graph, captured and instantiated on the host by the first call with this n (the
+ * handle keeps the graph of the last n). */
 int rflbm_batch_run(rflbm_batch_t* b, int64_t n);
+/* Captures and instantiates the graph of an n-step run (n >= 1) without running it, so that
+ * the next rflbm_batch_run(b, n) only launches it. Launches nothing. */
+int rflbm_batch_prepare(rflbm_batch_t* b, int64_t n);
 int rflbm_batch_synchronize(rflbm_batch_t* b);
 /* Populations (27*N doubles, public layout) and diagnostics of replica r. Synchronous. */
 int rflbm_batch_get_populations(rflbm_batch_t* b, int r, double* f);

@@ -693,9 +693,7 @@ int bsync(rflbm_batch* b, const char* what) {
 
 // Runs n steps through a CUDA graph of the launch sequence (captured once per n; the
 // starting step is read by the kernel from device memory, written before each launch).
-int run_graph(rflbm_batch* b, int64_t n) {
-  const unsigned long long r0[2] = {(unsigned long long)b->step, (unsigned long long)b->cur};
-  BCUDA(cudaMemcpyAsync(b->run, r0, sizeof(r0), cudaMemcpyHostToDevice, b->stream), "setting the step index");
+int build_graph(rflbm_batch* b, int64_t n) {
   if (!b->exec || b->graph_steps != n) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -719,6 +717,13 @@ int run_graph(rflbm_batch* b, int64_t n) {
     b->graph = g;
     b->graph_steps = n;
   }
+  return RFLBM_OK;
+}
+
+int run_graph(rflbm_batch* b, int64_t n) {
+  const unsigned long long r0[2] = {(unsigned long long)b->step, (unsigned long long)b->cur};
+  BCUDA(cudaMemcpyAsync(b->run, r0, sizeof(r0), cudaMemcpyHostToDevice, b->stream), "setting the step index");
+  if (int e = build_graph(b, n)) return e;
   BCUDA(cudaGraphLaunch(b->exec, b->stream), "launching the batched run graph");
   return RFLBM_OK;
 }
@@ -891,6 +896,12 @@ int rflbm_batch_run(rflbm_batch_t* b, int64_t n) {
   b->step += n;
   if (n & 1) b->cur ^= 1;
   return RFLBM_OK;
+}
+
+int rflbm_batch_prepare(rflbm_batch_t* b, int64_t n) {
+  if (!b) return bfail(RFLBM_EINVAL, "batch handle is NULL");
+  if (n < 1) return bfail(RFLBM_EINVAL, "rflbm_batch_prepare: n must be positive");
+  return build_graph(b, n);
 }
 
 int rflbm_batch_synchronize(rflbm_batch_t* b) {

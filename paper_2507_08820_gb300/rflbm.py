@@ -124,6 +124,7 @@ _sig = {
                                            C.POINTER(C.c_int)]),
     "rflbm_batch_init_rest": (C.c_int, [_H]),
     "rflbm_batch_run": (C.c_int, [_H, C.c_int64]),
+    "rflbm_batch_prepare": (C.c_int, [_H, C.c_int64]),
     "rflbm_batch_synchronize": (C.c_int, [_H]),
     "rflbm_batch_get_populations": (C.c_int, [_H, C.c_int, _P]),
     "rflbm_batch_stats": (C.c_int, [_H, C.c_int, C.POINTER(rflbm_stats_t)]),
@@ -507,6 +508,11 @@ def rflbm_batch_init_rest(b):
 
 def rflbm_batch_run(b, n):
     return _check(lib.rflbm_batch_run(b, int(n)))
+
+
+def rflbm_batch_prepare(b, n):
+    """Builds the CUDA graph of an n-step run without running it."""
+    return _check(lib.rflbm_batch_prepare(b, int(n)))
 
 
 def rflbm_batch_synchronize(b):

@@ -92,6 +92,52 @@ def test_per_replica_tiles_reproduce_single_box_runs(R, storage):
     R.rflbm_batch_destroy(b)
 
 
+def test_prepare_builds_the_run_without_running_it(R):
+    """rflbm_batch_prepare(n) launches nothing (the state and step stay), and the run of n
+    steps that follows replays its graph with the same result as an unprepared run."""
+    reps = SMALL[:5]
+    b = R.rflbm_batch_create(reps, storage=0, tile=0)
+    R.rflbm_batch_init_rest(b)
+    R.rflbm_batch_run(b, 2)
+    R.rflbm_batch_synchronize(b)
+    before = [_batch_pops(R, b, reps, r) for r in range(len(reps))]
+    R.rflbm_batch_prepare(b, 5)
+    R.rflbm_batch_synchronize(b)
+    for r in range(len(reps)):
+        assert np.array_equal(_batch_pops(R, b, reps, r), before[r]), r
+    assert R.rflbm_batch_stats(b, 0)[0].step == 2
+    R.rflbm_batch_run(b, 5)
+    R.rflbm_batch_synchronize(b)
+    for r, rep in enumerate(reps):
+        assert np.array_equal(_batch_pops(R, b, reps, r), _single(R, rep, 7, 0)), r
+    with pytest.raises(R.RflbmError) as e:
+        R.rflbm_batch_prepare(b, 0)
+    assert e.value.status == R.RFLBM_EINVAL
+    R.rflbm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_three_launch_groups_and_more_launches_than_chains(R, storage):
+    """140 replicas: three groups of up to 64, each with row tiles at two sizes and site
+    tiles (9 launches per step, more than the 8 launch-chain streams, so that some chains
+    carry two launches). Sampled replicas, the last one included, reproduce their
+    single-box runs bit for bit."""
+    edges = [8, 12, 16, 20, 24]
+    reps = [dict(nx=e, ny=e + (r % 3), nz=4 + r % 5, tau=0.55 + 0.01 * (r % 50), kT=1e-4 * (1 + r % 4),
+                 seed=100 + r) for r, e in enumerate(edges[r % 5] for r in range(140))]
+    b = R.rflbm_batch_create(reps, storage=storage, tile=0)
+    # per group: rows at 128 (edges 8, 16) and at 96 (float32: 12, 24) or 192 (16-bit: 24),
+    # sites at 128 (20, and 12 in 16-bit storage, whose rows are no whole 16-byte units)
+    assert R.rflbm_batch_launches_per_step(b) == 9
+    R.rflbm_batch_init_rest(b)
+    R.rflbm_batch_run(b, 4)
+    R.rflbm_batch_run(b, 3)
+    R.rflbm_batch_synchronize(b)
+    for r in list(range(0, 140, 9)) + [63, 64, 127, 128, 139]:
+        assert np.array_equal(_batch_pops(R, b, reps, r), _single(R, reps[r], 7, storage)), r
+    R.rflbm_batch_destroy(b)
+
+
 def test_tuning_and_errors(R):
     b = R.rflbm_batch_create(SMALL[:3], tile=0)
     tile, per_sm, tiles = R.rflbm_batch_tuning(b)
