@@ -381,9 +381,11 @@ int rflbm_slab_faces_ready(rflbm_t* h, void* stream);
  * slab's next work waits for it, and its state may be read and stepped again. */
 int rflbm_slab_exchange_done(rflbm_t* h, void* stream);
 /* The whole exchange for n slabs of one box on one device, given in z order (slab k + 1 is
- * above slab k, the last below the first): plain device-to-device copies on a stream of
- * the library that waits for every slab's boundary rows and overlaps their interior rows;
- * then every slab's next step waits for the copies. n = 1 makes one slab periodic in z. */
+ * above slab k, the last below the first): device-to-device copies (one 3-D copy per face
+ * while its plane pitch is within the device's maximum copy pitch, else one per plane row)
+ * on a stream of the library that waits for every slab's boundary rows and overlaps their
+ * interior rows; then every slab's next step waits for the copies. n = 1 makes one slab
+ * periodic in z. */
 int rflbm_slab_exchange(rflbm_t* const* slabs, int n);
 
 /* Global diagnostics of caller-owned populations that allocate nothing.

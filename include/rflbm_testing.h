@@ -24,6 +24,11 @@ extern "C" {
  * re-initialise it. */
 int rflbm_testing_expect_extra_bytes(rflbm_t* h, uint32_t bytes);
 
+/* rflbm_slab_exchange moves a face as one 3-D copy only while its plane pitch is at most
+ * `bytes` (and the device's maximum copy pitch); above it, one copy per plane row. The limit
+ * is process-wide; 0 restores the default (the device's maximum). bytes < 0: RFLBM_EINVAL. */
+int rflbm_testing_slab_copy_pitch_limit(int64_t bytes);
+
 /* Measurement of a design choice, not a production path: the back transform of Eq. 11,
  * f_i = w_i sum_k e_ki m_k / b_k (Table II modes, scaled moments M_k = m_k / b_k as input),
  * on its own, computed either as the step kernels compute it (method 0: sum-factorised

@@ -131,6 +131,7 @@ _sig = {
     "rflbm_structure_factor": (C.c_int, [_H, C.c_int, C.c_int, _P, _P]),
     "rflbm_shell_count": (C.c_int, [_H]),
     "rflbm_testing_expect_extra_bytes": (C.c_int, [_H, C.c_uint32]),
+    "rflbm_testing_slab_copy_pitch_limit": (C.c_int, [C.c_int64]),
     "rflbm_testing_backtransform": (C.c_int, [C.c_int, _P, C.c_int64, _P]),
     "rflbm_testing_backtransform_time": (C.c_int, [C.c_int, C.c_int64, C.c_int, C.POINTER(C.c_float)]),
     "rflbm_testing_noise_time": (C.c_int, [C.c_int64, C.POINTER(C.c_float)]),
@@ -340,6 +341,12 @@ def rflbm_testing_expect_extra_bytes(h, nbytes):
     arrive, so their bounded waits run out and the next synchronising call raises
     RFLBM_ETIMEOUT; 0 restores normal operation."""
     return _check(lib.rflbm_testing_expect_extra_bytes(h, int(nbytes)))
+
+
+def rflbm_testing_slab_copy_pitch_limit(nbytes):
+    """Testing hook (include/rflbm_testing.h): faces whose plane pitch exceeds nbytes move one
+    plane row per copy in rflbm_slab_exchange; 0 restores the default."""
+    return _check(lib.rflbm_testing_slab_copy_pitch_limit(int(nbytes)))
 
 
 def rflbm_testing_backtransform(method, m):

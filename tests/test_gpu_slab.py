@@ -125,6 +125,33 @@ def test_one_slab_is_periodic_through_its_own_faces(R):
     slab.close()
 
 
+@pytest.mark.parametrize("pattern", [0, 1])
+def test_face_copies_one_plane_row_at_a_time(R, pattern):
+    """The exchange's fallback for plane pitches beyond the copy pitch limit (one copy per
+    plane row instead of one 3-D copy per face) gives the same bits."""
+    shape, sizes = (64, 6, 12), (5, 6, 1)
+    f0 = _state(shape, seed=8)
+    kw = dict(tau=0.8, kT=1e-4, seed=3, pattern=pattern)
+    whole = R.Box(*shape, **kw)
+    R.rflbm_set_populations(whole.h, f0)
+    slabs = _split(shape, sizes, f0, R, **kw)
+    R.rflbm_testing_slab_copy_pitch_limit(1)
+    try:
+        for _ in range(5):
+            for b in slabs:
+                R.rflbm_step(b.h, 1)
+            R.rflbm_slab_exchange([b.h for b in slabs])
+    finally:
+        R.rflbm_testing_slab_copy_pitch_limit(0)
+    R.rflbm_step(whole.h, 5)
+    assert np.array_equal(_gather(slabs), whole.populations())
+    with pytest.raises(R.RflbmError):
+        R.rflbm_testing_slab_copy_pitch_limit(-1)
+    whole.close()
+    for b in slabs:
+        b.close()
+
+
 def test_thermal_start_is_keyed_by_the_global_site(R):
     shape = (32, 6, 10)
     whole = R.Box(*shape, tau=0.8, kT=1e-4, seed=6)
