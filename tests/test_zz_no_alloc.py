@@ -66,7 +66,7 @@ def test_noalloc_stats_match_handle_stats_on_two_calls(R):
 
 def test_noalloc_stats_leave_free_device_memory_unchanged(R):
     """The property the entry point exists for: after a first call, further calls do not
-    change the driver's count of free device memory (which also sees allocations made
+    change the CUDA driver's count of free device memory (which also sees allocations made
     outside PyTorch's caching allocator)."""
     import torch
     shape = (32, 32, 32)
