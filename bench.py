@@ -54,8 +54,9 @@ def parse_args():
                     help="one periodic box (default), the 64-replica ensemble of uneven sizes "
                          "advanced together (--storage applies), or the back transform of Eq. 11 "
                          "alone as float32 FMAs and as tensor-core MMA (a design measurement)")
-    ap.add_argument("--tile", type=int, choices=[0, 96, 128, 192, 256, 512], default=0,
-                    help="ensemble tile size for every replica (0: each replica its own, by row length)")
+    ap.add_argument("--tile", type=int, choices=[-1, 0, 96, 128, 192, 256, 512], default=0,
+                    help="ensemble tile size for every replica (0: each row length its own, autotuned; "
+                         "-1: by the order of preference, untimed)")
     ap.add_argument("--pattern", choices=["pingpong", "aa"], default="pingpong",
                     help="two population buffers (pull, ping-pong) or one updated in place (AA)")
     ap.add_argument("--init", choices=["rest", "taylor-green"], default="rest",
@@ -441,7 +442,7 @@ def ensemble_arm(args):
     kernels = " + ".join(kname.format(args.storage, t) for t in sorted(row_sites))
     site_share = {str(t): row_sites[t] / sites for t in sorted(row_sites)}
     stem = ("k_batch_step_" if args.storage == "f32" else "k_batch_rows_pair_") + args.storage + "_" + (
-        str(tile) if tile else "per_replica")
+        str(tile) if tile > 0 else "per_replica")
     if info.rank != 0:
         dist.finalize(info)
         return 0
@@ -455,7 +456,9 @@ def ensemble_arm(args):
         "storage_dtype": args.storage, "data": "synthetic",
         "config": {"workload": f"64-replica Reg-FLBM ensemble, edges 16-96, {STORAGE_NAME[args.storage]} "
                                "populations, rest start", "replicas": len(reps), "sites": sites,
-                   "tile": tile or "per replica", "row_tile_site_share": site_share,
+                   "tile": tile if tile > 0 else ("autotuned per row length" if tile == 0 else
+                                                  "per row length, untimed"),
+                   "row_tile_site_share": site_share,
                    "ctas_per_sm": per_sm, "tiles_per_step": tiles,
                    "parallelism": "replicas"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -716,7 +719,7 @@ def gb300_arm(args):
             sites_s = sites * k / (ev0.elapsed_time(ev1) * 1e-3)
             tile, per_sm, _ = R.rflbm_batch_tuning(bh)
             variants[name] = {"value": sites_s / 1e6, "unit": "MLUPS", "steps": k,
-                              "replicas": len(reps), "sites": sites, "tile": tile or "per replica",
+                              "replicas": len(reps), "sites": sites, "tile": "autotuned per row length",
                               "roofline_frac": bps * sites_s / 1e9 / peak_v, "bytes_per_site": bps}
             R.rflbm_batch_destroy(bh)
     box.close()

@@ -295,13 +295,16 @@ int rflbm_site_normals(uint64_t seed, int64_t step, uint32_t replica,
  * runs the Reg-FLBM step of a single box (Eq. 25, omega_g = 1, local rho in Eq. 10) with
  * Philox key = its seed and replica word 0, so it reproduces the run of
  * rflbm_create(nx, ny, nz, tau, kT, rho0, seed) in the same storage format bit for bit.
- * `tile` is the tile size in sites (96, 128, 192, 256 or 512) given to every replica, or 0:
+ * `tile` is the tile size in sites (96, 128, 192, 256 or 512) given to every replica; or -1:
  * each replica takes the first size that its row length divides in the order 128, 96, 192,
  * 256, 512 (float32) or 128, 192, 256, 512, 96 (16-bit storage), and tiles of 128 sites when
- * none does. A replica whose row length nx divides its tile size, is at most 256 and is a
- * whole number of 16-byte units takes tiles of tile / nx whole rows moved by TMA copies
- * (run by tile / 2 threads of two sites each in 16-bit storage); any other replica takes
- * tiles of `tile` consecutive sites, one thread each. A step is one launch per tile size and
+ * none does; or 0 (autotuned): the same, except that for each row length that takes row
+ * tiles the library times the replicas of that row length alone, a few steps at every size
+ * their rows divide, at creation, and keeps the fastest (the state is undefined until the
+ * initialisation call that must follow anyway). A replica whose row length nx divides its
+ * tile size, is at most 256 and is a whole number of 16-byte units takes tiles of tile / nx
+ * whole rows moved by TMA copies (run by tile / 2 threads of two sites each in 16-bit
+ * storage); any other replica takes tiles of `tile` consecutive sites, one thread each. A step is one launch per tile size and
  * kind of tile in use (per group of 64 replicas). A bounded wait for a copy that expires makes
  * the call report RFLBM_ETIMEOUT. The library allocates and owns all device memory. */
 typedef struct rflbm_batch rflbm_batch_t;
@@ -313,7 +316,7 @@ typedef struct {
 rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho0, int storage,
                                   int tile);
 void rflbm_batch_destroy(rflbm_batch_t* b);
-/* The tile size requested at creation (0: per replica), the resident CTAs per SM of the
+/* The tile size requested at creation (0 or -1: per replica), the resident CTAs per SM of the
  * kernel that updates the most sites, and the tiles per step. */
 int rflbm_batch_tuning(const rflbm_batch_t* b, int* tile, int* ctas_per_sm, int64_t* tiles_per_step);
 /* Tile size of replica r and its rows per tile (0: tiles of consecutive sites); either

@@ -499,7 +499,7 @@ struct rflbm_batch {
   int* tile_rep = nullptr;             // per global tile: its replica's index within its group
   CUtensorMap* maps = nullptr;  // 4 per replica (rows tiles), device memory
   int64_t tiles = 0;
-  int tile = 0;  // requested tile size (0: per replica)
+  int tile = 0;  // requested tile size (0: autotuned per row length, -1: by the order of preference)
   int ctas_per_sm = 1;
   unsigned long long* run = nullptr;  // device: first step of the current run, its buffer
   int* err = nullptr;
@@ -555,36 +555,38 @@ int ensure_chains(rflbm_batch* b) {
   return RFLBM_OK;
 }
 
-// Tile size of a replica: `tile` when given, else the first size of the storage format's
+// A replica whose rows can move as TMA row tiles: a row of whole 16-byte units, at most
+// 256 sites (the TMA box limit).
+bool rows_eligible(const rflbm_batch* b, const Geometry& g) {
+  return (g.nx * storage_bytes(b->storage)) % 16 == 0 && g.nx <= 256;
+}
+
+// Tile size of a replica: `tile` when positive, else the first size of the storage format's
 // order of preference that takes the replica's rows (sites tiles of kAutoSitesTile when none).
 int replica_tile(const rflbm_batch* b, const Geometry& g, int tile) {
-  if (tile) return tile;
-  const size_t elem = storage_bytes(b->storage);
+  if (tile > 0) return tile;
   const int* pref = b->storage == kStoreF32 ? kPrefF32 : kPref16;
-  if ((g.nx * elem) % 16 == 0 && g.nx <= 256)
+  if (rows_eligible(b, g))
     for (int k = 0; k < kNumTiles; ++k)
       if (pref[k] % (int)g.nx == 0) return pref[k];
   return kAutoSitesTile;
 }
 
 // Builds the per-replica descriptors, their tensor maps, the launches of a step and the
-// tile map, every replica at tile size `tile` (0: each at its own, see replica_tile). A
-// replica takes rows tiles when its row is a whole number of 16-byte units, divides its
-// tile, fits the TMA box limit (256), and its maps encode; else sites tiles.
-int layout_tiles(rflbm_batch* b, int tile) {
-  const size_t elem = storage_bytes(b->storage);
+// tile map, replica r at tile size tile_of[r]. A replica takes rows tiles when its rows are
+// eligible (rows_eligible), divide its tile, and its maps encode; else sites tiles.
+int layout_replicas(rflbm_batch* b, const std::vector<int>& tile_of) {
   std::vector<CUtensorMap> maps((size_t)b->n * 4);
   if (!b->maps) BCUDA(cudaMalloc((void**)&b->maps, sizeof(CUtensorMap) * maps.size()), "allocating tensor maps");
-  b->rep_tile.assign((size_t)b->n, 0);
+  b->rep_tile = tile_of;
   for (int r = 0; r < b->n; ++r) {
     ReplicaDev& d = b->host[r];
     const Geometry& g = d.geo;
-    const int t = replica_tile(b, g, tile);
-    b->rep_tile[(size_t)r] = t;
+    const int t = tile_of[(size_t)r];
     d.rows = 0;
     d.yblocks = 0;
     d.maps = nullptr;
-    if ((g.nx * elem) % 16 == 0 && t % g.nx == 0 && g.nx <= 256) {
+    if (rows_eligible(b, g) && t % g.nx == 0) {
       const uint32_t R = (uint32_t)t / g.nx;
       bool ok = true;
       for (int k = 0; k < 2 && ok; ++k)
@@ -630,13 +632,14 @@ int layout_tiles(rflbm_batch* b, int tile) {
   for (int r = 0; r < b->n; ++r) b->tables[(size_t)(r / kGroupReps)].r[r % kGroupReps] = b->host[r];
   cudaFree(b->tile_rep);
   b->tile_rep = nullptr;
-  BCUDA(cudaMalloc(&b->tile_rep, sizeof(int) * (size_t)tiles), "allocating the tile map");
-  BCUDA(cudaMemcpy(b->tile_rep, map.data(), sizeof(int) * (size_t)tiles, cudaMemcpyHostToDevice), "uploading the tile map");
+  BCUDA(cudaMalloc(&b->tile_rep, sizeof(int) * (size_t)std::max<int64_t>(tiles, 1)), "allocating the tile map");
+  if (tiles > 0)
+    BCUDA(cudaMemcpy(b->tile_rep, map.data(), sizeof(int) * (size_t)tiles, cudaMemcpyHostToDevice),
+          "uploading the tile map");
   for (const BatchLaunch& L : b->launches)
     if (L.rows) BCUDA(batch_prepare(b->storage, L.tile), "setting the shared-memory size of the batched step kernel");
   if (int e = ensure_chains(b)) return e;
   b->tiles = tiles;
-  b->tile = tile;
   // occupancy of the kernel that updates the most sites
   size_t top = 0;
   for (size_t k = 1; k < sites_at.size(); ++k)
@@ -652,6 +655,101 @@ int layout_tiles(rflbm_batch* b, int tile) {
   }
   b->graph_steps = -1;
   return RFLBM_OK;
+}
+
+int enqueue_run(rflbm_batch* b, int64_t nsteps, cudaStream_t st);
+int bsync(rflbm_batch* b, const char* what);
+
+// Autotuner of tile 0. Every replica starts at its size from the order of preference; then,
+// per row length (largest share of the sites first), the step of the whole ensemble is timed
+// with the replicas of that row length at every tile size their rows divide, the other
+// replicas at their current sizes, from a rest state: after one warm-up step, the shorter of
+// two timings of enough steps for about kTuneSites site updates (at least 3, at most 64).
+// Candidates come in the storage format's order of preference, and a later one replaces the
+// best so far only when the whole step is more than 2 % faster. (Timed alone, a small class
+// of replicas is launch-bound and prefers large tiles; in the ensemble the extra tile size
+// is one more launch per step and costs more than it saves.) The populations it leaves are
+// undefined until the initialisation call that must follow.
+constexpr double kTuneSites = 2e7;
+int autotune_tiles(rflbm_batch* b, std::vector<int>& tile_of) {
+  for (int r = 0; r < b->n; ++r) tile_of[(size_t)r] = replica_tile(b, b->host[r].geo, -1);
+  std::vector<std::pair<double, uint32_t>> classes;  // (sites, row length)
+  double total = 0.0;
+  for (int r = 0; r < b->n; ++r) {
+    const Geometry& g = b->host[r].geo;
+    total += g.n;
+    if (!rows_eligible(b, g)) continue;
+    auto it = std::find_if(classes.begin(), classes.end(), [&](const auto& c) { return c.second == g.nx; });
+    if (it == classes.end()) classes.push_back({(double)g.n, g.nx});
+    else it->first += g.n;
+  }
+  std::sort(classes.begin(), classes.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
+  const int64_t steps = std::min<int64_t>(64, std::max<int64_t>(3, (int64_t)(kTuneSites / total)));
+  for (auto& d : b->host)
+    for (int k = 0; k < 2; ++k)
+      BCUDA(cudaMemsetAsync(d.buf[k], 0, (size_t)d.geo.ps * kQ * storage_bytes(b->storage), b->stream),
+            "clearing replica populations");
+  const unsigned long long r0[2] = {0ull, 0ull};
+  BCUDA(cudaMemcpyAsync(b->run, r0, sizeof(r0), cudaMemcpyHostToDevice, b->stream), "setting the step index");
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  BCUDA(cudaEventCreate(&t0), "creating the autotuner's events");
+  cudaError_t ce = cudaEventCreate(&t1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(t0);
+    return bcuda(ce, "creating the autotuner's events");
+  }
+  const int* pref = b->storage == kStoreF32 ? kPrefF32 : kPref16;
+  int rc = RFLBM_OK;
+  for (const auto& cls : classes) {
+    const uint32_t nx = cls.second;
+    std::vector<char> in_class((size_t)b->n, 0);
+    for (int r = 0; r < b->n; ++r) in_class[(size_t)r] = b->host[r].geo.nx == nx && rows_eligible(b, b->host[r].geo);
+    float best = 0.0f;
+    int best_t = 0;
+    for (int k = 0; k < kNumTiles && rc == RFLBM_OK; ++k) {
+      const int t = pref[k];
+      if (t % (int)nx) continue;
+      for (int r = 0; r < b->n; ++r)
+        if (in_class[(size_t)r]) tile_of[(size_t)r] = t;
+      rc = layout_replicas(b, tile_of);
+      if (rc == RFLBM_OK) rc = enqueue_run(b, 1, b->stream);  // warm-up
+      float ms = 0.0f;
+      for (int rep = 0; rep < 2 && rc == RFLBM_OK; ++rep) {
+        ce = cudaEventRecord(t0, b->stream);
+        if (ce == cudaSuccess) rc = enqueue_run(b, steps, b->stream);
+        if (rc == RFLBM_OK && ce == cudaSuccess) ce = cudaEventRecord(t1, b->stream);
+        if (rc == RFLBM_OK && ce == cudaSuccess) ce = cudaEventSynchronize(t1);
+        float m = 0.0f;
+        if (rc == RFLBM_OK && ce == cudaSuccess) ce = cudaEventElapsedTime(&m, t0, t1);
+        if (rc == RFLBM_OK && ce != cudaSuccess) rc = bcuda(ce, "timing a tile size");
+        if (rep == 0 || m < ms) ms = m;
+      }
+      if (rc == RFLBM_OK && (best_t == 0 || ms < 0.98f * best)) {
+        best = ms;
+        best_t = t;
+      }
+    }
+    if (rc != RFLBM_OK) break;
+    for (int r = 0; r < b->n; ++r)  // (no size divides the row: the replicas keep site tiles)
+      if (in_class[(size_t)r]) tile_of[(size_t)r] = best_t ? best_t : replica_tile(b, b->host[r].geo, -1);
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  return rc;
+}
+
+// The layout of tile request `tile`: every replica at `tile` (> 0), at its size from the
+// order of preference (-1), or autotuned (0).
+int layout_tiles(rflbm_batch* b, int tile) {
+  std::vector<int> tile_of((size_t)b->n);
+  if (tile == 0) {
+    if (int e = autotune_tiles(b, tile_of)) return e;
+  } else {
+    for (int r = 0; r < b->n; ++r) tile_of[(size_t)r] = replica_tile(b, b->host[r].geo, tile);
+  }
+  if (int e = layout_replicas(b, tile_of)) return e;
+  b->tile = tile;
+  return tile == 0 ? bsync(b, "autotuning the batch") : RFLBM_OK;
 }
 
 // The launch sequence of one run on stream st: a single launch per step chains on st
@@ -739,7 +837,7 @@ rflbm_batch_t* rflbm_batch_create(const rflbm_replica_t* reps, int n, double rho
     return nullptr;
   }
   if (!(rho0 > 0.0) || (storage != RFLBM_STORE_F32 && storage != RFLBM_STORE_F16 && storage != RFLBM_STORE_BF16) ||
-      (tile != 0 && tile_index(tile) < 0)) {
+      (tile != 0 && tile != -1 && tile_index(tile) < 0)) {
     bfail(RFLBM_EINVAL, "rflbm_batch_create: invalid rho0, storage or tile");
     return nullptr;
   }

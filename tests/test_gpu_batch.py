@@ -77,10 +77,11 @@ PER_REPLICA = {0: [(128, 8), (96, 4), (128, 4), (128, 0), (128, 2), (128, 0), (1
 
 @pytest.mark.parametrize("storage", [0, 1, 2])
 def test_per_replica_tiles_reproduce_single_box_runs(R, storage):
-    """tile 0: every replica at the tile size its row length and storage select; the step
-    runs one launch per size and kind (rows at 128 and at 96 or 192, sites at 128)."""
-    b = R.rflbm_batch_create(SMALL, storage=storage, tile=0)
-    assert R.rflbm_batch_tuning(b)[0] == 0
+    """tile -1: every replica at the tile size its row length and storage select in the order
+    of preference; the step runs one launch per size and kind (rows at 128 and at 96 or 192,
+    sites at 128)."""
+    b = R.rflbm_batch_create(SMALL, storage=storage, tile=-1)
+    assert R.rflbm_batch_tuning(b)[0] == -1
     assert [R.rflbm_batch_replica_tiling(b, r) for r in range(len(SMALL))] == PER_REPLICA[min(storage, 1)]
     assert R.rflbm_batch_launches_per_step(b) == 3
     R.rflbm_batch_init_rest(b)
@@ -89,6 +90,31 @@ def test_per_replica_tiles_reproduce_single_box_runs(R, storage):
     R.rflbm_batch_synchronize(b)
     for r, rep in enumerate(SMALL):
         assert np.array_equal(_batch_pops(R, b, SMALL, r), _single(R, rep, 10, storage)), r
+    R.rflbm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_autotuned_tiles_are_valid_and_reproduce_single_box_runs(R, storage):
+    """tile 0: the autotuner gives every replica of one row length the same size, one that
+    its rows divide where they take row tiles (site tiles of 128 elsewhere), and the run
+    reproduces the single-box runs bit for bit."""
+    b = R.rflbm_batch_create(SMALL, storage=storage, tile=0)
+    assert R.rflbm_batch_tuning(b)[0] == 0
+    by_length = {}
+    for r, rep in enumerate(SMALL):
+        tile, rows = R.rflbm_batch_replica_tiling(b, r)
+        assert tile in (96, 128, 192, 256, 512)
+        if rows:
+            assert tile % rep["nx"] == 0 and rows == tile // rep["nx"]
+            assert by_length.setdefault(rep["nx"], tile) == tile
+        else:
+            assert tile == 128 and PER_REPLICA[min(storage, 1)][r][1] == 0
+    R.rflbm_batch_init_rest(b)
+    for n in (3, 4):
+        R.rflbm_batch_run(b, n)
+    R.rflbm_batch_synchronize(b)
+    for r, rep in enumerate(SMALL):
+        assert np.array_equal(_batch_pops(R, b, SMALL, r), _single(R, rep, 7, storage)), r
     R.rflbm_batch_destroy(b)
 
 
@@ -125,7 +151,7 @@ def test_three_launch_groups_and_more_launches_than_chains(R, storage):
     edges = [8, 12, 16, 20, 24]
     reps = [dict(nx=e, ny=e + (r % 3), nz=4 + r % 5, tau=0.55 + 0.01 * (r % 50), kT=1e-4 * (1 + r % 4),
                  seed=100 + r) for r, e in enumerate(edges[r % 5] for r in range(140))]
-    b = R.rflbm_batch_create(reps, storage=storage, tile=0)
+    b = R.rflbm_batch_create(reps, storage=storage, tile=-1)
     # per group: rows at 128 (edges 8, 16) and at 96 (float32: 12, 24) or 192 (16-bit: 24),
     # sites at 128 (20, and 12 in 16-bit storage, whose rows are no whole 16-byte units)
     assert R.rflbm_batch_launches_per_step(b) == 9
@@ -142,7 +168,7 @@ def test_tuning_and_errors(R):
     b = R.rflbm_batch_create(SMALL[:3], tile=0)
     tile, per_sm, tiles = R.rflbm_batch_tuning(b)
     assert tile == 0 and per_sm >= 1 and tiles > 0
-    assert R.rflbm_batch_launches_per_step(b) == 2  # rows at 128 (nx 16, 32) and at 96 (nx 24)
+    assert 1 <= R.rflbm_batch_launches_per_step(b) <= 3  # row tiles at up to three sizes
     with pytest.raises(R.RflbmError) as e:
         R.rflbm_batch_replica_tiling(b, 3)
     assert e.value.status == R.RFLBM_EINVAL
@@ -152,6 +178,9 @@ def test_tuning_and_errors(R):
     R.rflbm_batch_destroy(b)
     with pytest.raises(R.RflbmError):
         R.rflbm_batch_create([dict(nx=8, ny=8, nz=8, tau=0.4, kT=0.0, seed=1)])
+    for bad in (-2, 64, 100):
+        with pytest.raises(R.RflbmError):
+            R.rflbm_batch_create(SMALL[:1], tile=bad)
 
 
 @pytest.mark.parametrize("storage", [0, 1])
