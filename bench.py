@@ -534,15 +534,19 @@ def storage_accuracy(R, torch, stream, edge=128, steps=20, tau=0.8, kT=1e-4):
     state (rflbm_init_thermal draws it identically in every format), `steps` steps of each
     format; rho, u and Pi of every site against the float32 run, as RMS and maximum in units
     of each field's thermal standard deviation (float32 itself is within 2.2e-7 RMS of the
-    FP64 oracle in the parity tests), and the largest deviation of the 27 per-site mode
-    variances from the fluctuation-dissipation value rho0 kT b_k / cs2 (Sec. II.A)."""
+    FP64 oracle in the parity tests), the largest deviation of the 27 per-site mode
+    variances from the fluctuation-dissipation value rho0 kT b_k / cs2 (Sec. II.A), and the
+    static structure factors S(k) of rho, rho u and Pi (shell bands 4-8, 8-16, 16-32 of
+    |k| L / 2 pi): their largest deviation from the flat values of Sec. III (rho0 kT / cs2
+    for rho, rho0 kT for rho u, 2 rho0 kT cs2 and rho0 kT cs2 for the diagonal and
+    off-diagonal Pi), and of each 16-bit format's bands from float32's."""
     import numpy as np
     n = edge ** 3
     dev = torch.device("cuda", torch.cuda.current_device())
     cs2 = 1.0 / 3.0
     # thermal standard deviations of rho, u_a, Pi_aa, Pi_ab at rho0 = 1
     sd = [np.sqrt(kT / cs2)] + [np.sqrt(kT)] * 3 + [np.sqrt(2 * kT * cs2)] * 3 + [np.sqrt(kT * cs2)] * 3
-    fields, out = {}, {}
+    fields, out, sk_bands = {}, {}, {}
     for name, st in (("f32", R.RFLBM_STORE_F32), ("f16", R.RFLBM_STORE_F16), ("bf16", R.RFLBM_STORE_BF16)):
         box = R.Box(edge, edge, edge, tau=tau, kT=kT, seed=1, stream=stream.cuda_stream, storage=st)
         R.rflbm_init_thermal(box.h)
@@ -552,12 +556,26 @@ def storage_accuracy(R, torch, stream, edge=128, steps=20, tau=0.8, kT=1e-4):
         pi = torch.empty((6, n), dtype=torch.float64, device=dev)
         R.rflbm_moments(box.h, rho, u, pi)
         s1, s2 = R.rflbm_mode_sums(box.h)
+        ns = R.rflbm_shell_count(box.h)
+        bands, band_sd = [], None
+        for f in range(10):
+            sk, count = R.rflbm_structure_factor(box.h, f, ns)
+            bands.append([sk[lo:hi].sum() / count[lo:hi].sum() for lo, hi in ((4, 8), (8, 16), (16, 33))])
+            # one snapshot: S of a real Gaussian field is exponential on half of the vectors
+            band_sd = [float(np.sqrt(2.0 / count[lo:hi].sum())) for lo, hi in ((4, 8), (8, 16), (16, 33))]
         box.close()
+        bands = np.array(bands)
         var = s2 / n - (s1 / n) ** 2
         ratio = var / (kT * mode_norms() / cs2)
         fields[name] = torch.cat([rho[None], u, pi])
+        s_theory = np.array([kT / cs2] + [kT] * 3 + [2 * kT * cs2] * 3 + [kT * cs2] * 3)
+        sk_bands[name] = bands
         entry = {"fdt_mode_variance_max_dev": float(np.max(np.abs(ratio - 1.0))),
-                 "fdt_mode_variance_mean": float(np.mean(ratio))}
+                 "fdt_mode_variance_mean": float(np.mean(ratio)),
+                 "sk_max_dev_from_theory": float(np.max(np.abs(bands / s_theory[:, None] - 1.0))),
+                 "sk_band_sampling_rel_sd": band_sd}
+        if name != "f32":
+            entry["sk_max_rel_diff_vs_f32"] = float(np.max(np.abs(bands / sk_bands["f32"] - 1.0)))
         if name != "f32":
             d = (fields[name] - fields["f32"]).abs() / torch.tensor(sd, dtype=torch.float64, device=dev)[:, None]
             entry["vs_f32_rms_in_thermal_sd"] = float(torch.sqrt((d * d).mean()))
@@ -567,7 +585,7 @@ def storage_accuracy(R, torch, stream, edge=128, steps=20, tau=0.8, kT=1e-4):
     del fields
     torch.cuda.empty_cache()
     return {"workload": f"{edge}^3 thermal initial state, tau {tau}, kT {kT:g}, {steps} steps, seed 1",
-            "fields": "rho, u, Pi per site", **out}
+            "fields": "rho, u, Pi per site; S(k) of rho, rho u, Pi in shell bands 4-8, 8-16, 16-32", **out}
 
 
 def mode_norms():
