@@ -428,7 +428,7 @@ static int tile_index(int tile) {
 }
 
 #define RFLBM_BATCH_DISPATCH(storage, tile, CALL)               \
-  switch ((storage) * kNumTiles + tile_index(tile)) {           \
+  switch (tile_index(tile) < 0 ? -1 : (storage) * kNumTiles + tile_index(tile)) { \
     case 0: { constexpr int S = kStoreF32, T = 96; CALL; }      \
     case 1: { constexpr int S = kStoreF32, T = 128; CALL; }     \
     case 2: { constexpr int S = kStoreF32, T = 192; CALL; }     \
