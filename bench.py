@@ -797,6 +797,13 @@ def backtransform_arm(args):
         R.rflbm_testing_backtransform_time(method, tiles, reps)
         ms = min(R.rflbm_testing_backtransform_time(method, tiles, reps) for _ in range(3))
         out[name] = {"ms": ms, "value": tiles * 128 * reps / (ms * 1e-3) / 1e9}
+    # the forward projection (the ten moments of order <= 2) alone, FMA vs float16 MMA
+    out["forward"] = {"workload": f"{tiles} tiles of 128 sites x {reps} projections each, float16 populations "
+                                  "in registers", "unit": "G site projections/s"}
+    for name, method in (("fma", 0), ("mma", 1)):
+        R.rflbm_testing_forward_time(method, tiles, reps)
+        ms = min(R.rflbm_testing_forward_time(method, tiles, reps) for _ in range(3))
+        out["forward"][name] = {"ms": ms, "value": tiles * 128 * reps / (ms * 1e-3) / 1e9}
     # the noise draw of a step alone, against the sites per second of the 16-bit roofline
     nsites = 1 << 27
     R.rflbm_testing_noise_time(nsites)

@@ -46,6 +46,24 @@ int rflbm_testing_slab_copy_pitch_limit(int64_t bytes);
 int rflbm_testing_backtransform(int method, const float* m, int64_t n, float* f);
 int rflbm_testing_backtransform_time(int method, int64_t tiles, int reps, float* ms);
 
+/* Measurement of a design choice, not a production path: the forward projection of Eq. 5 for
+ * the moments the step uses (order <= 2), on its own, as the ten raw moments
+ * m_k = sum_i f_i c_x^p c_y^q c_z^r in the order 1, c_x, c_y, c_z, c_x^2, c_y^2, c_z^2, c_x c_y,
+ * c_x c_z, c_y c_z, computed either as the step kernels compute them (method 0: sum-factorised
+ * float32 FMAs) or on the tensor cores (method 1: one tcgen05 MMA tile of 128 sites x 16 moments
+ * x 32 populations per CTA with float16 operands, float32 accumulator in tensor memory: exact
+ * for populations that are float16 values, as 16-bit storage gives them).
+ * rflbm_testing_forward: f holds 27 planes of n populations (host, element [i n + s],
+ *   i = 9 (c_x + 1) + 3 (c_y + 1) + c_z + 1; method 1 rounds them to float16), m receives 10
+ *   planes of n moments (host). n must be a positive multiple of 128. Synchronous; allocates
+ *   device memory.
+ * rflbm_testing_forward_time: *ms receives the time of one launch over `tiles` tiles of 128
+ *   sites, each site projecting `reps` sets of synthetic float16 populations held in registers
+ *   (one untimed launch first). Synchronous; allocates device memory.
+ * A bounded wait for the MMA that expires returns RFLBM_ETIMEOUT. */
+int rflbm_testing_forward(int method, const float* f, int64_t n, float* m);
+int rflbm_testing_forward_time(int method, int64_t tiles, int reps, float* ms);
+
 /* Measurement of the noise draw of a step alone (the r_k of Eq. 9 by the generator stated in
  * rflbm.h: 6 Philox4x32-10 calls and 12 Box-Muller pairs per site), two sites per thread as in
  * the 16-bit step kernels, with nothing else done: *ms receives the time of one launch over

@@ -13,10 +13,20 @@
 // K chunk accumulate both), which keeps about 16 significant bits of M. The threads then read
 // their rows back from tensor memory and apply the weights w_i.
 //
+// The forward projection (Eq. 5) of the moments the step needs, order <= 2, on its own, in the
+// same two forms, with the operands the 16-bit storage formats give exactly: the ten raw
+// moments m_pqr = sum_i f_i c_x^p c_y^q c_z^r (p + q + r <= 2) of float16 populations. FMA
+// form: the step kernels' sum-factorised sweeps (moments_order2 of collide.cuh), in float32.
+// MMA form: D[site][k] = sum_i A[site][i] B[k][i] on one tcgen05 kind::f16 tile of M = 128
+// sites x N = 16 moments (10 used), K = 32 populations (27 used), float16 operands: A holds the
+// populations (exact: they are float16 values), B the products c_x^p c_y^q c_z^r in {-1, 0, 1};
+// the float32 accumulator in tensor memory, no split needed.
+//
 // Both operands sit in shared memory in the canonical K-major layout without swizzling:
 // element (row, k) at byte (row % 8) 16 + (row / 8) 512 + (k % 8) 2 + (k / 8) 128, i.e. core
 // matrices of 8 rows x 16 bytes, 128 bytes apart along K and 512 bytes apart along the rows.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -180,6 +190,140 @@ __global__ void __launch_bounds__(128) k_noise_only(uint32_t nsites, uint32_t st
   out[tid] = acc;
 }
 
+// ---- forward projection: the ten raw moments of order <= 2, in the order of fw_exps
+constexpr int kFwN = 16;  // moments, padded: the MMA's N
+__host__ __device__ constexpr int fw_exp(int k, int axis) {
+  // (p, q, r) of moment k: 1, c_x, c_y, c_z, c_x^2, c_y^2, c_z^2, c_x c_y, c_x c_z, c_y c_z
+  return k == 0 ? 0
+       : k <= 3 ? (axis == k - 1)
+       : k <= 6 ? 2 * (axis == k - 4)
+       : k == 7 ? (axis == 0 || axis == 1)
+       : k == 8 ? (axis == 0 || axis == 2)
+                : (axis == 1 || axis == 2);
+}
+__host__ __device__ constexpr int ipow(int c, int p) { return p == 0 ? 1 : (p == 1 ? c : c * c); }
+
+// The populations of a site as float16 values: loaded, or synthetic values for timing.
+template <bool kSynth>
+__device__ __forceinline__ void site_pops_in(const float* f, int64_t n, int64_t site, float (&g)[27]) {
+#pragma unroll
+  for (int i = 0; i < 27; ++i)
+    g[i] = kSynth ? __half2float(__float2half_rn(
+                        1e-3f * (float)(((uint32_t)site * 2654435761u + 40503u * (uint32_t)i) >> 20) - 2.0f))
+                  : f[(int64_t)i * n + site];
+}
+
+template <bool kSynth>
+__global__ void __launch_bounds__(kBtTile) k_fw_fma(const float* __restrict__ f, int64_t n, int reps,
+                                                    float* __restrict__ out) {
+  const int64_t site = (int64_t)blockIdx.x * kBtTile + threadIdx.x;
+  float gv[27];
+  site_pops_in<kSynth>(f, n, site, gv);
+  float acc[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
+  for (int rep = 0; rep < reps; ++rep) {
+    float G[3][3][3];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) G[i / 9][(i / 3) % 3][i % 3] = kSynth ? gv[i] + 1e-4f * (float)rep : gv[i];
+    float drho, jx, jy, jz, sxy, sxz, syz, axx, ayy, azz;
+    moments_order2(G, drho, jx, jy, jz, sxy, sxz, syz, axx, ayy, azz);
+    const float third = drho * (1.0f / 3.0f);  // raw diagonal moments from the Hermite ones
+    const float m[10] = {drho, jx, jy, jz, axx + third, ayy + third, azz + third, sxy, sxz, syz};
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] += m[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 10; ++k) out[(int64_t)k * n + site] = acc[k];
+}
+
+// D = A B with float16 operands (kind::f16, A and B of one type), float32 accumulator
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int m, int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+template <bool kSynth>
+__global__ void __launch_bounds__(kBtTile) k_fw_mma(const float* __restrict__ f, int64_t n, int reps,
+                                                    float* __restrict__ out, int* err) {
+  __shared__ __align__(1024) __half sA[kBtTile * kBtK];
+  __shared__ __align__(1024) __half sB[kFwN * kBtK];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int64_t site = (int64_t)blockIdx.x * kBtTile + t;
+
+  for (int e = t; e < kFwN * kBtK; e += kBtTile) {
+    const int k = e / kBtK, i = e % kBtK;
+    const int cx = i / 9 - 1, cy = (i / 3) % 3 - 1, cz = i % 3 - 1;
+    const int v = (k < 10 && i < 27) ? ipow(cx, fw_exp(k, 0)) * ipow(cy, fw_exp(k, 1)) * ipow(cz, fw_exp(k, 2)) : 0;
+    sB[canon(k, i)] = __float2half_rn((float)v);
+  }
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 32);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  float gv[27];
+  site_pops_in<kSynth>(f, n, site, gv);
+  float acc[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) acc[k] = 0.0f;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int rep = 0; rep < reps && ok; ++rep) {
+    // this site's row of A: its 27 populations as float16, 8 per 16-byte store
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __align__(16) __half2 h[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i0 = 8 * j + 2 * q;
+        const float a = i0 < 27 ? (kSynth ? gv[i0] + 1e-4f * (float)rep : gv[i0]) : 0.0f;
+        const float b = i0 + 1 < 27 ? (kSynth ? gv[i0 + 1] + 1e-4f * (float)rep : gv[i0 + 1]) : 0.0f;
+        h[q] = __floats2half2_rn(a, b);
+      }
+      *reinterpret_cast<uint4*>(&sA[canon(t, 8 * j)]) = *reinterpret_cast<const uint4*>(h);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after_sync();
+      constexpr uint32_t idesc = idesc_f16_f32(kBtTile, kFwN);
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        tc_mma_bf16(tmem, smem_desc_noswizzle(smem_addr(&sA[0]) + 256u * s, 128u, 512u),
+                    smem_desc_noswizzle(smem_addr(&sB[0]) + 256u * s, 128u, 512u), idesc, s != 0);
+      tc_commit(&bar);
+    }
+    ok = mbar_wait_bounded(&bar, phase, kBtPolls);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) atomicOr(err, 1);
+      mbar_wait_bounded(&bar, phase ^ 1u, kBtPolls);
+      ok = false;
+      break;
+    }
+    tc_fence_after_sync();
+    float D[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), D);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] += D[k];
+    tc_fence_before_sync();
+    __syncthreads();
+  }
+  if (ok) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) out[(int64_t)k * n + site] = acc[k];
+  }
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 32);
+}
+
 int bt_fail(int code, const char* msg, cudaError_t e = cudaSuccess) {
   return record_error(code, msg, e == cudaSuccess ? nullptr : cudaGetErrorString(e));
 }
@@ -246,6 +390,65 @@ extern "C" int rflbm_testing_backtransform_time(int method, int64_t tiles, int r
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return bt_fail(RFLBM_ECUDA, "rflbm_testing_backtransform_time", e);
   if (err) return bt_fail(RFLBM_ETIMEOUT, "rflbm_testing_backtransform_time: a bounded wait for the MMA expired");
+  return RFLBM_OK;
+}
+
+extern "C" int rflbm_testing_forward(int method, const float* f, int64_t n, float* m) {
+  if ((method != 0 && method != 1) || !f || !m || n < kBtTile || n % kBtTile)
+    return bt_fail(RFLBM_EINVAL, "rflbm_testing_forward: method 0 or 1, n a positive multiple of 128");
+  float *df = nullptr, *dm = nullptr;
+  int* derr = nullptr;
+  cudaError_t e = cudaMalloc(&df, sizeof(float) * 27 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&dm, sizeof(float) * 10 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&derr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(df, f, sizeof(float) * 27 * (size_t)n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const unsigned blocks = (unsigned)(n / kBtTile);
+    if (method == 0) k_fw_fma<false><<<blocks, kBtTile>>>(df, n, 1, dm);
+    else k_fw_mma<false><<<blocks, kBtTile>>>(df, n, 1, dm, derr);
+    e = cudaGetLastError();
+  }
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(m, dm, sizeof(float) * 10 * (size_t)n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&err, derr, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(df);
+  cudaFree(dm);
+  cudaFree(derr);
+  if (e != cudaSuccess) return bt_fail(RFLBM_ECUDA, "rflbm_testing_forward", e);
+  if (err) return bt_fail(RFLBM_ETIMEOUT, "rflbm_testing_forward: a bounded wait for the MMA expired");
+  return RFLBM_OK;
+}
+
+extern "C" int rflbm_testing_forward_time(int method, int64_t tiles, int reps, float* ms) {
+  if ((method != 0 && method != 1) || tiles < 1 || reps < 1 || !ms)
+    return bt_fail(RFLBM_EINVAL, "rflbm_testing_forward_time: invalid arguments");
+  const int64_t n = tiles * kBtTile;
+  float* dout = nullptr;
+  int* derr = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&dout, sizeof(float) * 10 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&derr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {  // warm-up, then timed
+    if (pass == 1) e = cudaEventRecord(e0);
+    if (method == 0) k_fw_fma<true><<<(unsigned)tiles, kBtTile>>>(nullptr, n, reps, dout);
+    else k_fw_mma<true><<<(unsigned)tiles, kBtTile>>>(nullptr, n, reps, dout, derr);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (pass == 1 && e == cudaSuccess) e = cudaEventRecord(e1);
+  }
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&err, derr, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(dout);
+  cudaFree(derr);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return bt_fail(RFLBM_ECUDA, "rflbm_testing_forward_time", e);
+  if (err) return bt_fail(RFLBM_ETIMEOUT, "rflbm_testing_forward_time: a bounded wait for the MMA expired");
   return RFLBM_OK;
 }
 

@@ -134,6 +134,8 @@ _sig = {
     "rflbm_testing_slab_copy_pitch_limit": (C.c_int, [C.c_int64]),
     "rflbm_testing_backtransform": (C.c_int, [C.c_int, _P, C.c_int64, _P]),
     "rflbm_testing_backtransform_time": (C.c_int, [C.c_int, C.c_int64, C.c_int, C.POINTER(C.c_float)]),
+    "rflbm_testing_forward": (C.c_int, [C.c_int, _P, C.c_int64, _P]),
+    "rflbm_testing_forward_time": (C.c_int, [C.c_int, C.c_int64, C.c_int, C.POINTER(C.c_float)]),
     "rflbm_testing_noise_time": (C.c_int, [C.c_int64, C.POINTER(C.c_float)]),
     "rflbm_slab_faces": (C.c_int, [_H] + [C.POINTER(rflbm_face_t)] * 4),
     "rflbm_slab_faces_ready": (C.c_int, [_H, _P]),
@@ -364,6 +366,24 @@ def rflbm_testing_backtransform_time(method, tiles, reps):
     transforms per site."""
     ms = C.c_float()
     _check(lib.rflbm_testing_backtransform_time(int(method), int(tiles), int(reps), C.byref(ms)))
+    return ms.value
+
+
+def rflbm_testing_forward(method, f):
+    """Testing (include/rflbm_testing.h): the forward projection alone; f: (27, n) float32
+    populations, n a multiple of 128. Returns the (10, n) raw moments of order <= 2.
+    method 0: float32 FMAs as in the step kernels, 1: tcgen05 MMA with float16 operands."""
+    f = np.ascontiguousarray(f, dtype=np.float32)
+    m = np.empty((10, f.shape[1]), dtype=np.float32)
+    _check(lib.rflbm_testing_forward(int(method), f.ctypes.data, f.shape[1], m.ctypes.data))
+    return m
+
+
+def rflbm_testing_forward_time(method, tiles, reps):
+    """Testing: milliseconds of one launch over `tiles` tiles of 128 sites, `reps` synthetic
+    projections per site."""
+    ms = C.c_float()
+    _check(lib.rflbm_testing_forward_time(int(method), int(tiles), int(reps), C.byref(ms)))
     return ms.value
 
 

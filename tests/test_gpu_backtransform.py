@@ -56,3 +56,34 @@ def test_both_forms_time(R):
 
 def test_noise_draw_alone_times(R):
     assert R.rflbm_testing_noise_time(1 << 20) > 0.0
+
+
+def _raw_moments(f):
+    """m_pqr = sum_i f_i c_x^p c_y^q c_z^r for the ten exponent triples of order <= 2, in FP64."""
+    exps = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2),
+            (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+    m = np.zeros((10, f.shape[1]))
+    for i, (a, b, c) in enumerate(itertools.product((-1, 0, 1), repeat=3)):
+        for k, (p, q, r) in enumerate(exps):
+            m[k] += float(a) ** p * float(b) ** q * float(c) ** r * f[i]
+    return m
+
+
+def test_mma_forward_projection_is_exact_for_float16_populations(R):
+    """Populations that are float16 values (as 16-bit storage gives them): the tensor-core
+    projection with float16 operands and float32 accumulation equals the FP64 moments within
+    float32 accumulation, and so does the FMA form."""
+    g = np.random.default_rng(7)
+    n = 128 * 40
+    f = (g.normal(0.0, 1e-2, (27, n)) + 1.0 / 27.0).astype(np.float16).astype(np.float32)
+    want = _raw_moments(f.astype(np.float64))
+    scale = np.max(np.abs(want))
+    for method in (0, 1):
+        got = R.rflbm_testing_forward(method, f)
+        err = np.max(np.abs(got - want)) / scale
+        assert err < 2e-6, (method, err)
+
+
+def test_forward_forms_time(R):
+    for method in (0, 1):
+        assert R.rflbm_testing_forward_time(method, 152 * 4, 4) > 0.0
