@@ -392,6 +392,46 @@ def advance(R, box, steps, exchange=None):
         exchange()
 
 
+def slab_rings(R, torch, args, peak, sizes=(2, 4)):
+    """K z-slabs of one periodic edge x edge x (K edge) box on this GPU, one edge^3 slab each,
+    on one stream, their faces exchanged by rflbm_slab_exchange after every step: the cost
+    of the decomposition with real neighbours, without the link between GPUs."""
+    storage = {"f32": R.RFLBM_STORE_F32, "f16": R.RFLBM_STORE_F16, "bf16": R.RFLBM_STORE_BF16}[args.storage]
+    pattern = {"pingpong": R.RFLBM_PATTERN_PINGPONG, "aa": R.RFLBM_PATTERN_AA}[args.pattern]
+    e = args.edge
+    steps = max(20, min(args.steps, 500))
+    out = {}
+    for k in sizes:
+        stream = torch.cuda.Stream()
+        slabs = [R.Box(e, e, e, tau=args.tau, kT=args.kT, seed=1, stream=stream.cuda_stream, storage=storage,
+                       pattern=pattern, z0=i * e, nz_global=k * e) for i in range(k)]
+        for b in slabs:
+            R.rflbm_init_rest(b.h)
+        hs = [b.h for b in slabs]
+
+        def step():
+            for b in slabs:
+                R.rflbm_step(b.h, 1)
+            R.rflbm_slab_exchange(hs)
+        for _ in range(10):
+            step()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            step()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        sites = k * e ** 3
+        out[str(k)] = {"slabs": k, "box": [e, e, k * e], "steps": steps, "ms_per_step": ms,
+                       "value": sites / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                       "roofline_frac": BYTES_PER_SITE[args.storage] * sites / (ms * 1e-3) / 1e9 / peak}
+        for b in slabs:
+            b.close()
+    return out
+
+
 def ensemble_arm(args):
     """The 64-replica ensemble (edges 16-96, seeds 1..64, kT log-uniform in [1e-5, 1e-3],
     tau uniform in [0.55, 1.2]) advanced together: MLUPS over all replicas, one CUDA graph
@@ -754,9 +794,12 @@ def gb300_arm(args):
                 "frac": achieved / peak, "traffic": None if slab else profiled_traffic(kstem, e),
                 "peak_source": f"hbm_gbs of {peak_kind}", "kernel": kname,
                 "algorithmic_bytes_per_launch": BYTES_PER_SITE[args.storage] * n}
+    rings = None
     if slab:
         roofline["kernel"] = f"{kname}: boundary rows, interior rows, face exchange (per step)"
         roofline["algorithmic_bytes_per_step"] = roofline.pop("algorithmic_bytes_per_launch")
+        if info.world == 1:
+            rings = slab_rings(R, torch, args, peak)
     cpu = None
     if not args.no_cpu_baseline and info.world == 1:  # the oracle baseline is an N = 1 figure
         r = oracle_sample_rate(e, args.tau, args.kT, budget_s=12.0, steps=None)
@@ -776,6 +819,8 @@ def gb300_arm(args):
         "variants": variants,
         "storage_accuracy": accuracy,
     }
+    if rings is not None:
+        line["slab_rings_one_gpu"] = rings
     print(json.dumps(line))
     dist.finalize(info)
     return 0
