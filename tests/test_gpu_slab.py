@@ -110,6 +110,30 @@ def test_slab_models_and_kernels(R, model):
             b.close()
 
 
+@pytest.mark.parametrize("kernel", ["gather", "tma"])
+@pytest.mark.parametrize("omega_g,phi", [(1.4, "local"), (0.7, "rho0"), (1.0, "rho0")])
+def test_slab_ghost_rates_and_noise_density(R, kernel, omega_g, phi):
+    """Ghost relaxation omega_g != 1 (the Eq. 22 reconstruction) and the noise amplitude at
+    rho0 (Eq. 10 with rho0) on slabs, against the whole box bit for bit, on both kernels."""
+    shape, sizes = (64, 5, 9), (4, 3, 2)
+    f0 = _state(shape, seed=13)
+    k = {"gather": R.RFLBM_KERNEL_GATHER, "tma": R.RFLBM_KERNEL_TMA}[kernel]
+    p = {"local": R.RFLBM_PHI_LOCAL_RHO, "rho0": R.RFLBM_PHI_RHO0}[phi]
+    kw = dict(tau=0.75, kT=2e-4, seed=17, omega_g=omega_g, phi_rho=p, kernel=k)
+    whole = R.Box(*shape, **kw)
+    R.rflbm_set_populations(whole.h, f0)
+    slabs = _split(shape, sizes, f0, R, **kw)
+    for _ in range(5):
+        for b in slabs:
+            R.rflbm_step(b.h, 1)
+        R.rflbm_slab_exchange([b.h for b in slabs])
+    R.rflbm_step(whole.h, 5)
+    assert np.array_equal(_gather(slabs), whole.populations())
+    whole.close()
+    for b in slabs:
+        b.close()
+
+
 def test_one_slab_is_periodic_through_its_own_faces(R):
     shape = (32, 4, 6)
     f0 = _state(shape, seed=3)
