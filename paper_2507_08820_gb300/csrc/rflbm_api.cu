@@ -63,6 +63,11 @@ struct rflbm {
   cudaStream_t halo_stream = nullptr; // copies of rflbm_slab_exchange
 };
 
+namespace rflbm_dev {
+// The row-segment width for rows that no width divides (rflbm_step_tma.cu), 0 when none.
+int tma_ragged_width(uint32_t nx, size_t elem);
+}  // namespace rflbm_dev
+
 namespace {
 
 thread_local std::string g_error;
@@ -255,9 +260,12 @@ bool encode_map(CUtensorMap* map, void* base, const Geometry& g, uint32_t box_x,
 void setup_tma(rflbm* h) {
   h->tma_width = 0;
   h->kernel = RFLBM_KERNEL_GATHER;
-  const int w = tma_segment_width(h->geo.nx);
-  if (w == 0 || h->cfg.kernel == RFLBM_KERNEL_GATHER) return;
   const int st = h->variant.storage;
+  int w = tma_segment_width(h->geo.nx);
+  // rows that no width divides: ragged last segments, for the ping-pong kernels only (the AA
+  // kernels' in-place slots need whole segments)
+  if (w == 0 && !h->aa) w = tma_ragged_width(h->geo.nx, storage_bytes(st));
+  if (w == 0 || h->cfg.kernel == RFLBM_KERNEL_GATHER) return;
   const uint32_t halo = st == kStoreF32 ? 4 : 8;  // 16 bytes each side
   for (int b = 0; b < (h->aa ? 1 : 2); ++b) {
     // loads: the three planes of one source row; stores: all 27 planes of the segment

@@ -56,6 +56,29 @@ int tma_segment_width(uint32_t nx) {
   return 0;
 }
 
+int tma_ragged_width(uint32_t nx, size_t elem) {
+  // rows that no width divides but that are whole 16-byte units (the tensor maps' row
+  // pitch): the last segment of each row ends past the row. Of the widths whose padded row
+  // keeps at least 77 % of the threads busy, the one with the fewest padded threads per
+  // measured efficiency of its width (one-site float32 at 128^3: 128 and 192 sites 94-96 %,
+  // 96 sites about 91 %, 64 sites 87 %, 32 sites 85 %); 0 when none qualifies.
+  if (nx == 0 || (nx * elem) % 16 != 0) return 0;
+  const int widths[5] = {128, 192, 96, 64, 32};
+  const double eff[5] = {1.0, 1.0, 0.97, 0.92, 0.90};
+  int best = 0;
+  double best_cost = 0.0;
+  for (int k = 0; k < 5; ++k) {
+    const uint32_t padded = (nx + widths[k] - 1) / widths[k] * widths[k];
+    if (padded > 1.3 * nx) continue;
+    const double cost = padded / eff[k];
+    if (best == 0 || cost < best_cost) {
+      best = widths[k];
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
 cudaError_t launch_step_tma(const TmaMaps& m, const StepParams& p, const StepVariant& v,
                             cudaStream_t stream) {
   if (v.storage != kStoreF32) return launch_step_tma_16(m, p, v, stream);

@@ -1,6 +1,8 @@
-// The fused stream-and-collide step with TMA staging, for boxes whose x edge is a
-// multiple of the row-segment width kW in {32, 64, 96, 128, 192}; templated on the
-// storage format.
+// The fused stream-and-collide step with TMA staging, for boxes whose rows are whole
+// 16-byte units, in row segments of width kW in {32, 64, 96, 128, 192}; templated on the
+// storage format. Where kW does not divide the x edge, the last segment of each row ends
+// past it: the copies fill its missing sites with zeros, its excess threads compute on
+// them, and the store of the segment is clipped at the row's end.
 //
 // One CTA of kW threads updates one row segment [x0, x0 + kW) of one lattice row (y, z).
 // The 27 populations of a site are pulled from 9 source rows (y - c_y, z - c_z), shifted
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
   T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
 
   const int t = threadIdx.x;
-  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t nseg = (p.geo.nx + kW - 1) / kW;  // the last segment of a row may end past x = nx - 1
   const uint32_t rb = blockIdx.x / nseg;
   const uint32_t row = p.row0 + rb + (rb >= p.row_split ? p.row_gap : 0u);  // y + ny * z
   const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
@@ -101,9 +103,9 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 0) step_
       patch_l = src[(int64_t)(3 * t + 2) * p.geo.ps + rowoff + (p.geo.nx - 1)];
       at_l = t * L::kGroup + 2 * L::kSeg + kH - 1;
     }
-    if (x0 + kW == p.geo.nx) {
+    if (x0 + kW >= p.geo.nx) {  // right of the row's last site, at x0 + kW or inside the segment
       patch_r = src[(int64_t)(3 * t) * p.geo.ps + rowoff];
-      at_r = t * L::kGroup + kH + kW;
+      at_r = t * L::kGroup + kH + (int)(p.geo.nx - x0);
     }
   }
 
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ 
   T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
 
   const int t = threadIdx.x;
-  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t nseg = (p.geo.nx + kW - 1) / kW;  // the last segment of a row may end past x = nx - 1
   const uint32_t rb = blockIdx.x / nseg;
   const uint32_t row = p.row0 + rb + (rb >= p.row_split ? p.row_gap : 0u);  // y + ny * z
   const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
@@ -207,9 +209,9 @@ __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ 
       patch_l = src[(int64_t)(3 * t + 2) * p.geo.ps + rowoff + (p.geo.nx - 1)];
       at_l = t * L::kGroup + 2 * L::kSeg + kH - 1;
     }
-    if (x0 + kW == p.geo.nx) {
+    if (x0 + kW >= p.geo.nx) {  // right of the row's last site, at x0 + kW or inside the segment
       patch_r = src[(int64_t)(3 * t) * p.geo.ps + rowoff];
-      at_r = t * L::kGroup + kH + kW;
+      at_r = t * L::kGroup + kH + (int)(p.geo.nx - x0);
     }
   }
 
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kW / 2) step_tma_pair(const __grid_constant__ 
 
 template <int kStore, int kW, bool kNoise>
 cudaError_t launch_tma_pair(const TmaMaps& m, const StepParams& p, cudaStream_t st) {
-  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.nrows;
+  const uint64_t blocks = (uint64_t)((p.geo.nx + kW - 1) / kW) * p.nrows;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kW / 2);
@@ -271,7 +273,7 @@ cudaError_t launch_tma_pair(const TmaMaps& m, const StepParams& p, cudaStream_t 
 
 template <int kStore, int kW, int kModel, bool kNoise, bool kGhostNeq, bool kPhiRho0>
 cudaError_t launch_tma_segment(const TmaMaps& m, const StepParams& p, cudaStream_t st) {
-  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.nrows;
+  const uint64_t blocks = (uint64_t)((p.geo.nx + kW - 1) / kW) * p.nrows;
   // programmatic stream serialisation: this launch may begin while the previous kernel
   // of the stream drains (the kernel waits for it before touching global memory)
   cudaLaunchConfig_t cfg = {};

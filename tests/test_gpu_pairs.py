@@ -58,7 +58,10 @@ def test_float32_fluctuating_aa_odd_steps(R, nx, odd_pairs):
     box.close()
 
 
-SHAPES = [(32, 5, 4), (64, 6, 5), (96, 4, 3), (128, 3, 3), (192, 3, 2), (256, 3, 2), (160, 3, 2)]
+# the last four with ragged last segments in ping-pong (16-bit storage: 104 and 200; 100 and
+# 300 are no whole 16-byte units there and run the gather kernel on both sides)
+SHAPES = [(32, 5, 4), (64, 6, 5), (96, 4, 3), (128, 3, 3), (192, 3, 2), (256, 3, 2), (160, 3, 2),
+          (100, 5, 4), (104, 4, 3), (200, 3, 2), (300, 2, 2)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)

@@ -100,12 +100,16 @@ def test_normals_accurate_for_extreme_radius_draws(R):
 
 
 # ------------------------------------------------------------------- one step, ragged boxes
-# (shape, TMA row-segment width): the TMA kernels need x edges that are multiples of 32
-# (single- and multi-segment rows below); other boxes run the general gather kernel
+# (shape, TMA row-segment width): the TMA kernels take x edges that a width divides (single-
+# and multi-segment rows below), and other rows of whole 16-byte units with a ragged last
+# segment where at least 77 % of the threads stay busy (100, 132, 200, 260, 300, 1000);
+# other boxes run the general gather kernel (48: a 64-site segment would idle a third)
 SHAPES = [((1, 1, 1), 0), ((2, 3, 4), 0), ((5, 1, 7), 0), ((17, 9, 5), 0), ((33, 31, 7), 0),
           ((32, 3, 2), 32), ((96, 4, 3), 96), ((64, 5, 3), 64), ((128, 2, 2), 128),
           ((256, 3, 1), 128), ((32, 1, 1), 32), ((128, 9, 7), 128), ((192, 3, 2), 192),
-          ((288, 2, 3), 96), ((576, 2, 1), 192), ((160, 3, 2), 32), ((320, 2, 2), 64)]
+          ((288, 2, 3), 96), ((576, 2, 1), 192), ((160, 3, 2), 32), ((320, 2, 2), 64),
+          ((100, 3, 2), 128), ((132, 3, 2), 32), ((200, 2, 2), 32), ((260, 2, 2), 96),
+          ((300, 2, 1), 64), ((1000, 1, 2), 128), ((48, 3, 2), 0)]
 KERNELS = ["gather", "tma"]
 
 

@@ -55,10 +55,13 @@ def _gather(slabs):
     return np.concatenate([b.populations() for b in slabs], axis=1)
 
 
-CASES = [  # shape, slab sizes: TMA rows of one segment (W = nx), of several, the general kernel
+CASES = [  # shape, slab sizes: TMA rows of one segment (W = nx), of several, ragged last
+    # segments (ping-pong; 104 also in 16-bit storage), the general kernel
     ((64, 6, 12), (5, 6, 1)),
     ((128, 4, 7), (3, 4)),
     ((256, 3, 5), (2, 1, 2)),
+    ((100, 4, 9), (4, 5)),
+    ((104, 3, 6), (2, 4)),
     ((12, 10, 9), (4, 5)),
     ((12, 10, 9), (3, 3, 3)),
 ]
