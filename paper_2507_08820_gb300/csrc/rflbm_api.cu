@@ -262,9 +262,8 @@ void setup_tma(rflbm* h) {
   h->kernel = RFLBM_KERNEL_GATHER;
   const int st = h->variant.storage;
   int w = tma_segment_width(h->geo.nx);
-  // rows that no width divides: ragged last segments, for the ping-pong kernels only (the AA
-  // kernels' in-place slots need whole segments)
-  if (w == 0 && !h->aa) w = tma_ragged_width(h->geo.nx, storage_bytes(st));
+  // rows that no width divides: ragged last segments (whose excess threads store nothing)
+  if (w == 0) w = tma_ragged_width(h->geo.nx, storage_bytes(st));
   if (w == 0 || h->cfg.kernel == RFLBM_KERNEL_GATHER) return;
   const uint32_t halo = st == kStoreF32 ? 4 : 8;  // 16 bytes each side
   for (int b = 0; b < (h->aa ? 1 : 2); ++b) {

@@ -1,6 +1,9 @@
 // The fused stream-and-collide step in the AA pattern: one population buffer updated in
-// place, with TMA staging; for boxes whose x edge is a multiple of the row-segment width
-// kW in {32, 64, 96, 128, 192}; templated on the storage format.
+// place, with TMA staging; for boxes whose rows are whole 16-byte units, in row segments
+// of width kW in {32, 64, 96, 128, 192}; templated on the storage format. Where kW does not
+// divide the x edge, the last segment of each row ends past it: the copies fill its missing
+// sites with zeros, the even form's store is clipped at the row's end, and the odd form's
+// excess threads store nothing.
 //
 // Between steps the buffer alternates between two views of the same populations
 // (P = plane_of, opp(i) the population with velocity -c_i, P(opp(i)) = 26 - P(i)):
@@ -56,7 +59,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 1152 / k
   T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
 
   const int t = threadIdx.x;
-  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t nseg = (p.geo.nx + kW - 1) / kW;  // the last segment of a row may end past x = nx - 1
   const uint32_t rb = blockIdx.x / nseg;
   const uint32_t row = p.row0 + rb + (rb >= p.row_split ? p.row_gap : 0u);  // y + ny * z
   const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 1152 / k
   T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
 
   const int t = threadIdx.x;
-  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t nseg = (p.geo.nx + kW - 1) / kW;  // the last segment of a row may end past x = nx - 1
   const uint32_t rb = blockIdx.x / nseg;
   const uint32_t row = p.row0 + rb + (rb >= p.row_split ? p.row_gap : 0u);  // y + ny * z
   const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
@@ -181,9 +184,9 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 1152 / k
       patch_l = buf[(int64_t)(3 * mirror) * p.geo.ps + rowoff + (p.geo.nx - 1)];
       at_l = t * L::kGroup + kH - 1;
     }
-    if (x0 + kW == p.geo.nx) {
+    if (x0 + kW >= p.geo.nx) {  // right of the row's last site, at x0 + kW or inside the segment
       patch_r = buf[(int64_t)(3 * mirror + 2) * p.geo.ps + rowoff];
-      at_r = t * L::kGroup + 2 * L::kSeg + kH + kW;
+      at_r = t * L::kGroup + 2 * L::kSeg + kH + (int)(p.geo.nx - x0);
     }
   }
 
@@ -249,7 +252,8 @@ __global__ void __launch_bounds__(kW, kModel == kModelBgk ? 1024 / kW : 1152 / k
   }
 
   // population i of x goes to plane P(i) at x + c_i (coalesced: a warp writes 32
-  // consecutive positions of each plane)
+  // consecutive positions of each plane); the excess threads of a ragged segment store nothing
+  if (x >= p.geo.nx) return;
   T* const dst = buf + s + (int64_t)p.geo.zlo * p.geo.nxy;
 #pragma unroll
   for (int i = 0; i < kQ; ++i)
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_even_pair(const __grid_constan
   T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
 
   const int t = threadIdx.x;
-  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t nseg = (p.geo.nx + kW - 1) / kW;  // the last segment of a row may end past x = nx - 1
   const uint32_t rb = blockIdx.x / nseg;
   const uint32_t row = p.row0 + rb + (rb >= p.row_split ? p.row_gap : 0u);  // y + ny * z
   const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
   T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
 
   const int t = threadIdx.x;
-  const uint32_t nseg = p.geo.nx / kW;
+  const uint32_t nseg = (p.geo.nx + kW - 1) / kW;  // the last segment of a row may end past x = nx - 1
   const uint32_t rb = blockIdx.x / nseg;
   const uint32_t row = p.row0 + rb + (rb >= p.row_split ? p.row_gap : 0u);  // y + ny * z
   const uint32_t x0 = (blockIdx.x - rb * nseg) * kW;
@@ -371,9 +375,9 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
       patch_l = buf[(int64_t)(3 * mirror) * p.geo.ps + rowoff + (p.geo.nx - 1)];
       at_l = t * L::kGroup + kH - 1;
     }
-    if (x0 + kW == p.geo.nx) {
+    if (x0 + kW >= p.geo.nx) {  // right of the row's last site, at x0 + kW or inside the segment
       patch_r = buf[(int64_t)(3 * mirror + 2) * p.geo.ps + rowoff];
-      at_r = t * L::kGroup + 2 * L::kSeg + kH + kW;
+      at_r = t * L::kGroup + 2 * L::kSeg + kH + (int)(p.geo.nx - x0);
     }
   }
   const PullDeltas d = deltas_at(x, y, z, p.geo);
@@ -434,7 +438,9 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
 
   // population i of x and x + 1 goes to plane P(i) at x + c_i and x + 1 + c_i: the rows
   // (y, z) shifts are shared; along x, x + 1 never wraps from x (x is even, nx is even),
-  // x - 1 wraps when x = 0, and x + 2 wraps when x + 2 = nx
+  // x - 1 wraps when x = 0, and x + 2 wraps when x + 2 = nx; the excess threads of a ragged
+  // segment store nothing
+  if (x >= p.geo.nx) return;
   T* const dst = buf + s + (int64_t)p.geo.zlo * p.geo.nxy;
   const int32_t dxb_plus = (x + 2u == p.geo.nx) ? 1 - (int32_t)p.geo.nx : 1;
 #pragma unroll
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(kW / 2) step_aa_odd_pair(const __grid_constant
 
 template <int kStore, int kW, bool kNoise>
 cudaError_t launch_aa_pair(const TmaMaps& m, const StepParams& p, bool odd, cudaStream_t st) {
-  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.nrows;
+  const uint64_t blocks = (uint64_t)((p.geo.nx + kW - 1) / kW) * p.nrows;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kW / 2);
@@ -477,7 +483,7 @@ cudaError_t launch_aa_pair(const TmaMaps& m, const StepParams& p, bool odd, cuda
 
 template <int kStore, int kW, int kModel, bool kNoise>
 cudaError_t launch_aa_segment(const TmaMaps& m, const StepParams& p, bool odd, cudaStream_t st) {
-  const uint64_t blocks = (uint64_t)(p.geo.nx / kW) * p.nrows;
+  const uint64_t blocks = (uint64_t)((p.geo.nx + kW - 1) / kW) * p.nrows;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kW);
