@@ -301,10 +301,12 @@ int rflbm_site_normals(uint64_t seed, int64_t step, uint32_t replica,
  * none does; or 0 (autotuned): the same, except that for each row length that takes row
  * tiles the library times the replicas of that row length alone, a few steps at every size
  * their rows divide, at creation, and keeps the fastest (the state is undefined until the
- * initialisation call that must follow anyway). A replica whose row length nx divides its
- * tile size, is at most 256 and is a whole number of 16-byte units takes tiles of tile / nx
- * whole rows moved by TMA copies (run by tile / 2 threads of two sites each in 16-bit
- * storage); any other replica takes tiles of `tile` consecutive sites, one thread each. A step is one launch per tile size and
+ * initialisation call that must follow anyway). A replica whose row length nx is at most
+ * 256 and a whole number of 16-byte units takes tiles of floor(tile / nx) whole rows moved by
+ * TMA copies (run by tile / 2 threads of two sites each in 16-bit storage) when nx divides its
+ * tile size or those rows keep at least 85 % of the tile's threads busy (with -1 and 0 such
+ * partial tiles are chosen only up to 256 sites, exact divisors first); any other replica
+ * takes tiles of `tile` consecutive sites, one thread each. A step is one launch per tile size and
  * kind of tile in use (per group of 64 replicas). A bounded wait for a copy that expires makes
  * the call report RFLBM_ETIMEOUT. The library allocates and owns all device memory. */
 typedef struct rflbm_batch rflbm_batch_t;

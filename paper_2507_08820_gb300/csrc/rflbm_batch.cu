@@ -79,14 +79,13 @@ constexpr int kBatchGroups = 9;  // source rows (c_y, c_z) of a site
 // Rows tiles are held to 56 registers (65536 / (kTile 56) resident CTAs per SM), which they
 // fit without spilling: the replica's parameters are read from the launch parameters and
 // the noise is held as 24 normals.
-template <int kStore, int kTile, bool kRows>
+template <int kStore, int kTile, bool kRows, bool kFull = true>
 __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
     k_batch_step(const __grid_constant__ ReplicaTable tab, const int* __restrict__ tile_rep, int64_t tile0,
                  const unsigned long long* run, uint32_t k, int* err) {
   using S = Storage<kStore>;
   using T = typename S::T;
   constexpr int kGroup = (int)(batch_group_bytes(kTile, sizeof(T)) / sizeof(T));  // elements
-  constexpr int rn = kTile;  // sites of a rows tile (R nx)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   T* const sm = reinterpret_cast<T*>(smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u));
@@ -132,6 +131,9 @@ __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
 
   // ---- rows tile: R rows of slab z from y0
   const uint32_t R = rep.rows;
+  // sites of the tile (R nx): kTile for full tiles, fewer where nx does not divide kTile (the
+  // threads from R nx on stay idle)
+  const int rn = kFull ? kTile : (int)(R * rep.geo.nx);
   const uint32_t nx = rep.geo.nx, ny = rep.geo.ny, nz = rep.geo.nz;
   const uint32_t z = li / rep.yblocks;
   const uint32_t y0 = (li - z * rep.yblocks) * R;
@@ -221,14 +223,13 @@ __global__ void __launch_bounds__(kTile, kRows ? 65536 / (kTile * 56) : 0)
 // Rows tiles with two sites per thread (16-bit storage): kTile sites, kTile / 2 threads,
 // thread t updating sites 2t and 2t + 1 of the tile (one row: nx is even) with the packed
 // collision of the single-box two-site kernels, the storage scale folded into the weights.
-template <int kStore, int kTile>
+template <int kStore, int kTile, bool kFull = true>
 __global__ void __launch_bounds__(kTile / 2)
     k_batch_rows_pair(const __grid_constant__ ReplicaTable tab, const int* __restrict__ tile_rep, int64_t tile0,
                       const unsigned long long* run, uint32_t k, int* err) {
   using S = Storage<kStore>;
   using T = typename S::T;
   constexpr int kGroup = (int)(batch_group_bytes(kTile, sizeof(T)) / sizeof(T));
-  constexpr int rn = kTile;
   constexpr int kThreads = kTile / 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -248,6 +249,7 @@ __global__ void __launch_bounds__(kTile / 2)
   const uint32_t li = (uint32_t)(j - rep.tile_begin);
 
   const uint32_t R = rep.rows;
+  const int rn = kFull ? kTile : (int)(R * rep.geo.nx);  // sites of the tile, as in k_batch_step
   const uint32_t nx = rep.geo.nx, ny = rep.geo.ny, nz = rep.geo.nz;
   const uint32_t z = li / rep.yblocks;
   const uint32_t y0 = (li - z * rep.yblocks) * R;
@@ -350,6 +352,7 @@ struct BatchLaunch {
   int group;
   int tile;
   bool rows;
+  bool full;  // rows tiles: R nx = tile (else fewer sites, the rest of the threads idle)
   int64_t begin, end;
 };
 
@@ -357,9 +360,18 @@ template <int kStore, int kTile>
 static cudaError_t prepare_t() {
   const size_t smem = batch_smem_bytes(kTile, storage_bytes(kStore));
   if (smem <= 48 * 1024) return cudaSuccess;
-  if constexpr (batch_rows_pairs<kStore>())
-    return cudaFuncSetAttribute(k_batch_rows_pair<kStore, kTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaFuncSetAttribute(k_batch_step<kStore, kTile, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if constexpr (batch_rows_pairs<kStore>()) {
+    if (cudaError_t e = cudaFuncSetAttribute(k_batch_rows_pair<kStore, kTile, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+      return e;
+    return cudaFuncSetAttribute(k_batch_rows_pair<kStore, kTile, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem);
+  }
+  if (cudaError_t e = cudaFuncSetAttribute(k_batch_step<kStore, kTile, true, true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
+    return e;
+  return cudaFuncSetAttribute(k_batch_step<kStore, kTile, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
 }
 
 // Step k of a run for the tiles of launch L, chained to the previous launch on the stream
@@ -380,9 +392,11 @@ static cudaError_t launch_one_t(const ReplicaTable& tab, const BatchLaunch& L, c
   cfg.dynamicSmemBytes = batch_smem_bytes(kTile, storage_bytes(kStore));
   if constexpr (batch_rows_pairs<kStore>()) {
     cfg.blockDim = dim3(kTile / 2);
-    return cudaLaunchKernelEx(&cfg, k_batch_rows_pair<kStore, kTile>, tab, tile_rep, L.begin, run, k, err);
+    if (L.full) return cudaLaunchKernelEx(&cfg, k_batch_rows_pair<kStore, kTile, true>, tab, tile_rep, L.begin, run, k, err);
+    return cudaLaunchKernelEx(&cfg, k_batch_rows_pair<kStore, kTile, false>, tab, tile_rep, L.begin, run, k, err);
   } else {
-    return cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, true>, tab, tile_rep, L.begin, run, k, err);
+    if (L.full) return cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, true, true>, tab, tile_rep, L.begin, run, k, err);
+    return cudaLaunchKernelEx(&cfg, k_batch_step<kStore, kTile, true, false>, tab, tile_rep, L.begin, run, k, err);
   }
 }
 
@@ -397,9 +411,9 @@ static int occupancy_t(bool rows) {
     if (prepare_t<kStore, kTile>() != cudaSuccess) return 1;
     const size_t smem = batch_smem_bytes(kTile, storage_bytes(kStore));
     if constexpr (batch_rows_pairs<kStore>())
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_rows_pair<kStore, kTile>, kTile / 2, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_rows_pair<kStore, kTile, true>, kTile / 2, smem);
     else
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<kStore, kTile, true>, kTile, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<kStore, kTile, true, true>, kTile, smem);
   }
   if (e != cudaSuccess) return 1;
   return std::max(n, 1);
@@ -561,14 +575,33 @@ bool rows_eligible(const rflbm_batch* b, const Geometry& g) {
   return (g.nx * storage_bytes(b->storage)) % 16 == 0 && g.nx <= 256;
 }
 
+// Share of a tile's threads that a replica's rows tiles keep busy (whole rows, floor(t / nx)
+// of them; 0 when a row is longer than the tile).
+double row_tile_use(const Geometry& g, int t) { return (double)((uint32_t)t / g.nx * g.nx) / t; }
+// partial rows tiles below this take site tiles (uniform float32 ensembles, 2000 steps: rows of
+// 40 sites 3 to a 128-site tile, 94 % busy, 71.7 % against 64.0 % in site tiles; rows of 100
+// one to a tile, 78 % busy, 63.1 % against 65.5 %)
+constexpr double kMinRowTileUse = 0.85;
+
+// Whether a replica at tile size t takes rows tiles: eligible rows that t divides, or whose
+// whole rows keep at least kMinRowTileUse of t's threads busy.
+bool takes_rows(const rflbm_batch* b, const Geometry& g, int t) {
+  return rows_eligible(b, g) && (uint32_t)t >= g.nx &&
+         ((uint32_t)t % g.nx == 0 || row_tile_use(g, t) >= kMinRowTileUse);
+}
+
 // Tile size of a replica: `tile` when positive, else the first size of the storage format's
-// order of preference that takes the replica's rows (sites tiles of kAutoSitesTile when none).
+// order of preference that its row length divides, else the first of at most 256 sites whose
+// whole-row tiles keep at least kMinRowTileUse of the threads busy, else sites tiles of
+// kAutoSitesTile.
 int replica_tile(const rflbm_batch* b, const Geometry& g, int tile) {
   if (tile > 0) return tile;
   const int* pref = b->storage == kStoreF32 ? kPrefF32 : kPref16;
-  if (rows_eligible(b, g))
-    for (int k = 0; k < kNumTiles; ++k)
-      if (pref[k] % (int)g.nx == 0) return pref[k];
+  if (!rows_eligible(b, g)) return kAutoSitesTile;
+  for (int k = 0; k < kNumTiles; ++k)
+    if (pref[k] % (int)g.nx == 0) return pref[k];
+  for (int k = 0; k < kNumTiles; ++k)
+    if (pref[k] <= 256 && takes_rows(b, g, pref[k])) return pref[k];
   return kAutoSitesTile;
 }
 
@@ -586,7 +619,7 @@ int layout_replicas(rflbm_batch* b, const std::vector<int>& tile_of) {
     d.rows = 0;
     d.yblocks = 0;
     d.maps = nullptr;
-    if (rows_eligible(b, g) && t % g.nx == 0) {
+    if (takes_rows(b, g, t)) {
       const uint32_t R = (uint32_t)t / g.nx;
       bool ok = true;
       for (int k = 0; k < 2 && ok; ++k)
@@ -609,15 +642,17 @@ int layout_replicas(rflbm_batch* b, const std::vector<int>& tile_of) {
   std::vector<int64_t> sites_at(kNumTiles * 2, 0);  // [kind][tile]: sites updated by such tiles
   for (int g = 0; g < ngroups; ++g) {
     const int r0 = g * kGroupReps, r1 = std::min(b->n, r0 + kGroupReps);
-    for (int pass = 0; pass < 2; ++pass) {
+    // passes: full rows tiles, partial rows tiles, sites tiles
+    for (int pass = 0; pass < 3; ++pass) {
       for (int ti = 0; ti < kNumTiles; ++ti) {
-        BatchLaunch L{g, kBatchTiles[ti], pass == 0, tiles, tiles};
+        BatchLaunch L{g, kBatchTiles[ti], pass < 2, pass == 0, tiles, tiles};
         for (int r = r0; r < r1; ++r) {
           ReplicaDev& d = b->host[r];
-          if ((d.rows != 0) != L.rows || b->rep_tile[(size_t)r] != L.tile) continue;
+          const bool full = d.rows * d.geo.nx == (uint32_t)L.tile;
+          if ((d.rows != 0) != L.rows || b->rep_tile[(size_t)r] != L.tile || (L.rows && full != L.full)) continue;
           d.tile_begin = tiles;
           tiles += d.ntiles;
-          sites_at[(size_t)(pass * kNumTiles + ti)] += d.geo.n;
+          sites_at[(size_t)((pass == 2 ? 1 : 0) * kNumTiles + ti)] += d.geo.n;
         }
         L.end = tiles;
         if (L.end > L.begin) b->launches.push_back(L);
@@ -706,9 +741,23 @@ int autotune_tiles(rflbm_batch* b, std::vector<int>& tile_of) {
     for (int r = 0; r < b->n; ++r) in_class[(size_t)r] = b->host[r].geo.nx == nx && rows_eligible(b, b->host[r].geo);
     float best = 0.0f;
     int best_t = 0;
-    for (int k = 0; k < kNumTiles && rc == RFLBM_OK; ++k) {
-      const int t = pref[k];
-      if (t % (int)nx) continue;
+    // the class's size from the order of preference first (a size the row divides where there
+    // is one), then the other sizes that take its rows, and kAutoSitesTile (site tiles where
+    // it does not take them)
+    int cand[kNumTiles + 1];
+    int ncand = 0;
+    int first_in_class = 0;
+    for (int r = 0; r < b->n; ++r)
+      if (in_class[(size_t)r]) {
+        cand[ncand++] = tile_of[(size_t)r];
+        first_in_class = r;
+        break;
+      }
+    const Geometry& gc = b->host[first_in_class].geo;
+    for (int k = 0; k < kNumTiles; ++k)
+      if (pref[k] != cand[0] && (takes_rows(b, gc, pref[k]) || pref[k] == kAutoSitesTile)) cand[ncand++] = pref[k];
+    for (int c = 0; c < ncand && rc == RFLBM_OK; ++c) {
+      const int t = cand[c];
       for (int r = 0; r < b->n; ++r)
         if (in_class[(size_t)r]) tile_of[(size_t)r] = t;
       rc = layout_replicas(b, tile_of);

@@ -53,12 +53,29 @@ def _batch_pops(R, b, reps, r):
     return f
 
 
+def _launch_kinds(reps, storage, tile):
+    """Launch kinds of one step at an explicit tile size: full rows tiles (the row length
+    divides the tile), partial rows tiles (whole rows keeping at least 85 % of the threads
+    busy) and site tiles (rows that are no whole 16-byte units, longer than the tile, or
+    leaving too many threads idle)."""
+    elem = 4 if storage == 0 else 2
+    kinds = set()
+    for rep in reps:
+        nx = rep["nx"]
+        if (nx * elem) % 16 == 0 and nx <= 256 and nx <= tile and (
+                tile % nx == 0 or (tile // nx * nx) >= 0.85 * tile):
+            kinds.add("full" if tile % nx == 0 else "partial")
+        else:
+            kinds.add("sites")
+    return len(kinds)
+
+
 @pytest.mark.parametrize("storage", [0, 1, 2])
 @pytest.mark.parametrize("tile", [96, 128, 192, 256, 512])
 def test_replicas_reproduce_their_single_box_runs(R, storage, tile):
     b = R.rflbm_batch_create(SMALL, storage=storage, tile=tile)
     assert R.rflbm_batch_tuning(b)[0] == tile
-    assert R.rflbm_batch_launches_per_step(b) == 2  # nx = 16 takes row tiles, nx = 20 site tiles
+    assert R.rflbm_batch_launches_per_step(b) == _launch_kinds(SMALL, storage, tile)
     R.rflbm_batch_init_rest(b)
     for n in (3, 4, 3):  # several calls: odd/even buffer parity and the step index
         R.rflbm_batch_run(b, n)
@@ -71,7 +88,7 @@ def test_replicas_reproduce_their_single_box_runs(R, storage, tile):
 
 
 # per-replica tile sizes of SMALL (tile size, rows per tile) in float32 and in 16-bit storage
-PER_REPLICA = {0: [(128, 8), (96, 4), (128, 4), (128, 0), (128, 2), (128, 0), (128, 4), (128, 8)],
+PER_REPLICA = {0: [(128, 8), (96, 4), (128, 4), (128, 6), (128, 2), (128, 0), (128, 4), (128, 8)],
                1: [(128, 8), (192, 8), (128, 4), (128, 0), (128, 2), (128, 0), (128, 4), (128, 8)]}
 
 
@@ -79,11 +96,11 @@ PER_REPLICA = {0: [(128, 8), (96, 4), (128, 4), (128, 0), (128, 2), (128, 0), (1
 def test_per_replica_tiles_reproduce_single_box_runs(R, storage):
     """tile -1: every replica at the tile size its row length and storage select in the order
     of preference; the step runs one launch per size and kind (rows at 128 and at 96 or 192,
-    sites at 128)."""
+    in float32 also partial rows tiles at 128 for nx = 20: 6 rows of 20 sites; sites at 128)."""
     b = R.rflbm_batch_create(SMALL, storage=storage, tile=-1)
     assert R.rflbm_batch_tuning(b)[0] == -1
     assert [R.rflbm_batch_replica_tiling(b, r) for r in range(len(SMALL))] == PER_REPLICA[min(storage, 1)]
-    assert R.rflbm_batch_launches_per_step(b) == 3
+    assert R.rflbm_batch_launches_per_step(b) == (4 if storage == 0 else 3)
     R.rflbm_batch_init_rest(b)
     for n in (3, 4, 3):
         R.rflbm_batch_run(b, n)
@@ -105,7 +122,7 @@ def test_autotuned_tiles_are_valid_and_reproduce_single_box_runs(R, storage):
         tile, rows = R.rflbm_batch_replica_tiling(b, r)
         assert tile in (96, 128, 192, 256, 512)
         if rows:
-            assert tile % rep["nx"] == 0 and rows == tile // rep["nx"]
+            assert rows == tile // rep["nx"] and rows * rep["nx"] >= 0.85 * tile
             assert by_length.setdefault(rep["nx"], tile) == tile
         else:
             assert tile == 128 and PER_REPLICA[min(storage, 1)][r][1] == 0
@@ -115,6 +132,27 @@ def test_autotuned_tiles_are_valid_and_reproduce_single_box_runs(R, storage):
     R.rflbm_batch_synchronize(b)
     for r, rep in enumerate(SMALL):
         assert np.array_equal(_batch_pops(R, b, SMALL, r), _single(R, rep, 7, storage)), r
+    R.rflbm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("tile", [-1, 0])
+def test_partial_row_tiles_reproduce_single_box_runs(R, storage, tile):
+    """Row lengths that divide no tile size take tiles of whole rows with idle threads where
+    at least 85 % of the threads stay busy (40 and 120 at 128), else site tiles (100: one row
+    of a 128-site tile would idle 22 %; 72), bit for bit as single boxes."""
+    reps = [dict(nx=40, ny=9, nz=5, tau=0.6, kT=1e-4, seed=31), dict(nx=100, ny=5, nz=4, tau=0.9, kT=2e-4, seed=32),
+            dict(nx=120, ny=3, nz=3, tau=0.7, kT=0.0, seed=33), dict(nx=72, ny=7, nz=3, tau=1.1, kT=1e-3, seed=34)]
+    b = R.rflbm_batch_create(reps, storage=storage, tile=tile)
+    tiling = [R.rflbm_batch_replica_tiling(b, r) for r in range(len(reps))]
+    if tile == -1:
+        assert tiling == [(128, 3), (128, 0), (128, 1), (128, 0)]
+    R.rflbm_batch_init_rest(b)
+    R.rflbm_batch_run(b, 3)
+    R.rflbm_batch_run(b, 2)
+    R.rflbm_batch_synchronize(b)
+    for r, rep in enumerate(reps):
+        assert np.array_equal(_batch_pops(R, b, reps, r), _single(R, rep, 5, storage)), (r, tiling[r])
     R.rflbm_batch_destroy(b)
 
 
@@ -152,8 +190,9 @@ def test_three_launch_groups_and_more_launches_than_chains(R, storage):
     reps = [dict(nx=e, ny=e + (r % 3), nz=4 + r % 5, tau=0.55 + 0.01 * (r % 50), kT=1e-4 * (1 + r % 4),
                  seed=100 + r) for r, e in enumerate(edges[r % 5] for r in range(140))]
     b = R.rflbm_batch_create(reps, storage=storage, tile=-1)
-    # per group: rows at 128 (edges 8, 16) and at 96 (float32: 12, 24) or 192 (16-bit: 24),
-    # sites at 128 (20, and 12 in 16-bit storage, whose rows are no whole 16-byte units)
+    # per group: rows at 128 (edges 8, 16; float32 also 20 as partial tiles of 6 rows) and at
+    # 96 (float32: 12, 24) or 192 (16-bit: 24); 16-bit: sites at 128 for 12 and 20, whose rows
+    # are no whole 16-byte units
     assert R.rflbm_batch_launches_per_step(b) == 9
     R.rflbm_batch_init_rest(b)
     R.rflbm_batch_run(b, 4)
