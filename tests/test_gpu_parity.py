@@ -337,3 +337,32 @@ def test_full_size_128cubed_sampled_sites(R):
     # float32 rounding of the 27 stored values of each site (~2^-24 |g_i|, |g_i| < 1e-2)
     # summed with random signs over 2.1e6 sites: a drift of order 1e-6 per step
     assert np.max(np.abs(np.array(st1.momentum) - np.array(st0.momentum))) < 1e-5
+
+
+@pytest.mark.parametrize("shape", [(100, 4, 3), (200, 3, 2), (260, 2, 2)])
+@pytest.mark.parametrize("variant", [dict(model=1, kT=1e-4), dict(model=1, kT=0.0), dict(omega_g=1.3, kT=2e-4),
+                                     dict(phi_rho=1, kT=1e-4)])
+@pytest.mark.parametrize("pattern", [0, 1])
+def test_ragged_segments_match_the_gather_kernel_bitwise(R, shape, variant, pattern):
+    """Rows that no segment width divides run ragged last segments on the TMA kernels: BGK,
+    ghost relaxation omega_g != 1 and the rho0 noise amplitude give the gather kernel's bits
+    (AA: BGK only; the AA kernels carry neither omega_g != 1 nor the rho0 amplitude)."""
+    if pattern == 1 and variant.get("model", 0) != 1:
+        pytest.skip("AA steps run Reg-FLBM with omega_g = 1 and the local density, or BGK")
+    n = int(np.prod(shape))
+    rho, u = W.random_fields(*shape, seed=19, drho=0.02, du=0.03)
+    f0 = np.ascontiguousarray(o.equilibrium_state(rho, u) + W.population_perturbation(n, 20, 2e-4))
+    out = []
+    for kernel in (R.RFLBM_KERNEL_TMA, R.RFLBM_KERNEL_GATHER):
+        box = R.Box(*shape, tau=0.7, seed=5, kernel=kernel, pattern=pattern, **variant)
+        if kernel == R.RFLBM_KERNEL_TMA:
+            assert R.rflbm_step_path(box.h)[0] == R.RFLBM_KERNEL_TMA
+        R.rflbm_set_populations(box.h, f0)
+        snaps = []
+        for steps in (1, 1, 3):
+            R.rflbm_step(box.h, steps)
+            snaps.append(box.populations())
+        out.append(snaps)
+        box.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b), float(np.max(np.abs(a - b)))
