@@ -80,10 +80,14 @@ typedef enum {
 } rflbm_phi_rho;
 
 /* Step kernels. Both compute the same step; they differ in how the 27 neighbours are
- * fetched. The TMA kernel needs nx to be a multiple of 32 (row segments of 128, 192, 96,
- * 64 or 32 sites, the first that divides nx); on other boxes every choice runs the
- * general kernel. Some variants of the TMA kernel update two sites per thread with packed
- * arithmetic (rflbm_step_sites_per_thread), bit for bit like the one-site forms. */
+ * fetched. The TMA kernel runs in row segments of 128, 192, 96, 64 or 32 sites: the first
+ * that divides nx when nx is a multiple of 32; otherwise, when a row is a whole number of
+ * 16-byte units (nx a multiple of 4 in float32, of 8 in 16-bit storage), the width whose
+ * segments cover the row with the fewest idle threads per measured efficiency, the last
+ * segment of each row ending past it, provided at least 77 % of the threads stay busy
+ * (rflbm_step_path reports the width). On other boxes every choice runs the general kernel.
+ * Some variants of the TMA kernel update two sites per thread with packed arithmetic
+ * (rflbm_step_sites_per_thread), bit for bit like the one-site forms. */
 typedef enum {
   RFLBM_KERNEL_AUTO = 0,    /* TMA when the box allows it, else the general kernel */
   RFLBM_KERNEL_GATHER = 1,  /* one thread per site, 27 addressed loads */
