@@ -259,3 +259,22 @@ def test_replica_against_the_oracle(R):
         scale = np.maximum(np.abs(want), o.weights()[:, None])
         assert float(np.max(np.abs(got - want) / scale)) < 1e-5, r
     R.rflbm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_random_ensemble_autotuned(R, storage):
+    """A seeded random ensemble: 24 replicas with row lengths in 8..132 (multiples of 4, so
+    exact, partial and site tiles mix), random tau and kT, autotuned tiles; five sampled
+    replicas reproduce their single-box runs bit for bit after 3 steps."""
+    g = np.random.default_rng(2024 + storage)
+    reps = [dict(nx=int(4 * g.integers(2, 34)), ny=int(g.integers(2, 9)), nz=int(g.integers(1, 6)),
+                 tau=float(g.uniform(0.55, 1.3)), kT=float(10 ** g.uniform(-5, -3)), seed=int(500 + r))
+            for r in range(24)]
+    b = R.rflbm_batch_create(reps, storage=storage, tile=0)
+    R.rflbm_batch_init_rest(b)
+    R.rflbm_batch_run(b, 3)
+    R.rflbm_batch_synchronize(b)
+    for r in g.choice(len(reps), 5, replace=False):
+        r = int(r)
+        assert np.array_equal(_batch_pops(R, b, reps, r), _single(R, reps[r], 3, storage)), (r, reps[r]["nx"])
+    R.rflbm_batch_destroy(b)
