@@ -118,3 +118,20 @@ def test_binding_rejects_wrong_dtype_and_short_buffers_before_any_launch(lib):
         R.rflbm_stats_f32_noalloc(torch.zeros(27 * 10, dtype=torch.float16), 10)
     with pytest.raises(ValueError):
         R.rflbm_stats_f32_noalloc(torch.zeros(27 * 10 - 1, dtype=torch.float32), 10)
+
+
+def test_batch_create_validates_before_touching_the_device(lib):
+    """An ensemble with no replicas, an unknown storage format, a non-positive rho0, a tile
+    size outside {-1 (rule), 0 (autotuned), 96, 128, 192, 256, 512} or an invalid replica is
+    refused with RFLBM_EINVAL before any CUDA call, so the check runs without a GPU."""
+    from paper_2507_08820_gb300 import rflbm as R
+    good = dict(nx=16, ny=16, nz=16, tau=0.8, kT=1e-4, seed=1)
+    cases = [([], {}), ([good], dict(storage=9)), ([good], dict(rho0=0.0)),
+             ([good], dict(tile=100)), ([good], dict(tile=-2)), ([good], dict(tile=64)),
+             ([good, dict(good, tau=0.5)], {}), ([dict(good, nx=0)], {}),
+             ([dict(good, kT=-1.0)], {})]
+    for reps, kw in cases:
+        with pytest.raises(R.RflbmError) as e:
+            R.rflbm_batch_create(reps, **kw)
+        assert e.value.status == R.RFLBM_EINVAL, (reps, kw)
+        assert R.rflbm_last_error(), (reps, kw)
