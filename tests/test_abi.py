@@ -135,3 +135,28 @@ def test_batch_create_validates_before_touching_the_device(lib):
             R.rflbm_batch_create(reps, **kw)
         assert e.value.status == R.RFLBM_EINVAL, (reps, kw)
         assert R.rflbm_last_error(), (reps, kw)
+
+
+def test_slab_config_validation_without_gpu(lib):
+    """A z-slab (nz_global > 0) holds its nz rows between two ghost rows, so its buffers are
+    sized for nx ny (nz + 2) sites; rows outside the decomposed box, z0 without a slab, a
+    negative nz_global and a decomposed box of 2^31 sites or more are refused."""
+    from paper_2507_08820_gb300 import rflbm as R
+
+    def cfg(**kw):
+        c = R.rflbm_config_default()
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return c
+
+    whole = R.rflbm_buffer_bytes(cfg(nx=32, ny=32, nz=34))
+    assert R.rflbm_buffer_bytes(cfg(nx=32, ny=32, nz=32, z0=0, nz_global=64)) == whole
+    assert R.rflbm_buffer_bytes(cfg(nx=32, ny=32, nz=32, z0=32, nz_global=64)) == whole
+    assert R.rflbm_buffer_bytes(cfg(nx=32, ny=32, nz=1, z0=63, nz_global=64)) == \
+        R.rflbm_buffer_bytes(cfg(nx=32, ny=32, nz=3))
+    for bad in (dict(z0=1), dict(nz_global=-1), dict(z0=-1, nz_global=64),
+                dict(z0=33, nz_global=64), dict(nz=65, nz_global=64),
+                dict(nx=1300, ny=1300, nz=2, nz_global=1300)):
+        with pytest.raises(R.RflbmError) as e:
+            R.rflbm_buffer_bytes(cfg(**{"nx": 32, "ny": 32, "nz": 32, **bad}))
+        assert e.value.status == R.RFLBM_EINVAL, bad
